@@ -1,0 +1,131 @@
+"""Pins of the oracle's wedge element against closed forms from the paper (CPU only)."""
+import numpy as np
+import pytest
+
+from oracle.element import (GHAT, QC, basis, basis_ref_gradients, geometry, hourglass_vectors,
+                            viscous_element_matrix)
+from oracle.mesh import ShellMesh
+
+REF_NODES = [(0.0, 0.0, -1.0), (1.0, 0.0, -1.0), (0.0, 1.0, -1.0),
+             (0.0, 0.0, 1.0), (1.0, 0.0, 1.0), (0.0, 1.0, 1.0)]
+
+
+def random_wedges(n=6, seed=1):
+    """Wedges of a real shell mesh (one per diamond region), plus random nodal viscosity."""
+    m = ShellMesh(3, 5, 0.55, 1.0)
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(m.n_wedges, size=n, replace=False)
+    x = m.node_xyz(m.wedge_nodes(ids).ravel()).reshape(-1, 6, 3)
+    return x, np.exp(rng.normal(size=n))
+
+
+def test_basis_nodal_and_partition_of_unity():
+    for a, p in enumerate(REF_NODES):
+        np.testing.assert_allclose(basis(*p), np.eye(6)[a], atol=1e-15)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        xi, eta = rng.random(2) * 0.5
+        z = rng.uniform(-1, 1)
+        assert abs(basis(xi, eta, z).sum() - 1.0) < 1e-15
+    np.testing.assert_allclose(basis(*QC), 1.0 / 6.0, atol=1e-16)
+
+
+def test_reference_gradients_match_finite_differences():
+    """Central differences of the (at most bilinear) basis are exact up to rounding."""
+    h = 1e-4
+    for q in (QC, (0.2, 0.1, 0.3), (0.05, 0.7, -0.6)):
+        g = basis_ref_gradients(*q)
+        for m in range(3):
+            e = np.zeros(3); e[m] = h
+            fd = (basis(*(np.array(q) + e)) - basis(*(np.array(q) - e))) / (2 * h)
+            np.testing.assert_allclose(g[:, m], fd, atol=1e-11)
+    # closed form at q_c
+    np.testing.assert_allclose(GHAT[:, 2], [-1 / 6] * 3 + [1 / 6] * 3, atol=1e-16)
+    np.testing.assert_allclose(GHAT.sum(axis=0), 0.0, atol=1e-16)
+
+
+def test_gradients_reproduce_linear_fields():
+    """sum_j f(x_j) grad N_j(q_c) = grad f for every affine f (isoparametric map)."""
+    x, _ = random_wedges()
+    _, _, grad, _ = geometry(x)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        a, b = rng.normal(size=3), rng.normal()
+        got = np.einsum("nj,njc->nc", x @ a + b, grad)
+        np.testing.assert_allclose(got, np.broadcast_to(a, got.shape), atol=1e-12)
+
+
+def _energy_by_finite_differences(xe, ue, eta):
+    """Eq. (oneptenergy) evaluated from the interpolants x(q), u(q) by central differences."""
+    h = 1e-4
+
+    def interp(vals, q):
+        return basis(*q) @ vals
+
+    dx = np.empty((3, 3)); du = np.empty((3, 3))
+    for m in range(3):
+        e = np.zeros(3); e[m] = h
+        qp, qm = np.array(QC) + e, np.array(QC) - e
+        dx[:, m] = (interp(xe, qp) - interp(xe, qm)) / (2 * h)
+        du[:, m] = (interp(ue, qp) - interp(ue, qm)) / (2 * h)
+    gradu = du @ np.linalg.inv(dx)              # d u_c / d x_m
+    eps = 0.5 * (gradu + gradu.T)
+    V = abs(np.linalg.det(dx)) * 1.0            # w_q = 1 (reference wedge volume)
+    return V * eta * (2.0 * np.sum(eps * eps) - 2.0 / 3.0 * np.trace(gradu) ** 2)
+
+
+def test_element_matrix_equals_one_point_energy():
+    """u^T A_e u = E_e(u) of Eq. (oneptenergy), computed independently by finite differences."""
+    x, eta = random_wedges()
+    _, _, grad, V = geometry(x)
+    A = viscous_element_matrix(grad, V, eta)
+    rng = np.random.default_rng(5)
+    for e in range(x.shape[0]):
+        for _ in range(3):
+            u = rng.normal(size=(6, 3))
+            E = _energy_by_finite_differences(x[e], u, eta[e])
+            assert abs(u.ravel() @ A[e] @ u.ravel() - E) <= 1e-7 * abs(E)
+
+
+def test_element_matrix_rank_and_kernel():
+    """Symmetric; rank 5 (deviatoric strain only); rank 6 without the -2/3 term; kernel holds
+    translations, rotations, the dilatation x and the six hourglass modes (Eq. hourglass)."""
+    x, eta = random_wedges()
+    _, _, grad, V = geometry(x)
+    A = viscous_element_matrix(grad, V, eta)
+    A0 = viscous_element_matrix(grad, V, eta, div_term=False)
+    for e in range(x.shape[0]):
+        scale = np.abs(A[e]).max()
+        np.testing.assert_array_equal(A[e], A[e].T)
+        assert np.linalg.matrix_rank(A[e], tol=1e-10 * scale) == 5
+        assert np.linalg.matrix_rank(A0[e], tol=1e-10 * scale) == 6
+        kernel = []
+        for d in range(3):
+            t = np.zeros((6, 3)); t[:, d] = 1.0
+            kernel.append(t)
+        for om in np.eye(3):
+            kernel.append(np.cross(om[None, :], x[e]))
+        kernel.append(x[e].copy())
+        for w in hourglass_vectors():
+            for d in range(3):
+                v = np.zeros((6, 3)); v[:, d] = w
+                kernel.append(v)
+        K = np.stack([k.ravel() for k in kernel])
+        assert np.linalg.matrix_rank(K) == 13
+        assert np.abs(A[e] @ K.T).max() <= 1e-13 * scale
+    # nodal values of the hourglass modes, Eq. (hourglass)
+    np.testing.assert_allclose(hourglass_vectors()[0], [1 / 3, -2 / 3, 1 / 3, -1 / 3, 2 / 3, -1 / 3], atol=1e-16)
+    np.testing.assert_allclose(hourglass_vectors()[1], [1 / 3, 1 / 3, -2 / 3, -1 / 3, -1 / 3, 2 / 3], atol=1e-16)
+
+
+def test_diagonal_closed_form():
+    """(A_e)_{(j,d),(j,d)} = V eta (|grad N_j|^2 + 1/3 (d_d N_j)^2)."""
+    x, eta = random_wedges()
+    _, _, grad, V = geometry(x)
+    A = viscous_element_matrix(grad, V, eta)
+    for e in range(x.shape[0]):
+        for j in range(6):
+            for d in range(3):
+                g = grad[e, j]
+                want = V[e] * eta[e] * (g @ g + g[d] ** 2 / 3.0)
+                assert abs(A[e, 3 * j + d, 3 * j + d] - want) <= 1e-13 * abs(want)
