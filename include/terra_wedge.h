@@ -1,0 +1,192 @@
+/*
+ * terra_wedge.h -- C ABI of the GB300 (sm_103a) matrix-free wedge Stokes library.
+ *
+ * The library applies the low-order W1-iso-W2 / W1 wedge Stokes operator of
+ * TERRA-NG (arxiv 2609.21633) on a radially extruded icosahedral shell:
+ * the variable-viscosity symmetric-gradient block A (Eq. elemmat, Eq. matfree,
+ * Eq. epsq / Eq. localapply), the divergence B and gradient B^T of the saddle
+ * matrix [[A, B^T], [B, 0]] (Sec. 7, Eq. block-precond), and their diagonals
+ * (Eq. pmass).  The mesh is built as in Sec. 2: ten diamonds of an
+ * icosahedral base grid, recursive normalised-midpoint refinement to
+ * 2^l x 2^l cells per diamond, uniform radial extrusion through N_r node
+ * layers, each hexahedral cell split implicitly into two wedges.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Status: every function returns tn_status; 0 (TN_OK) on success, a negative
+ * code otherwise.  tn_last_error() returns a thread-local message describing
+ * the last failure.  No C++ exception crosses this interface.
+ *
+ * Pointers: arguments named *_dev are DEVICE pointers (cudaMalloc / torch
+ * CUDA tensors) owned by the caller; arguments named *_host are host
+ * pointers.  The library never frees or retains caller pointers beyond the
+ * call (stream-ordered work enqueued by the call reads / writes them later on
+ * that stream).  The library owns the mesh hierarchy, the per-level
+ * viscosity and geometry tables and its workspaces.
+ *
+ * Streams: every operator call is enqueued on the given cudaStream_t
+ * (passed as void*, NULL = legacy default stream) and returns without
+ * synchronising, unless stated otherwise.
+ *
+ * Levels: a mesh holds a hierarchy of nested levels h = 0 (finest, the
+ * created lateral level l and N_r node layers) to depth-1; level h+1 has
+ * lateral level l_h - 1 and (N_r,h - 1)/2 + 1 node layers.  The pressure
+ * space of level h (Sec. 3: W1 on the grid one level coarser) is the node set
+ * of level h+1.
+ *
+ * Node layout (velocity components and scalars) of a level with N = 2^l_h,
+ * N_r node layers and row pitch P = round_up(N + 1, 4):
+ *     index(d, k, i, j) = ((d * N_r + k) * (N + 1) + i) * P + j
+ * d in [0,10) diamond, k in [0,N_r) radial node layer (radius r_k), i, j in
+ * [0, N] lattice position; j >= N+1 are padding (never read, never written).
+ * A velocity field is three such arrays (structure of arrays, one per
+ * Cartesian component x, y, z).  Lattice points on diamond edges exist in
+ * every diamond that shares them (2 copies on edges, 3 at the ten non-polar
+ * icosahedral vertices, 5 at the poles); inputs must hold equal values on all
+ * copies and outputs hold bitwise-equal values on all copies.
+ * Diamond corners (c00, c10, c01, c11) = lattice (0,0), (N,0), (0,N), (N,N):
+ * north d = k: (N, U_k, U_k+1, L_k); south d = 5 + k: (U_k+1, L_k, L_k+1, S),
+ * U_k at latitude +atan(1/2), longitude 72k deg; L_k at -atan(1/2), 36 + 72k deg.
+ * Radii r_k = r_in + ((r_out - r_in) * k) / (N_r - 1).
+ *
+ * Wedge layout (per-wedge viscosity): cell (d, i, j) between node layers k and
+ * k+1 (i, j in [0, N), k in [0, N_r - 1)) holds wedge W0 = lateral
+ * (i,j),(i+1,j),(i,j+1) and W1 = (i+1,j+1),(i,j+1),(i+1,j):
+ *     windex(d, k, i, j, w) = (((d * (N_r - 1) + k) * N + i) * N + j) * 2 + w
+ *
+ * Boundary conditions: at node layers 0 (r_in) and N_r - 1 (r_out) each node
+ * carries a projector P_j = I - s_j s_j^T (free-slip, s_j the unit radial
+ * direction) or P_j = 0 (no-slip); elsewhere P_j = I.  The constrained
+ * velocity block is P A P + (I - P); B acts as B P and B^T as P B^T.
+ */
+#ifndef TERRA_WEDGE_H
+#define TERRA_WEDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tn_status;
+enum {
+  TN_OK = 0,
+  TN_EINVAL = -1,        /* invalid argument (NULL, size, aliasing, level out of range) */
+  TN_ENOMEM = -2,        /* device or host allocation failed */
+  TN_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+  TN_ENOTCONVERGED = -4, /* an iterative solve did not reach its tolerance */
+  TN_ETIMEOUT = -5,      /* a bounded device wait ran out */
+  TN_EBUSY = -6,         /* resource temporarily unavailable (serving admission) */
+  TN_ESTATE = -7         /* call order violated (e.g. apply before set_viscosity) */
+};
+
+typedef enum { TN_F64 = 0, TN_F32 = 1 } tn_prec;
+typedef enum { TN_BC_FREESLIP = 0, TN_BC_NOSLIP = 1 } tn_bc;
+
+typedef struct tn_mesh tn_mesh;
+
+typedef struct {
+  int bc_inner;       /* tn_bc at r_in  (default TN_BC_FREESLIP) */
+  int bc_outer;       /* tn_bc at r_out (default TN_BC_FREESLIP) */
+  int div_term;       /* 1: keep the -2/3 div div term of Eq. elemmat (default); 0: drop it */
+  int max_levels;     /* upper bound on the hierarchy depth (0 = as deep as possible) */
+} tn_mesh_opts;
+
+typedef struct {
+  int lateral_level;  /* l_h */
+  int N;              /* 2^l_h */
+  int n_r;            /* radial node layers */
+  int pitch;          /* row pitch P (elements) */
+  int64_t layer_stride;    /* (N+1) * P */
+  int64_t diamond_stride;  /* N_r * (N+1) * P */
+  int64_t n_layout;        /* 10 * diamond_stride: elements of one scalar / component array */
+  int64_t n_unique_nodes;  /* (10 N^2 + 2) N_r */
+  int64_t n_cells;         /* 10 N^2 (N_r - 1) hexahedral cells */
+  int64_t n_wedges;        /* 2 n_cells: elements of a per-wedge array */
+  int depth;               /* number of levels in the hierarchy */
+  double r_in, r_out;
+} tn_level_info;
+
+/* Thread-local message of the last failure on this thread (never NULL). */
+const char* tn_last_error(void);
+
+/* Build the mesh hierarchy (Sec. 2) on the current CUDA device.
+ * lateral_level >= 1; radial_layers = N_r >= 3 node layers with N_r - 1 even
+ * (the pressure space coarsens radially too, Sec. 3); 0 < r_in < r_out.
+ * opts may be NULL (defaults).  Synchronous; allocates device tables. */
+tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, double r_out,
+                         const tn_mesh_opts* opts, tn_mesh** out);
+tn_status tn_mesh_destroy(tn_mesh* mesh);
+tn_status tn_mesh_info(const tn_mesh* mesh, int level, tn_level_info* info);
+
+/* Unit-sphere lattice points of a level, host copy: xyz_host[3 * ((d*(N+1)+i)*(N+1)+j) + c]
+ * (10 * (N+1)^2 * 3 doubles).  Synchronous. */
+tn_status tn_mesh_lateral_points(const tn_mesh* mesh, int level, double* xyz_host);
+
+/* Canonical copy of every layout node of a level, host copy (n_layout int64):
+ * canon[index(d,k,i,j)] = smallest layout index holding the same physical node;
+ * -1 on padding.  Lets callers build inputs that are equal on all copies. */
+tn_status tn_mesh_canonical_index(const tn_mesh* mesh, int level, int64_t* canon_host);
+
+/* Per-wedge viscosity of level 0 (wedge layout, n_wedges doubles, eta > 0),
+ * one value per wedge evaluated at the quadrature point q_c (Sec. 4).
+ * Copied into the library; coarser levels get the mean of their 8 child
+ * wedges.  Stream-ordered. */
+tn_status tn_set_viscosity(tn_mesh* mesh, const double* eta_wedge_dev, void* stream);
+
+/* Viscosity law of tn_set_temperature: eta_e = (jump_factor if r_mid < jump_r else 1)
+ * * exp(E * (1/2 - T(q_c))) (Frank-Kamenetskii form of Sec. 8, E = ln(viscosity contrast));
+ * T(q_c) = mean of the wedge's six nodal temperatures; r_mid = (r_k + r_k+1)/2. */
+typedef struct {
+  double E;
+  double jump_r;       /* radius of the jump; <= 0 disables it */
+  double jump_factor;
+} tn_visc_law;
+
+/* Per-wedge viscosity of all levels from nodal temperature T_node_dev (node layout of
+ * level 0, doubles).  Stream-ordered. */
+tn_status tn_set_temperature(tn_mesh* mesh, const double* T_node_dev, const tn_visc_law* law, void* stream);
+
+/* Copy the current level-h viscosity (wedge layout, doubles) to eta_dev.  Stream-ordered. */
+tn_status tn_get_viscosity(const tn_mesh* mesh, int level, double* eta_dev, void* stream);
+
+/* y = (P A P + (I - P)) u on level h (Eq. matfree with Eq. elemmat, one-point rule).
+ * u_dev[3], y_dev[3]: node layout of level h, type double (TN_F64) or float (TN_F32);
+ * y must not alias u.  Stream-ordered. */
+tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* const* y_dev,
+                     void* stream);
+
+/* q = B P u: divergence onto the pressure space of level h (node layout of level h+1).
+ * B[k, (j,d)] = -sum_e V_e psi_k(q_c^e) dN_j/dx_d(q_c^e), psi_k the pressure basis
+ * (nested iso-interpolation of the coarse W1 function, Sec. 3).  Stream-ordered. */
+tn_status tn_apply_B(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev, void* stream);
+
+/* y = P B^T p: gradient of a pressure field (node layout of level h+1) onto the velocity
+ * space of level h.  Stream-ordered. */
+tn_status tn_apply_BT(tn_mesh* mesh, int level, tn_prec prec, const void* p_dev, void* const* y_dev, void* stream);
+
+/* d = diag(P A P + (I - P)) on level h (3 arrays, node layout).  Stream-ordered. */
+tn_status tn_diag_A(tn_mesh* mesh, int level, tn_prec prec, void* const* d_dev, void* stream);
+
+/* m = diag(M_{1/eta}) of Eq. (pmass) on the pressure space of level h (node layout of
+ * level h+1): sum_e V_e / eta_e psi_k(q_c^e)^2 over the fine wedges.  Stream-ordered. */
+tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m_dev, void* stream);
+
+/* Nested iso-interpolation between level h+1 (coarse) and level h (fine), ncomp = 1 or 3
+ * arrays: prolongation fine = P coarse, restriction coarse = P^T fine.  With
+ * apply_bc != 0 the velocity boundary projector of the target level is applied to
+ * the result (multigrid transfers of the constrained space).  Stream-ordered. */
+tn_status tn_prolong(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int apply_bc,
+                     const void* const* coarse_dev, void* const* fine_dev, void* stream);
+tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int apply_bc,
+                      const void* const* fine_dev, void* const* coarse_dev, void* stream);
+
+/* Boussinesq buoyancy right-hand side f = P sum_e V_e Ra T(q_c) r_hat(q_c) N_j(q_c) on level 0
+ * (Eq. stokes with the full temperature); f_dev[3] doubles.  Stream-ordered. */
+tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double* const* f_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TERRA_WEDGE_H */

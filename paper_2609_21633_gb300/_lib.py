@@ -1,0 +1,205 @@
+"""ctypes binding of ``include/terra_wedge.h`` (argument marshalling only).
+
+Every function here has the C name of the entry point it calls.  Device
+buffers are torch CUDA tensors (torch provides device memory and streams); the
+work itself runs in the library's sm_103a kernels.  The shared library must be
+built in-tree (``__graft_entry__.build()``); loading fails loudly otherwise --
+there is no CPU fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libterra_wedge.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "terra_wedge.h")
+
+TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOTCONVERGED, TN_ETIMEOUT, TN_EBUSY, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+TN_F64, TN_F32 = 0, 1
+TN_BC_FREESLIP, TN_BC_NOSLIP = 0, 1
+
+
+class TnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+class tn_mesh_opts(ctypes.Structure):
+    _fields_ = [("bc_inner", ctypes.c_int), ("bc_outer", ctypes.c_int), ("div_term", ctypes.c_int),
+                ("max_levels", ctypes.c_int)]
+
+
+class tn_level_info(ctypes.Structure):
+    _fields_ = [("lateral_level", ctypes.c_int), ("N", ctypes.c_int), ("n_r", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("layer_stride", ctypes.c_int64), ("diamond_stride", ctypes.c_int64), ("n_layout", ctypes.c_int64),
+                ("n_unique_nodes", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("n_wedges", ctypes.c_int64),
+                ("depth", ctypes.c_int), ("r_in", ctypes.c_double), ("r_out", ctypes.c_double)]
+
+
+class tn_visc_law(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("jump_r", ctypes.c_double), ("jump_factor", ctypes.c_double)]
+
+
+_lib = None
+P = ctypes.c_void_p
+PP = ctypes.POINTER(ctypes.c_void_p)
+_SIGS = {
+    "tn_last_error": ([], ctypes.c_char_p),
+    "tn_mesh_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                        ctypes.POINTER(tn_mesh_opts), ctypes.POINTER(P)], ctypes.c_int),
+    "tn_mesh_destroy": ([P], ctypes.c_int),
+    "tn_mesh_info": ([P, ctypes.c_int, ctypes.POINTER(tn_level_info)], ctypes.c_int),
+    "tn_mesh_lateral_points": ([P, ctypes.c_int, P], ctypes.c_int),
+    "tn_mesh_canonical_index": ([P, ctypes.c_int, P], ctypes.c_int),
+    "tn_set_viscosity": ([P, P, P], ctypes.c_int),
+    "tn_set_temperature": ([P, P, ctypes.POINTER(tn_visc_law), P], ctypes.c_int),
+    "tn_get_viscosity": ([P, ctypes.c_int, P, P], ctypes.c_int),
+    "tn_apply_A": ([P, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
+    "tn_apply_B": ([P, ctypes.c_int, ctypes.c_int, PP, P, P], ctypes.c_int),
+    "tn_apply_BT": ([P, ctypes.c_int, ctypes.c_int, P, PP, P], ctypes.c_int),
+    "tn_diag_A": ([P, ctypes.c_int, ctypes.c_int, PP, P], ctypes.c_int),
+    "tn_diag_pmass": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
+    "tn_prolong": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
+    "tn_restrict": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
+    "tn_buoyancy": ([P, P, ctypes.c_double, PP, P], ctypes.c_int),
+}
+
+
+def lib():
+    """Load the in-tree shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not found: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes, fn.restype = args, res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != TN_OK:
+        raise TnError(status, lib().tn_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _ptrs(ts):
+    arr = (ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+    return ctypes.cast(arr, PP), arr
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _prec(dtype):
+    import torch
+    if dtype == torch.float64:
+        return TN_F64
+    if dtype == torch.float32:
+        return TN_F32
+    raise TypeError(f"unsupported dtype {dtype}")
+
+
+def tn_mesh_create(lateral_level, radial_layers, r_in, r_out, bc_inner=TN_BC_FREESLIP, bc_outer=TN_BC_FREESLIP,
+                   div_term=True, max_levels=0):
+    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels)
+    out = P()
+    _check(lib().tn_mesh_create(lateral_level, radial_layers, r_in, r_out, ctypes.byref(opts), ctypes.byref(out)))
+    return out
+
+
+def tn_mesh_destroy(mesh):
+    _check(lib().tn_mesh_destroy(mesh))
+
+
+def tn_mesh_info(mesh, level=0):
+    info = tn_level_info()
+    _check(lib().tn_mesh_info(mesh, level, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in tn_level_info._fields_}
+
+
+def tn_mesh_lateral_points(mesh, level=0):
+    import numpy as np
+    N = tn_mesh_info(mesh, level)["N"]
+    out = np.empty((10, N + 1, N + 1, 3), dtype=np.float64)
+    _check(lib().tn_mesh_lateral_points(mesh, level, out.ctypes.data_as(P)))
+    return out
+
+
+def tn_mesh_canonical_index(mesh, level=0):
+    import numpy as np
+    n = tn_mesh_info(mesh, level)["n_layout"]
+    out = np.empty(n, dtype=np.int64)
+    _check(lib().tn_mesh_canonical_index(mesh, level, out.ctypes.data_as(P)))
+    return out
+
+
+def tn_set_viscosity(mesh, eta, stream=None):
+    _check(lib().tn_set_viscosity(mesh, _ptr(eta), _stream(stream)))
+
+
+def tn_set_temperature(mesh, T, E, jump_r=0.0, jump_factor=1.0, stream=None):
+    law = tn_visc_law(E, jump_r, jump_factor)
+    _check(lib().tn_set_temperature(mesh, _ptr(T), ctypes.byref(law), _stream(stream)))
+
+
+def tn_get_viscosity(mesh, level, eta_out, stream=None):
+    _check(lib().tn_get_viscosity(mesh, level, _ptr(eta_out), _stream(stream)))
+
+
+def tn_apply_A(mesh, level, u, y, stream=None):
+    pu, _a = _ptrs(u)
+    py, _b = _ptrs(y)
+    _check(lib().tn_apply_A(mesh, level, _prec(u[0].dtype), pu, py, _stream(stream)))
+
+
+def tn_apply_B(mesh, level, u, q, stream=None):
+    pu, _a = _ptrs(u)
+    _check(lib().tn_apply_B(mesh, level, _prec(u[0].dtype), pu, _ptr(q), _stream(stream)))
+
+
+def tn_apply_BT(mesh, level, p, y, stream=None):
+    py, _b = _ptrs(y)
+    _check(lib().tn_apply_BT(mesh, level, _prec(p.dtype), _ptr(p), py, _stream(stream)))
+
+
+def tn_diag_A(mesh, level, d, stream=None):
+    pd, _a = _ptrs(d)
+    _check(lib().tn_diag_A(mesh, level, _prec(d[0].dtype), pd, _stream(stream)))
+
+
+def tn_diag_pmass(mesh, level, m, stream=None):
+    _check(lib().tn_diag_pmass(mesh, level, _prec(m.dtype), _ptr(m), _stream(stream)))
+
+
+def tn_prolong(mesh, level, coarse, fine, apply_bc=False, stream=None):
+    pc, _a = _ptrs(coarse)
+    pf, _b = _ptrs(fine)
+    _check(lib().tn_prolong(mesh, level, _prec(coarse[0].dtype), len(coarse), int(apply_bc), pc, pf, _stream(stream)))
+
+
+def tn_restrict(mesh, level, fine, coarse, apply_bc=False, stream=None):
+    pf, _a = _ptrs(fine)
+    pc, _b = _ptrs(coarse)
+    _check(lib().tn_restrict(mesh, level, _prec(fine[0].dtype), len(fine), int(apply_bc), pf, pc, _stream(stream)))
+
+
+def tn_buoyancy(mesh, T, Ra, f, stream=None):
+    pf, _a = _ptrs(f)
+    _check(lib().tn_buoyancy(mesh, _ptr(T), Ra, pf, _stream(stream)))
+
+
+def header_entry_points():
+    """Names of the functions declared in include/terra_wedge.h."""
+    import re
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:tn_status|const char\*)\s+(tn_\w+)\s*\(", src, flags=re.M)))

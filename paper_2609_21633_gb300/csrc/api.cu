@@ -1,0 +1,381 @@
+// C ABI of the wedge Stokes library: argument checks, mesh hierarchy lifetime, dispatch.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace tn {
+
+namespace {
+thread_local std::string g_err = "no error";
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+tn_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return TN_ECUDA;
+}
+
+tn_status inval(const std::string& msg) {
+  set_error(msg);
+  return TN_EINVAL;
+}
+
+template <typename T>
+cudaError_t upload(T*& dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc((void**)&dst, sizeof(T) * (src.empty() ? 1 : src.size()));
+  if (e != cudaSuccess) return e;
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+std::vector<float> to_f32(const std::vector<T>& v) {
+  std::vector<float> out(v.size());
+  for (size_t i = 0; i < v.size(); ++i) out[i] = (float)v[i];
+  return out;
+}
+
+void free_level(Level& L) {
+  void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off,
+                  L.grp_s64, L.grp_s32, L.owned, L.eta64, L.eta32, L.scr64, L.scr32};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  L = Level();
+}
+
+cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+bool level_ok(const tn_mesh* m, int level) { return m && level >= 0 && level < (int)m->lv.size(); }
+
+BC bc_of(const tn_mesh* m) { return BC{m->bc_in, m->bc_out}; }
+
+template <typename T>
+cudaError_t apply_B_t(tn_mesh* m, int level, const void* const* u, void* q, cudaStream_t st) {
+  const Level& F = m->lv[level];
+  const Level& C = m->lv[level + 1];
+  T* scr = sizeof(T) == 8 ? (T*)F.scr64 : (T*)F.scr32;
+  cudaError_t e = launch_div_fine<T>(F, bc_of(m), (const T* const*)u, scr, st);
+  if (e != cudaSuccess) return e;
+  const T* fin[1] = {scr};
+  T* cout[1] = {(T*)q};
+  return launch_restrict<T>(F, C, bc_of(m), 1, 0, fin, cout, st);
+}
+
+template <typename T>
+cudaError_t apply_BT_t(tn_mesh* m, int level, const void* p, void* const* y, cudaStream_t st) {
+  const Level& F = m->lv[level];
+  const Level& C = m->lv[level + 1];
+  T* scr = sizeof(T) == 8 ? (T*)F.scr64 : (T*)F.scr32;
+  const T* cin[1] = {(const T*)p};
+  T* fout[1] = {scr};
+  cudaError_t e = launch_prolong<T>(F, C, bc_of(m), 1, 0, cin, fout, st);
+  if (e != cudaSuccess) return e;
+  return launch_grad_fine<T>(F, bc_of(m), scr, (T* const*)y, st);
+}
+
+
+}  // namespace
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+const char* tn_last_error(void) { return g_err.c_str(); }
+
+tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, double r_out, const tn_mesh_opts* opts,
+                         tn_mesh** out) {
+  if (!out) return inval("tn_mesh_create: out is NULL");
+  *out = nullptr;
+  if (lateral_level < 1 || lateral_level > 12) return inval("tn_mesh_create: lateral_level must be in [1, 12]");
+  if (radial_layers < 3 || (radial_layers - 1) % 2 != 0)
+    return inval("tn_mesh_create: radial_layers must be >= 3 with radial_layers - 1 even");
+  if (!(r_in > 0.0) || !(r_out > r_in)) return inval("tn_mesh_create: need 0 < r_in < r_out");
+  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0};
+  if (opts) o = *opts;
+  if ((o.bc_inner != TN_BC_FREESLIP && o.bc_inner != TN_BC_NOSLIP) ||
+      (o.bc_outer != TN_BC_FREESLIP && o.bc_outer != TN_BC_NOSLIP))
+    return inval("tn_mesh_create: unknown boundary condition");
+  tn_mesh* m = new (std::nothrow) tn_mesh();
+  if (!m) {
+    set_error("tn_mesh_create: host allocation failed");
+    return TN_ENOMEM;
+  }
+  m->bc_in = o.bc_inner;
+  m->bc_out = o.bc_outer;
+  m->div_term = o.div_term ? 1 : 0;
+  m->r_in = r_in;
+  m->r_out = r_out;
+  cudaGetDevice(&m->device);
+  int l = lateral_level, nr = radial_layers;
+  while (true) {
+    m->lv.emplace_back();
+    Level& L = m->lv.back();
+    std::vector<double> geo, lay, s, grp_s;
+    std::vector<int> gptr;
+    std::vector<int64_t> goff;
+    std::vector<uint8_t> owned;
+    std::string err;
+    build_level_host(L, l, nr, r_in, r_out, geo, lay, s, gptr, goff, grp_s, owned, err);
+    if (!err.empty()) {
+      tn_mesh_destroy(m);
+      return inval("tn_mesh_create: " + err);
+    }
+    L.h_grp_ptr = gptr;
+    L.h_grp_off = goff;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) {
+      if (e == cudaSuccess) e = x;
+    };
+    chk(upload(L.geo64, geo));
+    chk(upload(L.geo32, to_f32(geo)));
+    chk(upload(L.lay64, lay));
+    chk(upload(L.lay32, to_f32(lay)));
+    chk(upload(L.s64, s));
+    chk(upload(L.s32, to_f32(s)));
+    chk(upload(L.grp_ptr, gptr));
+    chk(upload(L.grp_off, goff));
+    chk(upload(L.grp_s64, grp_s));
+    chk(upload(L.grp_s32, to_f32(grp_s)));
+    chk(upload(L.owned, owned));
+    chk(cudaMalloc((void**)&L.eta64, sizeof(double) * L.n_wedges));
+    chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
+    chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
+    chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));
+    if (e != cudaSuccess) {
+      tn_mesh_destroy(m);
+      set_error(std::string("tn_mesh_create: device allocation failed: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+    }
+    const bool can_coarsen = l >= 2 && (nr - 1) % 2 == 0 && nr >= 3;
+    if (!can_coarsen || (o.max_levels > 0 && (int)m->lv.size() >= o.max_levels)) break;
+    l -= 1;
+    nr = (nr - 1) / 2 + 1;
+  }
+  *out = m;
+  return TN_OK;
+}
+
+tn_status tn_mesh_destroy(tn_mesh* mesh) {
+  if (!mesh) return TN_OK;
+  for (auto& L : mesh->lv) free_level(L);
+  delete mesh;
+  return TN_OK;
+}
+
+tn_status tn_mesh_info(const tn_mesh* mesh, int level, tn_level_info* info) {
+  if (!level_ok(mesh, level) || !info) return inval("tn_mesh_info: bad mesh, level or info");
+  const Level& L = mesh->lv[level];
+  info->lateral_level = L.l;
+  info->N = L.N;
+  info->n_r = L.n_r;
+  info->pitch = L.P;
+  info->layer_stride = L.layer_stride;
+  info->diamond_stride = L.diamond_stride;
+  info->n_layout = L.n_layout;
+  info->n_unique_nodes = ((int64_t)10 * L.N * L.N + 2) * L.n_r;
+  info->n_cells = (int64_t)10 * L.N * L.N * (L.n_r - 1);
+  info->n_wedges = L.n_wedges;
+  info->depth = (int)mesh->lv.size();
+  info->r_in = mesh->r_in;
+  info->r_out = mesh->r_out;
+  return TN_OK;
+}
+
+tn_status tn_mesh_lateral_points(const tn_mesh* mesh, int level, double* xyz_host) {
+  if (!level_ok(mesh, level) || !xyz_host) return inval("tn_mesh_lateral_points: bad arguments");
+  const Level& L = mesh->lv[level];
+  std::memcpy(xyz_host, L.lat_xyz.data(), sizeof(double) * L.lat_xyz.size());
+  return TN_OK;
+}
+
+tn_status tn_mesh_canonical_index(const tn_mesh* mesh, int level, int64_t* canon) {
+  if (!level_ok(mesh, level) || !canon) return inval("tn_mesh_canonical_index: bad arguments");
+  const Level& L = mesh->lv[level];
+  for (int64_t i = 0; i < L.n_layout; ++i) canon[i] = -1;
+  for (int d = 0; d < 10; ++d)
+    for (int k = 0; k < L.n_r; ++k)
+      for (int i = 0; i <= L.N; ++i)
+        for (int j = 0; j <= L.N; ++j) {
+          int64_t idx = d * L.diamond_stride + k * L.layer_stride + (int64_t)i * L.P + j;
+          canon[idx] = idx;
+        }
+  for (size_t g = 0; g + 1 < L.h_grp_ptr.size(); ++g) {
+    int64_t first = L.h_grp_off[L.h_grp_ptr[g]];
+    for (int q = L.h_grp_ptr[g]; q < L.h_grp_ptr[g + 1]; ++q)
+      for (int k = 0; k < L.n_r; ++k) canon[L.h_grp_off[q] + k * L.layer_stride] = first + k * L.layer_stride;
+  }
+  return TN_OK;
+}
+
+static tn_status finish_eta(tn_mesh* m, cudaStream_t st) {
+  for (size_t h = 0; h < m->lv.size(); ++h) {
+    if (h > 0) {
+      cudaError_t e = launch_eta_coarsen(m->lv[h - 1], m->lv[h], m->lv[h - 1].eta64, m->lv[h].eta64, st);
+      if (e != cudaSuccess) return cuda_fail(e, "viscosity coarsening");
+    }
+    cudaError_t e = launch_to_f32(m->lv[h].eta64, m->lv[h].eta32, m->lv[h].n_wedges, st);
+    if (e != cudaSuccess) return cuda_fail(e, "viscosity conversion");
+  }
+  m->eta_set = true;
+  return TN_OK;
+}
+
+tn_status tn_set_viscosity(tn_mesh* mesh, const double* eta_dev, void* stream) {
+  if (!mesh || !eta_dev) return inval("tn_set_viscosity: NULL argument");
+  Level& L = mesh->lv[0];
+  cudaError_t e = cudaMemcpyAsync(L.eta64, eta_dev, sizeof(double) * L.n_wedges, cudaMemcpyDeviceToDevice, S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "tn_set_viscosity");
+  return finish_eta(mesh, S(stream));
+}
+
+tn_status tn_set_temperature(tn_mesh* mesh, const double* T_dev, const tn_visc_law* law, void* stream) {
+  if (!mesh || !T_dev || !law) return inval("tn_set_temperature: NULL argument");
+  Level& L = mesh->lv[0];
+  cudaError_t e = launch_eta_from_T(L, T_dev, law->E, law->jump_r, law->jump_factor, L.eta64, S(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "tn_set_temperature");
+  return finish_eta(mesh, S(stream));
+}
+
+tn_status tn_get_viscosity(const tn_mesh* mesh, int level, double* eta_dev, void* stream) {
+  if (!level_ok(mesh, level) || !eta_dev) return inval("tn_get_viscosity: bad arguments");
+  const Level& L = mesh->lv[level];
+  cudaError_t e = cudaMemcpyAsync(eta_dev, L.eta64, sizeof(double) * L.n_wedges, cudaMemcpyDeviceToDevice, S(stream));
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_get_viscosity");
+}
+
+static tn_status check_vecs(const char* who, const void* const* a, int na, const void* const* b, int nb) {
+  if (!a || !b) return inval(std::string(who) + ": NULL vector array");
+  for (int i = 0; i < na; ++i)
+    if (!a[i]) return inval(std::string(who) + ": NULL input vector");
+  for (int i = 0; i < nb; ++i)
+    if (!b[i]) return inval(std::string(who) + ": NULL output vector");
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      if (a[i] == b[j]) return inval(std::string(who) + ": output aliases input");
+  for (int i = 0; i < nb; ++i)
+    for (int j = i + 1; j < nb; ++j)
+      if (b[i] == b[j]) return inval(std::string(who) + ": output components alias each other");
+  return TN_OK;
+}
+
+tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* u, void* const* y, void* stream) {
+  if (!level_ok(mesh, level)) return inval("tn_apply_A: bad mesh or level");
+  if (!mesh->eta_set) {
+    set_error("tn_apply_A: viscosity not set");
+    return TN_ESTATE;
+  }
+  tn_status s = check_vecs("tn_apply_A", u, 3, (const void* const*)y, 3);
+  if (s) return s;
+  const Level& L = mesh->lv[level];
+  cudaError_t e;
+  if (prec == TN_F64)
+    e = launch_apply_A<double>(L, bc_of(mesh), mesh->div_term, (const double* const*)u, (double* const*)y, S(stream));
+  else if (prec == TN_F32)
+    e = launch_apply_A<float>(L, bc_of(mesh), mesh->div_term, (const float* const*)u, (float* const*)y, S(stream));
+  else
+    return inval("tn_apply_A: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_apply_A");
+}
+
+tn_status tn_apply_B(tn_mesh* mesh, int level, tn_prec prec, const void* const* u, void* q, void* stream) {
+  if (!level_ok(mesh, level) || level + 1 >= (int)mesh->lv.size()) return inval("tn_apply_B: bad mesh or level");
+  void* qa[1] = {q};
+  tn_status s = check_vecs("tn_apply_B", u, 3, (const void* const*)qa, 1);
+  if (s) return s;
+  cudaError_t e;
+  if (prec == TN_F64) e = apply_B_t<double>(mesh, level, u, q, S(stream));
+  else if (prec == TN_F32) e = apply_B_t<float>(mesh, level, u, q, S(stream));
+  else return inval("tn_apply_B: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_apply_B");
+}
+
+tn_status tn_apply_BT(tn_mesh* mesh, int level, tn_prec prec, const void* p, void* const* y, void* stream) {
+  if (!level_ok(mesh, level) || level + 1 >= (int)mesh->lv.size()) return inval("tn_apply_BT: bad mesh or level");
+  const void* pa[1] = {p};
+  tn_status s = check_vecs("tn_apply_BT", pa, 1, (const void* const*)y, 3);
+  if (s) return s;
+  cudaError_t e;
+  if (prec == TN_F64) e = apply_BT_t<double>(mesh, level, p, y, S(stream));
+  else if (prec == TN_F32) e = apply_BT_t<float>(mesh, level, p, y, S(stream));
+  else return inval("tn_apply_BT: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_apply_BT");
+}
+
+tn_status tn_diag_A(tn_mesh* mesh, int level, tn_prec prec, void* const* d, void* stream) {
+  if (!level_ok(mesh, level)) return inval("tn_diag_A: bad mesh or level");
+  if (!mesh->eta_set) {
+    set_error("tn_diag_A: viscosity not set");
+    return TN_ESTATE;
+  }
+  const void* none[1] = {nullptr};
+  if (!d || !d[0] || !d[1] || !d[2] || d[0] == d[1] || d[0] == d[2] || d[1] == d[2])
+    return inval("tn_diag_A: bad output vectors");
+  (void)none;
+  const Level& L = mesh->lv[level];
+  cudaError_t e;
+  if (prec == TN_F64) e = launch_diag_A<double>(L, bc_of(mesh), mesh->div_term, (double* const*)d, S(stream));
+  else if (prec == TN_F32) e = launch_diag_A<float>(L, bc_of(mesh), mesh->div_term, (float* const*)d, S(stream));
+  else return inval("tn_diag_A: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_diag_A");
+}
+
+tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m, void* stream) {
+  if (!level_ok(mesh, level) || level + 1 >= (int)mesh->lv.size() || !m) return inval("tn_diag_pmass: bad arguments");
+  if (!mesh->eta_set) {
+    set_error("tn_diag_pmass: viscosity not set");
+    return TN_ESTATE;
+  }
+  cudaError_t e;
+  if (prec == TN_F64) e = launch_diag_pmass<double>(mesh->lv[level], mesh->lv[level + 1], (double*)m, S(stream));
+  else if (prec == TN_F32) e = launch_diag_pmass<float>(mesh->lv[level], mesh->lv[level + 1], (float*)m, S(stream));
+  else return inval("tn_diag_pmass: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_diag_pmass");
+}
+
+tn_status tn_prolong(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int apply_bc, const void* const* c,
+                     void* const* f, void* stream) {
+  if (!level_ok(mesh, level) || level + 1 >= (int)mesh->lv.size()) return inval("tn_prolong: bad mesh or level");
+  if (ncomp != 1 && ncomp != 3) return inval("tn_prolong: ncomp must be 1 or 3");
+  tn_status s = check_vecs("tn_prolong", c, ncomp, (const void* const*)f, ncomp);
+  if (s) return s;
+  const Level& F = mesh->lv[level];
+  const Level& C = mesh->lv[level + 1];
+  cudaError_t e;
+  if (prec == TN_F64)
+    e = launch_prolong<double>(F, C, bc_of(mesh), ncomp, apply_bc, (const double* const*)c, (double* const*)f, S(stream));
+  else if (prec == TN_F32)
+    e = launch_prolong<float>(F, C, bc_of(mesh), ncomp, apply_bc, (const float* const*)c, (float* const*)f, S(stream));
+  else return inval("tn_prolong: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_prolong");
+}
+
+tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int apply_bc, const void* const* f,
+                      void* const* c, void* stream) {
+  if (!level_ok(mesh, level) || level + 1 >= (int)mesh->lv.size()) return inval("tn_restrict: bad mesh or level");
+  if (ncomp != 1 && ncomp != 3) return inval("tn_restrict: ncomp must be 1 or 3");
+  tn_status s = check_vecs("tn_restrict", f, ncomp, (const void* const*)c, ncomp);
+  if (s) return s;
+  const Level& F = mesh->lv[level];
+  const Level& C = mesh->lv[level + 1];
+  cudaError_t e;
+  if (prec == TN_F64)
+    e = launch_restrict<double>(F, C, bc_of(mesh), ncomp, apply_bc, (const double* const*)f, (double* const*)c, S(stream));
+  else if (prec == TN_F32)
+    e = launch_restrict<float>(F, C, bc_of(mesh), ncomp, apply_bc, (const float* const*)f, (float* const*)c, S(stream));
+  else return inval("tn_restrict: unknown precision");
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_restrict");
+}
+
+tn_status tn_buoyancy(tn_mesh* mesh, const double* T_dev, double Ra, double* const* f, void* stream) {
+  if (!mesh || !T_dev || !f || !f[0] || !f[1] || !f[2]) return inval("tn_buoyancy: NULL argument");
+  cudaError_t e = launch_buoyancy(mesh->lv[0], bc_of(mesh), T_dev, Ra, f, S(stream));
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_buoyancy");
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal definitions shared by the host mesh code, the kernels and the C ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/terra_wedge.h"
+
+namespace tn {
+
+// Per-level mesh data.  Host vectors hold the definition; device pointers are
+// owned by the level and freed by tn_mesh_destroy.
+struct Level {
+  int l = 0, N = 0, n_r = 0, P = 0;  // lateral level, 2^l, node layers, row pitch
+  int64_t layer_stride = 0, diamond_stride = 0, n_layout = 0;
+  int64_t n_tri = 0, n_wedges = 0, n_lat_layout = 0;  // 10 N^2 2, n_tri (n_r-1), 10 (N+1) P
+
+  std::vector<double> lat_xyz;  // (10, N+1, N+1, 3)
+  std::vector<double> radii;    // n_r
+
+  // Geometry per lateral triangle t = ((d N + i) N + j) 2 + w, SoA over q:
+  // q = 0..8: M^{-1}[m][x] (row-major), q = 9: |det M|, M = [s1 - s0, s2 - s0, (s0+s1+s2)/3].
+  double* geo64 = nullptr;
+  float* geo32 = nullptr;
+  // Per radial cell k: (1/(2 rho), 1/(6 h), rho^2 h, rho), rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
+  double* lay64 = nullptr;
+  float* lay32 = nullptr;
+  // Lateral unit vectors s, SoA [3][10 (N+1) P] in lateral layout (d (N+1) + i) P + j.
+  double* s64 = nullptr;
+  float* s32 = nullptr;
+  // Interface groups: lattice points shared by several diamonds.
+  int n_groups = 0;
+  int* grp_ptr = nullptr;       // n_groups + 1
+  int64_t* grp_off = nullptr;   // copy offsets d * diamond_stride + i * P + j, ascending per group
+  double* grp_s64 = nullptr;    // [3][n_groups] unit vector of the group's point
+  float* grp_s32 = nullptr;
+  uint8_t* owned = nullptr;     // [10 (N+1) P] 1 if this copy is the canonical one (or not shared)
+  std::vector<int> h_grp_ptr;
+  std::vector<int64_t> h_grp_off;
+  // Viscosity per wedge (wedge layout).
+  double* eta64 = nullptr;
+  float* eta32 = nullptr;
+  // Scratch scalar field in this level's node layout (B / B^T intermediate).
+  double* scr64 = nullptr;
+  float* scr32 = nullptr;
+};
+
+}  // namespace tn
+
+struct tn_mesh {
+  std::vector<tn::Level> lv;
+  int bc_in = TN_BC_FREESLIP, bc_out = TN_BC_FREESLIP, div_term = 1;
+  bool eta_set = false;
+  int device = 0;
+  double r_in = 0, r_out = 0;
+};
+
+namespace tn {
+
+// Host mesh construction (mesh.cpp).
+void build_lateral_points(int level, std::vector<double>& pts);
+void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, std::vector<double>& geo,
+                      std::vector<double>& lay, std::vector<double>& s, std::vector<int>& grp_ptr,
+                      std::vector<int64_t>& grp_off, std::vector<double>& grp_s, std::vector<uint8_t>& owned,
+                      std::string& err);
+
+void set_error(const std::string& msg);
+
+// ---- kernel launchers (kernels.cu) --------------------------------------------------------
+struct BC {
+  int in, out;  // TN_BC_* at node layer 0 and n_r - 1
+};
+template <typename T>
+cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st);
+template <typename T>
+cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st);
+template <typename T>
+cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cudaStream_t st);
+template <typename T>
+cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st);
+// Interface sum over shared copies; mode 0: plain sum; 1: + (I - P) u at boundary layers;
+// 2: + diag(I - P) at boundary layers.
+template <typename T>
+cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* const* y, const T* const* u,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* c,
+                           T* const* f, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* f,
+                            T* const* c, cudaStream_t st);
+cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double jump_r, double jump_f, double* eta,
+                              cudaStream_t st);
+cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st);
+cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);
+
+}  // namespace tn

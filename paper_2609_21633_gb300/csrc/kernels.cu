@@ -1,0 +1,836 @@
+// sm_103a kernels of the matrix-free wedge Stokes operator.
+//
+// Element-level work follows Eq. (epsq) / Eq. (localapply) with one quadrature
+// point at the wedge barycentre q_c (Sec. 4): the strain of the gathered
+// element DoFs is formed at q_c, contracted into the stress, and the stress is
+// contracted with every test gradient -- the 18 x 18 element matrix is never
+// formed (Sec. 6).  Geometry is factorised: at q_c the isoparametric Jacobian
+// of a wedge between radii r_k and r_k+1 over lateral unit vectors s0, s1, s2
+// is J = M diag(rho, rho, h), M = [s1 - s0, s2 - s0, (s0 + s1 + s2)/3],
+// rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2, so a lateral table of M^{-1}
+// and |det M| plus a per-layer table of (1/(2 rho), 1/(6 h), rho^2 h) carry
+// all of it ("radial coordinate compression").  With g'_j the reference
+// gradients scaled to entries in {-1, 0, 1}:
+//     grad u  = sum_m a_m W_m M^{-1}[m, :],   a_m = sum_j u_j g'_j[m]
+//     y_j     = sum_m g'_j[m] H[:, m],        H[:, m] = W_m S M^{-1}[m, :]^T
+// with W = (1/(2 rho), 1/(2 rho), 1/(6 h)) and S = V eta (grad u + grad u^T
+// - 2/3 tr(grad u) I) the stress of Eq. (stress) times V = rho^2 h |det M|.
+//
+// The element-to-node scatter is deterministic and atomic-free: a CTA owns a
+// tile of lateral node columns, computes every cell that touches it (one
+// halo cell row / column), and streams the radial direction, carrying each
+// cell's top-face contributions in registers to the next layer.  Lateral
+// contributions of the four cells around a node are exchanged through shared
+// memory and summed in a fixed order.  Nodes on diamond edges receive a
+// partial sum per diamond; launch_interface adds the copies in ascending
+// layout order and writes the total to every copy (the on-device stand-in
+// for the paper's additive halo exchange, Sec. 2).
+#include <cstdio>
+
+#include "internal.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
+
+template <typename T>
+struct Tab;  // precision-selected views of a level's tables
+template <>
+struct Tab<double> {
+  static const double* geo(const Level& L) { return L.geo64; }
+  static const double* lay(const Level& L) { return L.lay64; }
+  static const double* s(const Level& L) { return L.s64; }
+  static const double* gs(const Level& L) { return L.grp_s64; }
+  static const double* eta(const Level& L) { return L.eta64; }
+};
+template <>
+struct Tab<float> {
+  static const float* geo(const Level& L) { return L.geo32; }
+  static const float* lay(const Level& L) { return L.lay32; }
+  static const float* s(const Level& L) { return L.s32; }
+  static const float* gs(const Level& L) { return L.grp_s32; }
+  static const float* eta(const Level& L) { return L.eta32; }
+};
+
+struct Dims {
+  int N, n_r, P;
+  int64_t layer_stride, diamond_stride, n_tri, n_lat_layout;
+};
+Dims dims(const Level& L) {
+  return Dims{L.N, L.n_r, L.P, L.layer_stride, L.diamond_stride, L.n_tri, L.n_lat_layout};
+}
+
+// ------------------------------------------------------------------------------------ element ops
+// Viscous block: Eq. (epsq) then Eq. (localapply) at q_c.
+template <typename T>
+struct OpA {
+  static constexpr int NIN = 3, NOUT = 3;
+  int div_term;
+  __device__ __forceinline__ void operator()(const T (&u)[6][NIN], const T* Mi, T w0, T w1, T V, T eta,
+                                             T (&y)[6][NOUT]) const {
+    T G[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T ax = (u[1][c] - u[0][c]) + (u[4][c] - u[3][c]);
+      T ay = (u[2][c] - u[0][c]) + (u[5][c] - u[3][c]);
+      T az = (u[3][c] + u[4][c] + u[5][c]) - (u[0][c] + u[1][c] + u[2][c]);
+      ax *= w0, ay *= w0, az *= w1;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) G[c][x] = ax * Mi[x] + ay * Mi[3 + x] + az * Mi[6 + x];
+    }
+    T ve = V * eta;
+    T t = div_term ? (T)(2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]) : (T)0;
+    T S[3][3];
+    S[0][0] = ve * ((G[0][0] + G[0][0]) - t);
+    S[1][1] = ve * ((G[1][1] + G[1][1]) - t);
+    S[2][2] = ve * ((G[2][2] + G[2][2]) - t);
+    S[0][1] = S[1][0] = ve * (G[0][1] + G[1][0]);
+    S[0][2] = S[2][0] = ve * (G[0][2] + G[2][0]);
+    S[1][2] = S[2][1] = ve * (G[1][2] + G[2][1]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T h0 = w0 * (S[c][0] * Mi[0] + S[c][1] * Mi[1] + S[c][2] * Mi[2]);
+      T h1 = w0 * (S[c][0] * Mi[3] + S[c][1] * Mi[4] + S[c][2] * Mi[5]);
+      T h2 = w1 * (S[c][0] * Mi[6] + S[c][1] * Mi[7] + S[c][2] * Mi[8]);
+      T s = h0 + h1;
+      y[0][c] = -s - h2;
+      y[1][c] = h0 - h2;
+      y[2][c] = h1 - h2;
+      y[3][c] = h2 - s;
+      y[4][c] = h0 + h2;
+      y[5][c] = h1 + h2;
+    }
+  }
+};
+
+// Fine-level divergence: each of the six nodes gets -V tr(grad u)(q_c) / 6
+// (pressure test function psi = N_n with N_n(q_c) = 1/6).
+template <typename T>
+struct OpDiv {
+  static constexpr int NIN = 3, NOUT = 1;
+  __device__ __forceinline__ void operator()(const T (&u)[6][NIN], const T* Mi, T w0, T w1, T V, T,
+                                             T (&y)[6][NOUT]) const {
+    T tr = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T ax = (u[1][c] - u[0][c]) + (u[4][c] - u[3][c]);
+      T ay = (u[2][c] - u[0][c]) + (u[5][c] - u[3][c]);
+      T az = (u[3][c] + u[4][c] + u[5][c]) - (u[0][c] + u[1][c] + u[2][c]);
+      tr += (ax * w0) * Mi[c] + (ay * w0) * Mi[3 + c] + (az * w1) * Mi[6 + c];
+    }
+    T v = -V * tr * (T)(1.0 / 6.0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) y[j][0] = v;
+  }
+};
+
+// Fine-level gradient (transpose of OpDiv): y_j += -V p(q_c) grad N_j(q_c), p(q_c) = mean of 6.
+template <typename T>
+struct OpGrad {
+  static constexpr int NIN = 1, NOUT = 3;
+  __device__ __forceinline__ void operator()(const T (&p)[6][NIN], const T* Mi, T w0, T w1, T V, T,
+                                             T (&y)[6][NOUT]) const {
+    T pc = ((p[0][0] + p[1][0] + p[2][0]) + (p[3][0] + p[4][0] + p[5][0])) * (T)(1.0 / 6.0);
+    T f = -V * pc;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T h0 = f * w0 * Mi[c], h1 = f * w0 * Mi[3 + c], h2 = f * w1 * Mi[6 + c];
+      T s = h0 + h1;
+      y[0][c] = -s - h2;
+      y[1][c] = h0 - h2;
+      y[2][c] = h1 - h2;
+      y[3][c] = h2 - s;
+      y[4][c] = h0 + h2;
+      y[5][c] = h1 + h2;
+    }
+  }
+};
+
+// ------------------------------------------------------------------------------------ tile kernel
+// Boundary handling flags of the tile kernel.
+enum { PROJ_IN = 1, PROJ_OUT = 2, ADD_ID = 4 };
+
+template <typename T>
+__device__ __forceinline__ void project_vec(T (&v)[3], const T* s, int64_t soff, int64_t sstride, int bc) {
+  if (bc == TN_BC_NOSLIP) {
+    v[0] = v[1] = v[2] = (T)0;
+    return;
+  }
+  T sx = s[soff], sy = s[soff + sstride], sz = s[soff + 2 * sstride];
+  T dot = v[0] * sx + v[1] * sy + v[2] * sz;
+  v[0] -= dot * sx, v[1] -= dot * sy, v[2] -= dot * sz;
+}
+
+template <typename T, typename Op, int TT, int FLAGS>
+__global__ void __launch_bounds__((TT + 1) * (TT + 1))
+    k_tile(Dims D, Op op, const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
+           T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
+           const T* __restrict__ lay, const T* __restrict__ eta, const T* __restrict__ svec, int bc_in, int bc_out,
+           int kc) {
+  constexpr int NIN = Op::NIN, NOUT = Op::NOUT, W = TT + 1;
+  __shared__ T sm[4][NOUT][W][W];
+  const int N = D.N, n_r = D.n_r, P = D.P;
+  const int ntj = N / TT;
+  const int i0 = (blockIdx.x / ntj) * TT, j0 = (blockIdx.x % ntj) * TT;
+  const int d = blockIdx.z;
+  const int kc0 = blockIdx.y * kc, kc1 = min(n_r - 1, kc0 + kc);
+  const int ti = threadIdx.x / W, tj = threadIdx.x % W;
+  const int ci = i0 - 1 + ti, cj = j0 - 1 + tj;  // this thread's cell
+  const bool cell_ok = ci >= 0 && cj >= 0;       // ci, cj <= N - 1 always
+  const T* in[3] = {in0, in1, in2};
+  T* out[3] = {out0, out1, out2};
+
+  // lateral corner offsets of this cell: 00, 10, 01, 11
+  const int ci0 = max(ci, 0), cj0 = max(cj, 0);
+  const int64_t base = (int64_t)d * D.diamond_stride;
+  const int64_t cofs[4] = {(int64_t)ci0 * P + cj0, (int64_t)(ci0 + 1) * P + cj0, (int64_t)ci0 * P + cj0 + 1,
+                           (int64_t)(ci0 + 1) * P + cj0 + 1};
+  const int64_t lat_base = (int64_t)d * (N + 1) * P;
+
+  // per-cell lateral geometry (both triangles), kept in registers for the whole column
+  T Mi[2][9], dM[2];
+  {
+    const int64_t t0 = (((int64_t)d * N + ci0) * N + cj0) * 2;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Mi[w][q] = geo[(int64_t)q * D.n_tri + t0 + w];
+      dM[w] = geo[(int64_t)9 * D.n_tri + t0 + w];
+    }
+  }
+  // wedge-local lateral node -> cell corner: W0 = (00, 10, 01), W1 = (11, 01, 10)
+  constexpr int corner[2][3] = {{0, 1, 2}, {3, 2, 1}};
+
+  auto load_level = [&](int k, T (&v)[4][NIN]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) v[q][c] = cell_ok ? in[c][base + (int64_t)k * D.layer_stride + cofs[q]] : (T)0;
+    if ((FLAGS & PROJ_IN) && cell_ok && (k == 0 || k == n_r - 1)) {
+      const int bc = k == 0 ? bc_in : bc_out;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T vv[3] = {v[q][0], v[q][NIN > 1 ? 1 : 0], v[q][NIN > 2 ? 2 : 0]};
+        project_vec(vv, svec, lat_base + cofs[q], D.n_lat_layout, bc);
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) v[q][c] = vv[c];
+      }
+    }
+  };
+
+  // exchange the node-level sums of the four corners and write owned nodes of level k
+  auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) sm[q][c][ti][tj] = acc[q][c];
+    __syncthreads();
+    // nodes owned by this thread: (ci, cj) if ti, tj >= 1; plus the extra last row / column
+    const bool last_i = (i0 + TT == N) && ti == TT, last_j = (j0 + TT == N) && tj == TT;
+#pragma unroll
+    for (int oi = 0; oi < 2; ++oi)
+#pragma unroll
+      for (int oj = 0; oj < 2; ++oj) {
+        if (oi == 1 && !last_i) continue;
+        if (oj == 1 && !last_j) continue;
+        const int xi = ti + oi, xj = tj + oj;  // node position in tile-thread coordinates
+        if (xi < 1 || xj < 1) continue;
+        const int ni = ci + oi, nj = cj + oj;
+        T v[3] = {0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) {
+          T a = (xi <= TT && xj <= TT) ? sm[0][c][xi][xj] : (T)0;  // cell (ni, nj), corner 00
+          T b = (xj <= TT) ? sm[1][c][xi - 1][xj] : (T)0;          // cell (ni-1, nj), corner 10
+          T e = (xi <= TT) ? sm[2][c][xi][xj - 1] : (T)0;          // cell (ni, nj-1), corner 01
+          T f = sm[3][c][xi - 1][xj - 1];                          // cell (ni-1, nj-1), corner 11
+          v[c] = ((a + b) + e) + f;
+        }
+        const int64_t idx = base + (int64_t)k * D.layer_stride + (int64_t)ni * P + nj;
+        const bool shared = ni == 0 || ni == N || nj == 0 || nj == N;
+        if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
+          const int bc = k == 0 ? bc_in : bc_out;
+          const int64_t so = lat_base + (int64_t)ni * P + nj;
+          T raw[3] = {v[0], v[1], v[2]};
+          project_vec(raw, svec, so, D.n_lat_layout, bc);
+          if ((FLAGS & ADD_ID) && !shared) {
+            T uu[3], pu[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) uu[c] = pu[c] = in[c][idx];
+            project_vec(pu, svec, so, D.n_lat_layout, bc);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) raw[c] += uu[c] - pu[c];
+          }
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) v[c] = raw[c];
+        }
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) out[c][idx] = v[c];
+      }
+    __syncthreads();
+  };
+
+  T ub[4][NIN], ut[4][NIN];
+  T carry[4][NOUT];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) carry[q][c] = 0;
+
+  const int kstart = kc0 > 0 ? kc0 - 1 : 0;
+  load_level(kstart, ub);
+  for (int k = kstart; k < kc1; ++k) {
+    load_level(k + 1, ut);
+    T accb[4][NOUT], acct[4][NOUT];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
+    if (cell_ok) {
+      const T w0 = lay[4 * k], w1 = lay[4 * k + 1], vol = lay[4 * k + 2];
+      const int64_t widx = ((((int64_t)d * (n_r - 1) + k) * N + ci) * N + cj) * 2;
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        T ue[6][NIN], ye[6][NOUT];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < NIN; ++c) ue[a][c] = ub[corner[w][a]][c], ue[3 + a][c] = ut[corner[w][a]][c];
+        const T e = eta ? eta[widx + w] : (T)1;
+        op(ue, Mi[w], w0, w1, vol * dM[w], e, ye);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) accb[corner[w][a]][c] += ye[a][c], acct[corner[w][a]][c] += ye[3 + a][c];
+      }
+    }
+    if (k >= kc0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) accb[q][c] += carry[q][c];
+      exchange_write(k, accb);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) carry[q][c] = acct[q][c];
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c];
+    }
+  }
+  if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
+}
+
+template <typename T, typename Op, int FLAGS>
+cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const T* eta,
+                        cudaStream_t st) {
+  Dims D = dims(L);
+  const int tt = L.N >= TILE ? TILE : L.N;
+  const int ntiles = (L.N / tt) * (L.N / tt);
+  const int ncells = L.n_r - 1;
+  // radial chunks: enough CTAs to fill the GPU a few times over
+  int kc = ncells;
+  while (kc > 8 && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < 4 * 152) kc = (kc + 1) / 2;
+  dim3 grid(ntiles, (ncells + kc - 1) / kc, 10);
+  const T* i1 = Op::NIN > 1 ? in[1] : in[0];
+  const T* i2 = Op::NIN > 2 ? in[2] : in[0];
+  T* o1 = Op::NOUT > 1 ? out[1] : out[0];
+  T* o2 = Op::NOUT > 2 ? out[2] : out[0];
+  const T* sv = Tab<T>::s(L);
+  const T* geo = Tab<T>::geo(L);
+  const T* lay = Tab<T>::lay(L);
+#define TN_TILE_CASE(TTv)                                                                                     \
+  case TTv:                                                                                                   \
+    k_tile<T, Op, TTv, FLAGS><<<grid, (TTv + 1) * (TTv + 1), 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, \
+                                                                       geo, lay, eta, sv, bc.in, bc.out, kc); \
+    break;
+  switch (tt) {
+    TN_TILE_CASE(16)
+    TN_TILE_CASE(8)
+    TN_TILE_CASE(4)
+    TN_TILE_CASE(2)
+    TN_TILE_CASE(1)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef TN_TILE_CASE
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ interface
+template <typename T>
+__global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, const int64_t* __restrict__ goff,
+                            const T* __restrict__ gs, int ncomp, int mode, T* y0, T* y1, T* y2,
+                            const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
+                            int bc_in, int bc_out) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)n_groups * D.n_r) return;
+  const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
+  T* y[3] = {y0, y1, y2};
+  const T* u[3] = {u0, u1, u2};
+  const int b = gptr[g], e = gptr[g + 1];
+  const int64_t lo = (int64_t)k * D.layer_stride;
+  T v[3] = {0, 0, 0};
+  for (int q = b; q < e; ++q)
+    for (int c = 0; c < ncomp; ++c) v[c] += y[c][goff[q] + lo];
+  if (mode != 0 && (k == 0 || k == D.n_r - 1)) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    T w[3];
+    if (mode == 1)
+      for (int c = 0; c < 3; ++c) w[c] = u[c][goff[b] + lo];
+    if (bc == TN_BC_NOSLIP) {
+      for (int c = 0; c < 3; ++c) v[c] += mode == 1 ? w[c] : (T)1;
+    } else {
+      T s[3] = {gs[g], gs[n_groups + g], gs[2 * n_groups + g]};
+      if (mode == 1) {
+        T dot = w[0] * s[0] + w[1] * s[1] + w[2] * s[2];
+        for (int c = 0; c < 3; ++c) v[c] += dot * s[c];
+      } else {
+        for (int c = 0; c < 3; ++c) v[c] += s[c] * s[c];
+      }
+    }
+  }
+  for (int q = b; q < e; ++q)
+    for (int c = 0; c < ncomp; ++c) y[c][goff[q] + lo] = v[c];
+}
+
+// ------------------------------------------------------------------------------------ diag(A)
+// Thread per layout node; gathers the 3x3 node block of A from the (up to) 12 wedges
+// around the node: A_jj = sum_e V eta (|g|^2 I + 1/3 g g^T) (the -2/3 div term gives
+// -2/3 g g^T, the symmetric-gradient term g g^T, so 1/3 with div_term, 1 without).
+template <typename T>
+__global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, const T* __restrict__ eta,
+                         const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* d0, T* d1, T* d2) {
+  const int N = D.N, M = N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)10 * D.n_r * M * M;
+  if (tid >= total) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
+            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  // (cell di, cell dj, wedge, local lateral node) of the six triangles around lattice node (i, j)
+  const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
+  const T gxi[3] = {-1, 1, 0}, geta[3] = {-1, 0, 1};
+  const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
+  T B[6] = {0, 0, 0, 0, 0, 0};  // xx yy zz xy xz yz
+  T alpha = 0;
+  for (int q = 0; q < 6; ++q) {
+    const int ci = i + tri[q][0], cj = j + tri[q][1], w = tri[q][2], a = tri[q][3];
+    if (ci < 0 || cj < 0 || ci >= N || cj >= N) continue;
+    const int64_t t = (((int64_t)d * N + ci) * N + cj) * 2 + w;
+    T Mi[9];
+    for (int r = 0; r < 9; ++r) Mi[r] = geo[(int64_t)r * D.n_tri + t];
+    const T dM = geo[(int64_t)9 * D.n_tri + t];
+    for (int side = 0; side < 2; ++side) {  // side 0: node is bottom of layer k; 1: top of layer k-1
+      const int kk = side == 0 ? k : k - 1;
+      if (kk < 0 || kk >= D.n_r - 1) continue;
+      const T w0 = lay[4 * kk], w1 = lay[4 * kk + 1], vol = lay[4 * kk + 2];
+      const T gz = side == 0 ? (T)-1 : (T)1;
+      T g[3];
+      for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
+      const T ve = vol * dM * eta[((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w];
+      const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+      alpha += ve * g2;
+      const T tv = ve * third;
+      B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
+      B[3] += tv * g[0] * g[1], B[4] += tv * g[0] * g[2], B[5] += tv * g[1] * g[2];
+    }
+  }
+  T A[3][3] = {{alpha + B[0], B[3], B[4]}, {B[3], alpha + B[1], B[5]}, {B[4], B[5], alpha + B[2]}};
+  T out[3] = {A[0][0], A[1][1], A[2][2]};
+  const bool shared = i == 0 || i == N || j == 0 || j == N;
+  if (k == 0 || k == D.n_r - 1) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    const int64_t so = ((int64_t)d * M + i) * D.P + j;
+    if (bc == TN_BC_NOSLIP) {
+      out[0] = out[1] = out[2] = 0;
+    } else {
+      const T s[3] = {svec[so], svec[so + D.n_lat_layout], svec[so + 2 * D.n_lat_layout]};
+      T Pm[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Pm[r][c] = (r == c ? (T)1 : (T)0) - s[r] * s[c];
+      for (int c = 0; c < 3; ++c) {  // (P A P)_cc = sum_{a,b} P_ca A_ab P_bc
+        T acc = 0;
+        for (int a2 = 0; a2 < 3; ++a2)
+          for (int b2 = 0; b2 < 3; ++b2) acc += Pm[c][a2] * A[a2][b2] * Pm[b2][c];
+        out[c] = acc;
+      }
+    }
+    if (!shared) {
+      if (bc == TN_BC_NOSLIP) {
+        out[0] += 1, out[1] += 1, out[2] += 1;
+      } else {
+        for (int c = 0; c < 3; ++c) out[c] += svec[so + c * D.n_lat_layout] * svec[so + c * D.n_lat_layout];
+      }
+    }
+  }
+  const int64_t idx = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j;
+  d0[idx] = out[0], d1[idx] = out[1], d2[idx] = out[2];
+}
+
+// ------------------------------------------------------------------------------------ transfers
+// Nested iso-interpolation (Sec. 3): weight 1 at coincident nodes, 1/2 at lateral or radial
+// edge midpoints, 1/4 where both apply.  Lateral parents of fine lattice position (i, j):
+// even/even -> (i/2, j/2); odd i -> ((i-1)/2, j/2), ((i+1)/2, j/2); odd j -> (i/2, (j-1)/2),
+// (i/2, (j+1)/2); odd/odd -> midpoint of the coarse anti-diagonal ((i+1)/2, (j-1)/2), ((i-1)/2, (j+1)/2).
+template <typename T>
+__global__ void k_prolong(Dims F, Dims C, int ncomp, int apply_bc, const T* __restrict__ c0,
+                          const T* __restrict__ c1, const T* __restrict__ c2, T* f0, T* f1, T* f2,
+                          const T* __restrict__ svec, int bc_in, int bc_out) {
+  const int N = F.N, M = N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * F.n_r * M * M) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % F.n_r),
+            d = (int)(tid / ((int64_t)M * M * F.n_r));
+  int li[2], lj[2], nl;
+  if (!(i & 1) && !(j & 1)) {
+    li[0] = i / 2, lj[0] = j / 2, nl = 1;
+  } else if ((i & 1) && !(j & 1)) {
+    li[0] = (i - 1) / 2, lj[0] = j / 2, li[1] = (i + 1) / 2, lj[1] = j / 2, nl = 2;
+  } else if (!(i & 1) && (j & 1)) {
+    li[0] = i / 2, lj[0] = (j - 1) / 2, li[1] = i / 2, lj[1] = (j + 1) / 2, nl = 2;
+  } else {
+    li[0] = (i + 1) / 2, lj[0] = (j - 1) / 2, li[1] = (i - 1) / 2, lj[1] = (j + 1) / 2, nl = 2;
+  }
+  int rk[2], nrk;
+  if (!(k & 1)) rk[0] = k / 2, nrk = 1;
+  else rk[0] = (k - 1) / 2, rk[1] = (k + 1) / 2, nrk = 2;
+  const T* cs[3] = {c0, c1, c2};
+  T* fs[3] = {f0, f1, f2};
+  T v[3];
+  for (int c = 0; c < ncomp; ++c) {
+    T rad[2];
+    for (int r = 0; r < nrk; ++r) {
+      const int64_t b = (int64_t)d * C.diamond_stride + (int64_t)rk[r] * C.layer_stride;
+      rad[r] = nl == 1 ? cs[c][b + (int64_t)li[0] * C.P + lj[0]]
+                       : (T)0.5 * (cs[c][b + (int64_t)li[0] * C.P + lj[0]] + cs[c][b + (int64_t)li[1] * C.P + lj[1]]);
+    }
+    v[c] = nrk == 1 ? rad[0] : (T)0.5 * (rad[0] + rad[1]);
+  }
+  if (apply_bc && ncomp == 3 && (k == 0 || k == F.n_r - 1))
+    project_vec(v, svec, ((int64_t)d * M + i) * F.P + j, F.n_lat_layout, k == 0 ? bc_in : bc_out);
+  const int64_t idx = (int64_t)d * F.diamond_stride + (int64_t)k * F.layer_stride + (int64_t)i * F.P + j;
+  for (int c = 0; c < ncomp; ++c) fs[c][idx] = v[c];
+}
+
+// Restriction P^T: coarse node (I, J, K) gathers the fine nodes it interpolates to: lateral
+// (2I, 2J) with weight 1 and its six lattice neighbours with weight 1/2, radial 2K (1) and
+// 2K +- 1 (1/2).  Fine nodes shared by several diamonds are counted by their canonical copy
+// only; the coarse copies are then summed by launch_interface.
+template <typename T>
+__global__ void k_restrict(Dims F, Dims C, int ncomp, const uint8_t* __restrict__ owned, const T* __restrict__ f0,
+                           const T* __restrict__ f1, const T* __restrict__ f2, T* c0, T* c1, T* c2) {
+  const int NC = C.N, MC = NC + 1, NF = F.N, MF = NF + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
+  const int J = (int)(tid % MC), I = (int)((tid / MC) % MC), K = (int)((tid / ((int64_t)MC * MC)) % C.n_r),
+            d = (int)(tid / ((int64_t)MC * MC * C.n_r));
+  const int nb[7][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, -1}, {-1, 1}};
+  const T* fs[3] = {f0, f1, f2};
+  T* cs[3] = {c0, c1, c2};
+  T v[3] = {0, 0, 0};
+  for (int r = -1; r <= 1; ++r) {
+    const int kf = 2 * K + r;
+    if (kf < 0 || kf >= F.n_r) continue;
+    const T wr = r == 0 ? (T)1 : (T)0.5;
+    T lat[3] = {0, 0, 0};
+    for (int q = 0; q < 7; ++q) {
+      const int fi = 2 * I + nb[q][0], fj = 2 * J + nb[q][1];
+      if (fi < 0 || fj < 0 || fi > NF || fj > NF) continue;
+      if (!owned[((int64_t)d * MF + fi) * F.P + fj]) continue;
+      const T wl = q == 0 ? (T)1 : (T)0.5;
+      const int64_t idx = (int64_t)d * F.diamond_stride + (int64_t)kf * F.layer_stride + (int64_t)fi * F.P + fj;
+      for (int c = 0; c < ncomp; ++c) lat[c] += wl * fs[c][idx];
+    }
+    for (int c = 0; c < ncomp; ++c) v[c] += wr * lat[c];
+  }
+  const int64_t idx = (int64_t)d * C.diamond_stride + (int64_t)K * C.layer_stride + (int64_t)I * C.P + J;
+  for (int c = 0; c < ncomp; ++c) cs[c][idx] = v[c];
+}
+
+// In-place projection of the boundary layers (after a restriction's interface sum).
+template <typename T>
+__global__ void k_project_bdry(Dims D, T* y0, T* y1, T* y2, const T* __restrict__ svec, int bc_in, int bc_out) {
+  const int M = D.N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * 2 * M * M) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), side = (int)((tid / ((int64_t)M * M)) % 2),
+            d = (int)(tid / ((int64_t)M * M * 2));
+  const int k = side == 0 ? 0 : D.n_r - 1;
+  const int64_t idx = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j;
+  T v[3] = {y0[idx], y1[idx], y2[idx]};
+  project_vec(v, svec, ((int64_t)d * M + i) * D.P + j, D.n_lat_layout, side == 0 ? bc_in : bc_out);
+  y0[idx] = v[0], y1[idx] = v[1], y2[idx] = v[2];
+}
+
+// ------------------------------------------------------------------------------------ diag(M_1/eta)
+// Thread per coarse (pressure) node: sum over the coarse wedges around it and their 8 fine
+// children of V_e / eta_e psi_k(q_c^e)^2.  psi_k at a child's barycentre is the coarse W1
+// basis at the child's barycentre in the coarse reference wedge: lateral (2/3, 1/6, 1/6)
+// (permuted) for the three corner children, (1/3, 1/3, 1/3) for the middle one; radial
+// (3/4, 1/4) for the lower child layer and (1/4, 3/4) for the upper one.
+template <typename T>
+__global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T* __restrict__ layF,
+                             const T* __restrict__ etaF, T* m) {
+  const int NC = C.N, MC = NC + 1, NF = F.N;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
+  const int J = (int)(tid % MC), I = (int)((tid / MC) % MC), K = (int)((tid / ((int64_t)MC * MC)) % C.n_r),
+            d = (int)(tid / ((int64_t)MC * MC * C.n_r));
+  const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
+  // children of coarse W0 / W1: (fine di, fine dj, fine wedge), barycentric weight of local node a
+  const int kid[2][4][3] = {{{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}}};
+  T acc = 0;
+  for (int q = 0; q < 6; ++q) {
+    const int ci = I + tri[q][0], cj = J + tri[q][1], w = tri[q][2], a = tri[q][3];
+    if (ci < 0 || cj < 0 || ci >= NC || cj >= NC) continue;
+    for (int side = 0; side < 2; ++side) {  // node is bottom of coarse layer K (side 0) or top of K-1
+      const int kc = side == 0 ? K : K - 1;
+      if (kc < 0 || kc >= C.n_r - 1) continue;
+      for (int c = 0; c < 4; ++c) {
+        const T wl = c == 3 ? (T)(1.0 / 3.0) : (c == a ? (T)(2.0 / 3.0) : (T)(1.0 / 6.0));
+        const int fi = 2 * ci + kid[w][c][0], fj = 2 * cj + kid[w][c][1], fw = kid[w][c][2];
+        const int64_t t = (((int64_t)d * NF + fi) * NF + fj) * 2 + fw;
+        const T dM = geoF[(int64_t)9 * F.n_tri + t];
+        for (int r = 0; r < 2; ++r) {
+          const int kf = 2 * kc + r;
+          // weight of this coarse node: bottom node (side 0) -> 3/4 in lower child, 1/4 in upper
+          const T wr = (side == 0) == (r == 0) ? (T)0.75 : (T)0.25;
+          const T psi = wl * wr;
+          const T V = layF[4 * kf + 2] * dM;
+          const T e = etaF[((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw];
+          acc += V / e * psi * psi;
+        }
+      }
+    }
+  }
+  m[(int64_t)d * C.diamond_stride + (int64_t)K * C.layer_stride + (int64_t)I * C.P + J] = acc;
+}
+
+// ------------------------------------------------------------------------------------ viscosity
+// lay[4 k + 3] holds the layer mid-radius (r_k + r_k+1) / 2.
+__global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, double jump_r, double jump_f,
+                             const double* __restrict__ lay, double* eta) {
+  const int N = D.N;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nw = (int64_t)10 * (D.n_r - 1) * N * N * 2;
+  if (tid >= nw) return;
+  const int w = (int)(tid % 2), j = (int)((tid / 2) % N), i = (int)((tid / (2 * N)) % N),
+            k = (int)((tid / (2 * (int64_t)N * N)) % (D.n_r - 1)), d = (int)(tid / (2 * (int64_t)N * N * (D.n_r - 1)));
+  int pi_[3], pj_[3];
+  if (w == 0) pi_[0] = i, pj_[0] = j, pi_[1] = i + 1, pj_[1] = j, pi_[2] = i, pj_[2] = j + 1;
+  else pi_[0] = i + 1, pj_[0] = j + 1, pi_[1] = i, pj_[1] = j + 1, pi_[2] = i + 1, pj_[2] = j;
+  const int64_t b = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride;
+  double s = 0;
+  for (int a = 0; a < 3; ++a) s += T[b + (int64_t)pi_[a] * D.P + pj_[a]];
+  for (int a = 0; a < 3; ++a) s += T[b + D.layer_stride + (int64_t)pi_[a] * D.P + pj_[a]];
+  const double Te = s / 6.0;
+  double e = exp(E * (0.5 - Te));
+  if (jump_r > 0 && lay[4 * k + 3] < jump_r) e = jump_f * e;
+  eta[tid] = e;
+}
+
+__global__ void k_eta_coarsen(Dims F, Dims C, const double* __restrict__ ef, double* ec) {
+  const int NC = C.N, NF = F.N;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nw = (int64_t)10 * (C.n_r - 1) * NC * NC * 2;
+  if (tid >= nw) return;
+  const int w = (int)(tid % 2), J = (int)((tid / 2) % NC), I = (int)((tid / (2 * NC)) % NC),
+            K = (int)((tid / (2 * (int64_t)NC * NC)) % (C.n_r - 1)),
+            d = (int)(tid / (2 * (int64_t)NC * NC * (C.n_r - 1)));
+  const int kid[2][4][3] = {{{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}}};
+  double s = 0;
+  for (int c = 0; c < 4; ++c)
+    for (int r = 0; r < 2; ++r) {
+      const int fi = 2 * I + kid[w][c][0], fj = 2 * J + kid[w][c][1], fw = kid[w][c][2], kf = 2 * K + r;
+      s += ef[((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw];
+    }
+  ec[tid] = s / 8.0;
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* b, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------------------------ buoyancy
+// f_j = sum_e V_e Ra T(q_c) r_hat(q_c) / 6 with r_hat(q_c) = sbar / |sbar| (x(q_c) = rho sbar).
+__global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double* __restrict__ lay,
+                           const double* __restrict__ svec, const double* __restrict__ T, double Ra, int bc_in,
+                           int bc_out, double* f0, double* f1, double* f2) {
+  const int N = D.N, M = N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * D.n_r * M * M) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
+            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
+  double f[3] = {0, 0, 0};
+  for (int q = 0; q < 6; ++q) {
+    const int ci = i + tri[q][0], cj = j + tri[q][1], w = tri[q][2];
+    if (ci < 0 || cj < 0 || ci >= N || cj >= N) continue;
+    int pi_[3], pj_[3];
+    if (w == 0) pi_[0] = ci, pj_[0] = cj, pi_[1] = ci + 1, pj_[1] = cj, pi_[2] = ci, pj_[2] = cj + 1;
+    else pi_[0] = ci + 1, pj_[0] = cj + 1, pi_[1] = ci, pj_[1] = cj + 1, pi_[2] = ci + 1, pj_[2] = cj;
+    double sb[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+      for (int c = 0; c < 3; ++c) sb[c] += svec[((int64_t)d * M + pi_[a]) * D.P + pj_[a] + c * D.n_lat_layout];
+    const double nrm = sqrt(sb[0] * sb[0] + sb[1] * sb[1] + sb[2] * sb[2]);
+    const int64_t t = (((int64_t)d * N + ci) * N + cj) * 2 + w;
+    const double dM = geo[(int64_t)9 * D.n_tri + t];
+    for (int side = 0; side < 2; ++side) {
+      const int kk = side == 0 ? k : k - 1;
+      if (kk < 0 || kk >= D.n_r - 1) continue;
+      const int64_t b = (int64_t)d * D.diamond_stride + (int64_t)kk * D.layer_stride;
+      double s = 0;
+      for (int a = 0; a < 3; ++a) s += T[b + (int64_t)pi_[a] * D.P + pj_[a]];
+      for (int a = 0; a < 3; ++a) s += T[b + D.layer_stride + (int64_t)pi_[a] * D.P + pj_[a]];
+      const double V = lay[4 * kk + 2] * dM;
+      const double wgt = V * Ra * (s / 6.0) / 6.0 / nrm;
+      for (int c = 0; c < 3; ++c) f[c] += wgt * sb[c];
+    }
+  }
+  const bool shared = i == 0 || i == N || j == 0 || j == N;
+  (void)shared;
+  if (k == 0 || k == D.n_r - 1)
+    project_vec(f, svec, ((int64_t)d * M + i) * D.P + j, D.n_lat_layout, k == 0 ? bc_in : bc_out);
+  const int64_t idx = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j;
+  f0[idx] = f[0], f1[idx] = f[1], f2[idx] = f[2];
+}
+
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st) {
+  OpA<T> op{div_term};
+  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, Tab<T>::eta(L), st);
+  if (e != cudaSuccess) return e;
+  return launch_interface<T>(L, bc, 3, 1, y, u, st);
+}
+
+template <typename T>
+cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st) {
+  T* out[1] = {q};
+  cudaError_t e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return launch_interface<T>(L, bc, 1, 0, out, nullptr, st);
+}
+
+template <typename T>
+cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cudaStream_t st) {
+  const T* in[1] = {p};
+  cudaError_t e = launch_tile<T, OpGrad<T>, PROJ_OUT>(L, bc, OpGrad<T>{}, in, y, nullptr, st);
+  if (e != cudaSuccess) return e;
+  return launch_interface<T>(L, bc, 3, 0, y, nullptr, st);
+}
+
+template <typename T>
+cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cudaStream_t st) {
+  Dims D = dims(L);
+  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
+  k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), Tab<T>::eta(L), Tab<T>::s(L), bc.in,
+                                            bc.out, div_term, d[0], d[1], d[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_interface<T>(L, bc, 3, 2, d, nullptr, st);
+}
+
+template <typename T>
+cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st) {
+  const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
+  k_diag_pmass<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), Tab<T>::eta(F), m);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  T* out[1] = {m};
+  return launch_interface<T>(C, BC{0, 0}, 1, 0, out, nullptr, st);
+}
+
+template <typename T>
+cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* const* y, const T* const* u,
+                             cudaStream_t st) {
+  const int64_t n = (int64_t)L.n_groups * L.n_r;
+  if (n == 0) return cudaSuccess;
+  T* y1 = ncomp > 1 ? y[1] : y[0];
+  T* y2 = ncomp > 2 ? y[2] : y[0];
+  const T* u0 = u ? u[0] : nullptr;
+  const T* u1 = u ? u[1] : nullptr;
+  const T* u2 = u ? u[2] : nullptr;
+  k_interface<T><<<nblk(n, 128), 128, 0, st>>>(dims(L), L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), ncomp, mode,
+                                               y[0], y1, y2, u0, u1, u2, bc.in, bc.out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* c,
+                           T* const* f, cudaStream_t st) {
+  const int64_t n = (int64_t)10 * F.n_r * (F.N + 1) * (F.N + 1);
+  const T* c1 = ncomp > 1 ? c[1] : c[0];
+  const T* c2 = ncomp > 2 ? c[2] : c[0];
+  T* f1 = ncomp > 1 ? f[1] : f[0];
+  T* f2 = ncomp > 2 ? f[2] : f[0];
+  k_prolong<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), ncomp, apply_bc, c[0], c1, c2, f[0], f1, f2,
+                                             Tab<T>::s(F), bc.in, bc.out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* f,
+                            T* const* c, cudaStream_t st) {
+  const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
+  const T* f1 = ncomp > 1 ? f[1] : f[0];
+  const T* f2 = ncomp > 2 ? f[2] : f[0];
+  T* c1 = ncomp > 1 ? c[1] : c[0];
+  T* c2 = ncomp > 2 ? c[2] : c[0];
+  k_restrict<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), ncomp, F.owned, f[0], f1, f2, c[0], c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_interface<T>(C, bc, ncomp, 0, c, nullptr, st);
+  if (e != cudaSuccess || !(apply_bc && ncomp == 3)) return e;
+  const int64_t nb = (int64_t)10 * 2 * (C.N + 1) * (C.N + 1);
+  k_project_bdry<T><<<nblk(nb, 256), 256, 0, st>>>(dims(C), c[0], c[1], c[2], Tab<T>::s(C), bc.in, bc.out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double jump_r, double jump_f, double* eta,
+                              cudaStream_t st) {
+  k_eta_from_T<<<nblk(L.n_wedges, 256), 256, 0, st>>>(dims(L), T, E, jump_r, jump_f, L.lay64, eta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st) {
+  k_eta_coarsen<<<nblk(C.n_wedges, 256), 256, 0, st>>>(dims(F), dims(C), ef, ec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
+  k_to_f32<<<nblk(n, 256), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st) {
+  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
+  k_buoyancy<<<nblk(n, 256), 256, 0, st>>>(dims(L), L.geo64, L.lay64, L.s64, T, Ra, bc.in, bc.out, f[0], f[1], f[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_interface<double>(L, bc, 3, 0, f, nullptr, st);
+}
+
+#define TN_INST(T)                                                                                               \
+  template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t);      \
+  template cudaError_t launch_div_fine<T>(const Level&, BC, const T* const*, T*, cudaStream_t);                 \
+  template cudaError_t launch_grad_fine<T>(const Level&, BC, const T*, T* const*, cudaStream_t);                \
+  template cudaError_t launch_diag_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                        \
+  template cudaError_t launch_diag_pmass<T>(const Level&, const Level&, T*, cudaStream_t);                      \
+  template cudaError_t launch_interface<T>(const Level&, BC, int, int, T* const*, const T* const*, cudaStream_t); \
+  template cudaError_t launch_prolong<T>(const Level&, const Level&, BC, int, int, const T* const*, T* const*,   \
+                                         cudaStream_t);                                                         \
+  template cudaError_t launch_restrict<T>(const Level&, const Level&, BC, int, int, const T* const*, T* const*,  \
+                                          cudaStream_t);
+TN_INST(double)
+TN_INST(float)
+#undef TN_INST
+
+}  // namespace tn

@@ -1,0 +1,228 @@
+"""GPU parity of the wedge Stokes operators against the CPU FP64 oracle.
+
+Every call goes through the C ABI (ctypes binding).  FP64 bar: normwise max-relative
+error <= 1e-12 (max |y_gpu - y_oracle| / max |y_oracle|); the FP32 path is checked
+against a bound derived from single-precision rounding."""
+import numpy as np
+import pytest
+
+from oracle import operators as O
+from oracle.fields import buoyancy_rhs, coarsen_viscosity, viscosity
+from oracle.mesh import ShellMesh
+from paper_2609_21633_gb300 import inputs
+from tests.layout import LayoutMap, max_rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+BCS = {"free/free": (0, 0), "noslip/free": (1, 0), "noslip/noslip": (1, 1)}
+ORACLE_BC = {0: O.FREE, 1: O.NOSLIP}
+
+
+@pytest.fixture(scope="module")
+def tn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2609_21633_gb300 as tn
+    tn.lib()
+    return tn
+
+
+class Case:
+    """One mesh on both sides with random fields (seeded)."""
+
+    def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0):
+        self.tn = tn
+        self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term)
+        self.info = tn.tn_mesh_info(self.m, 0)
+        self.om = ShellMesh(level, n_r, r_in, r_out)
+        self.map = LayoutMap(self.info, self.om)
+        self.P = O.boundary_projectors(self.om, (ORACLE_BC[bc[0]], ORACLE_BC[bc[1]]))
+        self.eta = inputs.lognormal_viscosity(self.om.n_wedges, seed + 1)
+        self.div_term = div_term
+        self.eta_dev = torch.tensor(self.map.wedges_to_layout(self.eta), device="cuda")
+        tn.tn_set_viscosity(self.m, self.eta_dev)
+        self.rng_seed = seed
+
+    def vec(self, seed, n=None):
+        return inputs.normal((3, self.om.n_nodes) if n is None else n, seed)
+
+    def dev(self, vals, dtype=torch.float64):
+        return torch.tensor(self.map.to_layout(vals), device="cuda", dtype=dtype)
+
+    def zeros(self, n=3, dtype=torch.float64, info=None):
+        info = info or self.info
+        return [torch.zeros(info["n_layout"], device="cuda", dtype=dtype) for _ in range(n)]
+
+    def host(self, t, mp=None):
+        return (mp or self.map).from_layout(t.double().cpu().numpy())
+
+    def close(self):
+        self.tn.tn_mesh_destroy(self.m)
+
+
+def test_mesh_matches_oracle(tn):
+    for level in (1, 3, 5):
+        c = Case(tn, level, 3)
+        pts = tn.tn_mesh_lateral_points(c.m, 0)
+        assert np.abs(pts - c.om.lat_pts).max() <= 2e-16
+        canon = tn.tn_mesh_canonical_index(c.m, 0)
+        # two layout entries are copies of one node exactly when the oracle de-duplicates them together
+        assert np.array_equal(c.map.node[np.searchsorted(c.map.idx, canon[c.map.idx])], c.map.node)
+        groups = np.unique(canon[c.map.idx]).size
+        assert groups == c.om.n_nodes
+        c.close()
+
+
+@pytest.mark.parametrize("level,n_r", [(1, 3), (2, 5), (3, 9), (4, 17), (4, 27), (4, 33), (5, 9)])
+@pytest.mark.parametrize("bc", ["free/free", "noslip/free"])
+def test_apply_A_f64(tn, level, n_r, bc):
+    c = Case(tn, level, n_r, BCS[bc])
+    u = c.vec(10)
+    want = O.apply_A_constrained(c.om, c.eta, u, c.P)
+    ud = [c.dev(u[i]) for i in range(3)]
+    y = c.zeros()
+    tn.tn_apply_A(c.m, 0, ud, y)
+    got = np.stack([c.host(t) for t in y])
+    assert max_rel(got, want) <= TOL64
+    # deterministic: a second apply is bitwise identical
+    y2 = c.zeros()
+    tn.tn_apply_A(c.m, 0, ud, y2)
+    assert all(torch.equal(a, b) for a, b in zip(y, y2))
+    c.close()
+
+
+def test_apply_A_without_div_term(tn):
+    c = Case(tn, 3, 9, div_term=False)
+    u = c.vec(11)
+    want = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=False)
+    y = c.zeros()
+    tn.tn_apply_A(c.m, 0, [c.dev(u[i]) for i in range(3)], y)
+    assert max_rel(np.stack([c.host(t) for t in y]), want) <= TOL64
+    c.close()
+
+
+def test_apply_A_f32(tn):
+    c = Case(tn, 4, 17)
+    u = c.vec(12)
+    want = O.apply_A_constrained(c.om, c.eta, u, c.P)
+    y = c.zeros(dtype=torch.float32)
+    tn.tn_apply_A(c.m, 0, [c.dev(u[i], torch.float32) for i in range(3)], y)
+    got = np.stack([c.host(t) for t in y])
+    assert max_rel(got, want) <= TOL32
+    c.close()
+
+
+@pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"), (4, 27, "free/free"),
+                                          (5, 9, "free/free")])
+def test_apply_B_and_BT_f64(tn, level, n_r, bc):
+    c = Case(tn, level, n_r, BCS[bc])
+    pm = O.pressure_mesh(c.om)
+    Pp = O.prolongation(c.om, pm)
+    B = O.assemble_B(c.om, Pp)
+    Pm = O.projector_matrix(c.P)
+    pinfo = tn.tn_mesh_info(c.m, 1)
+    pmap = LayoutMap(pinfo, pm)
+    u = c.vec(20)
+    q = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
+    tn.tn_apply_B(c.m, 0, [c.dev(u[i]) for i in range(3)], q)
+    want_q = B @ (Pm @ u.ravel())
+    assert max_rel(pmap.from_layout(q.cpu().numpy()), want_q) <= TOL64
+    p = inputs.normal(pm.n_nodes, 21)
+    y = c.zeros()
+    tn.tn_apply_BT(c.m, 0, torch.tensor(pmap.to_layout(p), device="cuda"), y)
+    want_y = (Pm @ (B.T @ p)).reshape(3, -1)
+    assert max_rel(np.stack([c.host(t) for t in y]), want_y) <= TOL64
+    c.close()
+
+
+@pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"), (4, 17, "free/free")])
+def test_diagonals_f64(tn, level, n_r, bc):
+    c = Case(tn, level, n_r, BCS[bc])
+    want = O.diag_A_constrained(c.om, c.eta, c.P)
+    d = c.zeros()
+    tn.tn_diag_A(c.m, 0, d)
+    assert max_rel(np.stack([c.host(t) for t in d]), want) <= TOL64
+    pm = O.pressure_mesh(c.om)
+    pinfo = tn.tn_mesh_info(c.m, 1)
+    pmap = LayoutMap(pinfo, pm)
+    mm = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
+    tn.tn_diag_pmass(c.m, 0, mm)
+    want_m = O.diag_pressure_mass(c.om, O.prolongation(c.om, pm), c.eta)
+    assert max_rel(pmap.from_layout(mm.cpu().numpy()), want_m) <= TOL64
+    c.close()
+
+
+@pytest.mark.parametrize("level,n_r", [(3, 9), (4, 17)])
+def test_transfers_f64(tn, level, n_r):
+    c = Case(tn, level, n_r, BCS["noslip/free"])
+    cm = O.pressure_mesh(c.om)
+    cinfo = tn.tn_mesh_info(c.m, 1)
+    cmap = LayoutMap(cinfo, cm)
+    Pt = O.prolongation(c.om, cm)
+    Pc = O.boundary_projectors(cm, (O.NOSLIP, O.FREE))
+    # scalar prolongation / restriction
+    x = inputs.normal(cm.n_nodes, 30)
+    f = torch.zeros(c.info["n_layout"], device="cuda", dtype=torch.float64)
+    tn.tn_prolong(c.m, 0, [torch.tensor(cmap.to_layout(x), device="cuda")], [f])
+    assert max_rel(c.host(f), Pt @ x) <= 1e-15
+    z = inputs.normal(c.om.n_nodes, 31)
+    g = torch.zeros(cinfo["n_layout"], device="cuda", dtype=torch.float64)
+    tn.tn_restrict(c.m, 0, [c.dev(z)], [g])
+    assert max_rel(cmap.from_layout(g.cpu().numpy()), Pt.T @ z) <= 1e-14
+    # velocity with boundary projection
+    v = inputs.normal((3, cm.n_nodes), 32)
+    fv = c.zeros()
+    tn.tn_prolong(c.m, 0, [torch.tensor(cmap.to_layout(v[i]), device="cuda") for i in range(3)], fv, apply_bc=True)
+    want = O.project(c.P, np.stack([Pt @ v[i] for i in range(3)]))
+    assert max_rel(np.stack([c.host(t) for t in fv]), want) <= 1e-15
+    w = c.vec(33)
+    gv = [torch.zeros(cinfo["n_layout"], device="cuda", dtype=torch.float64) for _ in range(3)]
+    tn.tn_restrict(c.m, 0, [c.dev(w[i]) for i in range(3)], gv, apply_bc=True)
+    want = O.project(Pc, np.stack([Pt.T @ w[i] for i in range(3)]))
+    assert max_rel(np.stack([cmap.from_layout(t.cpu().numpy()) for t in gv]), want) <= 1e-14
+    c.close()
+
+
+def test_temperature_viscosity_and_buoyancy(tn):
+    c = Case(tn, 4, 17)
+    T = inputs.temperature(c.om.node_xyz(), 0.55, 1.0) + inputs.normal(c.om.n_nodes, 40, 0.01)
+    Td = c.dev(T)
+    tn.tn_set_temperature(c.m, Td, np.log(1e3), 0.9, 30.0)
+    eta_want = viscosity(c.om, T, np.log(1e3), jump_r=0.9, jump_factor=30.0)
+    got = torch.zeros(c.info["n_wedges"], device="cuda", dtype=torch.float64)
+    tn.tn_get_viscosity(c.m, 0, got)
+    assert np.abs(c.map.wedges_from_layout(got.cpu().numpy()) / eta_want - 1).max() <= 1e-14
+    # coarse level = mean of the 8 children
+    cm = ShellMesh(3, 9, 0.55, 1.0)
+    cinfo = tn.tn_mesh_info(c.m, 1)
+    cmap = LayoutMap(cinfo, cm)
+    gc = torch.zeros(cinfo["n_wedges"], device="cuda", dtype=torch.float64)
+    tn.tn_get_viscosity(c.m, 1, gc)
+    assert np.abs(cmap.wedges_from_layout(gc.cpu().numpy()) / coarsen_viscosity(c.om, cm, eta_want) - 1).max() <= 1e-14
+    f = c.zeros()
+    tn.tn_buoyancy(c.m, Td, 7e3, f)
+    want = buoyancy_rhs(c.om, T, 7e3, c.P)
+    assert max_rel(np.stack([c.host(t) for t in f]), want) <= TOL64
+    c.close()
+
+
+def test_argument_errors(tn):
+    c = Case(tn, 2, 5)
+    u = [c.dev(c.vec(1)[i]) for i in range(3)]
+    with pytest.raises(tn.TnError) as e:
+        tn.tn_apply_A(c.m, 0, u, [u[0], c.zeros(1)[0], c.zeros(1)[0]])
+    assert e.value.status == tn.TN_EINVAL
+    with pytest.raises(tn.TnError):
+        tn.tn_apply_A(c.m, 7, u, c.zeros())
+    with pytest.raises(tn.TnError):
+        tn.tn_apply_B(c.m, c.info["depth"] - 1, u, c.zeros(1)[0])
+    m2 = tn.tn_mesh_create(2, 5, 0.55, 1.0)
+    with pytest.raises(tn.TnError) as e:
+        tn.tn_apply_A(m2, 0, u, c.zeros())
+    assert e.value.status == tn.TN_ESTATE
+    tn.tn_mesh_destroy(m2)
+    c.close()
