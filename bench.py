@@ -1,0 +1,316 @@
+"""Benchmark: FP64 Stokes-operator applies on the radial-jump shell (lateral level 7, 129 radial layers).
+
+One step = one apply each of A, B, B^T and diag(A) (the operator applications of the
+hot path) on 63.4 M velocity DoFs + 2.66 M pressure DoFs.  value = DoFs processed per
+second, summed over the four operators (A, diag: velocity DoFs; B, B^T: velocity +
+pressure DoFs), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: independent replicas, one per rank (the apply does not shard without a
+halo exchange; no collective on the data path), scaling "weak".
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+R_IN, R_OUT = 0.55, 1.0
+LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, contrast 1e3
+# Algorithmic FP64 work of one A apply per hexahedral cell (2 wedges), FMA = 2 flops:
+# per wedge 33 (differences) + 9 (scaling) + 45 (grad u) + 20 (stress) + 54 (stress x M^-T)
+# + 21 (test-gradient combination) + 18 (accumulation) = 200.
+A_FLOPS_PER_CELL = 400.0
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--level", type=int, default=7)
+    ap.add_argument("--n_r", type=int, default=129)
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dof_counts(level, n_r):
+    nv = 3 * (10 * 4 ** level + 2) * n_r
+    npr = (10 * 4 ** (level - 1) + 2) * ((n_r - 1) // 2 + 1)
+    return nv, npr, 4 * nv + 2 * npr  # A + diag: nv each; B, B^T: nv + np each
+
+
+def workload_name(level, n_r):
+    return f"radial-jump shell l={level} (N={2 ** level}), {n_r} radial layers, FP64 A+B+BT+diag apply"
+
+
+# ---------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 7]
+        os.unlink(self.path)
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i] and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------- oracle arm
+def oracle_step_sample(level, n_r, layers, seed, frac=1.0):
+    """Time the CPU oracle on a bounded sample of the workload: the wedges of the first
+    ``frac`` of the lateral triangles (diamond-major order) in the innermost ``layers``
+    radial cells of the same shell (same lateral resolution and radial spacing).
+    Returns (seconds, DoFs processed, description)."""
+    from oracle import operators as O
+    from oracle.fields import viscosity
+    from oracle.mesh import ShellMesh
+    from paper_2609_21633_gb300 import inputs
+    dr = (R_OUT - R_IN) / (n_r - 1)
+    om = ShellMesh(level, layers + 1, R_IN, R_IN + dr * layers)
+    T = inputs.temperature(om.node_xyz(), R_IN, R_OUT) + inputs.normal(om.n_nodes, seed + 7, 0.01)
+    eta = viscosity(om, T, LAW["E"], jump_r=LAW["jump_r"], jump_factor=LAW["jump_factor"])
+    P = O.boundary_projectors(om)
+    u = inputs.normal((3, om.n_nodes), seed + 8)
+    pm = O.pressure_mesh(om)
+    p = inputs.normal(pm.n_nodes, seed + 9)
+    Pp = O.prolongation(om, pm)
+    Pm = O.projector_matrix(P)
+    wedges = np.arange(max(1, int(round(frac * om.n_wedges))))
+    t0 = time.perf_counter()
+    O.apply_A_constrained(om, eta, u, P, wedges=wedges)
+    B = O.assemble_B(om, Pp, wedges=wedges)
+    B @ (Pm @ u.ravel())
+    Pm @ (B.T @ p)
+    O.diag_A_constrained(om, eta, P, wedges=wedges)
+    dt = time.perf_counter() - t0
+    share = len(wedges) / om.n_wedges
+    nv, npr = 3 * om.n_nodes, pm.n_nodes
+    desc = (f"{len(wedges) // 2} of {10 * 4 ** level * (n_r - 1)} cells (innermost {layers} radial cells, "
+            f"{100 * share:.0f}% of their wedges) of the same shell, one A+B+BT+diag step, numpy/scipy, 1 thread")
+    return dt, share * (4 * nv + 2 * npr), desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    samples = []
+    # size each step so that warm-up + timed steps take about two and a half minutes
+    frac = min(1.0, 150.0 / 21.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_step_sample(args.level, args.n_r, 2, args.seed, frac)
+    for _ in range(args.steps):
+        dt, ndof, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed, frac)
+        samples.append((dt, ndof))
+    tot_t = sum(s[0] for s in samples)
+    value = sum(s[1] for s in samples) / tot_t / 1e9
+    line = {
+        "impl": "reference", "metric": "Stokes-apply GDoF/s (FP64 A+B+BT+diag step)", "value": value,
+        "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / len(samples), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.level, args.n_r), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2609_21633_gb300 as tn
+    from paper_2609_21633_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    st = torch.cuda.current_stream()
+
+    m = tn.tn_mesh_create(args.level, args.n_r, R_IN, R_OUT)
+    info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
+    n = info["n_layout"]
+    canon = torch.from_numpy(tn.tn_mesh_canonical_index(m, 0))
+    valid = canon >= 0
+    # node coordinates of the layout, for the prescribed temperature field
+    pts = tn.tn_mesh_lateral_points(m, 0)
+    N, P, n_r = info["N"], info["pitch"], info["n_r"]
+    radii = R_IN + ((R_OUT - R_IN) * np.arange(n_r)) / (n_r - 1)
+    lat = np.zeros((10, N + 1, P, 3))
+    lat[:, :, : N + 1] = pts
+    xyz = (radii[None, :, None, None, None] * lat[:, None]).reshape(-1, 3)
+    T = inputs.temperature(xyz, R_IN, R_OUT)
+    noise = inputs.normal(n, args.seed + 100 * rank, 0.01)
+    T = np.where(valid.numpy(), T + noise[np.maximum(canon.numpy(), 0)], 0.0)
+    Td = torch.tensor(T, device=dev)
+    tn.tn_set_temperature(m, Td, LAW["E"], LAW["jump_r"], LAW["jump_factor"])
+
+    def field(seed, size, can=None):
+        v = inputs.normal(size, seed)
+        if can is not None:
+            v = np.where(can >= 0, v[np.maximum(can, 0)], 0.0)
+        return torch.tensor(v, device=dev)
+
+    pcanon = tn.tn_mesh_canonical_index(m, 1)
+    u = [field(args.seed + 10 * rank + c, n, canon.numpy()) for c in range(3)]
+    p = field(args.seed + 10 * rank + 5, pinfo["n_layout"], pcanon)
+    yA = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
+    yBT = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
+    dA = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
+    q = torch.empty(pinfo["n_layout"], device=dev, dtype=torch.float64)
+
+    ev = {k: [] for k in ("A", "B", "BT", "diag")}
+
+    def step(record=False):
+        for name, fn in (("A", lambda: tn.tn_apply_A(m, 0, u, yA, st)), ("B", lambda: tn.tn_apply_B(m, 0, u, q, st)),
+                         ("BT", lambda: tn.tn_apply_BT(m, 0, p, yBT, st)), ("diag", lambda: tn.tn_diag_A(m, 0, dA, st))):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                fn()
+                e1.record(st)
+                ev[name].append((e0, e1))
+            else:
+                fn()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = tt.item()
+        dist.barrier()
+    per_op = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in ev.items()}
+
+    nv, npr, ndof = dof_counts(args.level, args.n_r)
+    value = world * ndof * args.steps / (ms / 1e3) / 1e9
+
+    # ---- end to end through the public API: pinned host inputs -> device -> step -> host outputs
+    hu = [t.cpu().pin_memory() for t in u]
+    hp = p.cpu().pin_memory()
+    outs = yA + [q] + yBT + dA
+    hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+    h2d = sum(t.numel() * t.element_size() for t in hu) + hp.numel() * hp.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in hout)
+
+    def e2e_step():
+        for a, b in zip(u, hu):
+            a.copy_(b, non_blocking=True)
+        p.copy_(hp, non_blocking=True)
+        step()
+        for a, b in zip(hout, outs):
+            a.copy_(b, non_blocking=True)
+
+    e2e_steps = max(2, min(args.steps, 10))
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(st)
+    for _ in range(e2e_steps):
+        e2e_step()
+    c1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = c0.elapsed_time(c1)
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = tt.item()
+    e2e_value = world * ndof * e2e_steps / (e2e_ms / 1e3) / 1e9
+
+    if rank == 0:
+        cells = 10 * 4 ** args.level * (args.n_r - 1)
+        a_flops = A_FLOPS_PER_CELL * cells
+        achieved = a_flops / (per_op["A"] / 1e3) / 1e12
+        line = {
+            "metric": "Stokes-apply GDoF/s (FP64 A+B+BT+diag step)", "value": value, "unit": "GDoF/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.level, args.n_r), "velocity_dofs": nv, "pressure_dofs": npr,
+                       "dofs_per_step": ndof, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (3 x %.0f MB velocity components)" % (n * 8 / 1e6)},
+            "per_op_ms": per_op,
+            "roofline": {"bound": "alu", "kernel": "A apply (tile kernel + interface sum)", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "peak_note": "FP64 DFMA peak from unit counts x max clock",
+                         "hbm_frac_of_measured": (64.0 * cells) / (per_op["A"] / 1e3) / 6771.8e9},
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": 11 * args.steps,
+        }
+        if world == 1:
+            dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
+            line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                                    "sample": desc, "seconds": dt}
+        print(json.dumps(line))
+    tn.tn_mesh_destroy(m)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -216,14 +216,16 @@ def diag_pressure_mass(mesh, Pp, eta):
 
 
 # ----------------------------------------------------------------------------- diagonal of A
-def diag_A_constrained(mesh, eta, P, div_term=True, chunk=50000):
+def diag_A_constrained(mesh, eta, P, div_term=True, chunk=50000, wedges=None):
     """Diagonal of P A P + (I - P), shape (3, n), from the 3x3 node blocks of A.
 
     The node block A_jj is accumulated element by element from the explicit
-    element matrices; the constrained block is P_j A_jj P_j + I - P_j."""
+    element matrices (over the given wedges, all if None); the constrained
+    block is P_j A_jj P_j + I - P_j."""
     n = mesh.n_nodes
     blocks = np.zeros((n, 3, 3))
-    for ch in _chunks(np.arange(mesh.n_wedges), chunk):
+    ids = np.arange(mesh.n_wedges) if wedges is None else np.asarray(wedges)
+    for ch in _chunks(ids, chunk):
         nodes = mesh.wedge_nodes(ch)
         grad, V = wedge_geometry(mesh, ch)
         Ae = viscous_element_matrix(grad, V, eta[ch], div_term).reshape(-1, 6, 3, 6, 3)
