@@ -186,6 +186,82 @@ tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int app
  * (Eq. stokes with the full temperature); f_dev[3] doubles.  Stream-ordered. */
 tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double* const* f_dev, void* stream);
 
+
+/* ------------------------------------------------------------------------------------------
+ * Geometric multigrid (Sec. 7): V-cycle over the mesh hierarchy, two pre- and two
+ * post-smoothing steps of a degree-2 Chebyshev polynomial in D^-1 K per level (D = diag of
+ * the constrained operator K = P A P + I - P), coarsest level solved by conjugate gradients.
+ *
+ * Chebyshev step (Chebyshev acceleration, Saad, Iterative Methods for Sparse Linear Systems,
+ * Alg. 12.1, two iterations) on the interval [cheb_lo, cheb_hi] x lambda, lambda the estimate
+ * of the largest eigenvalue of D^-1 K from power_iters power iterations
+ * (v <- D^-1 K v / ||D^-1 K v||, lambda = ||D^-1 K v||, Euclidean over unique nodes).
+ * The level-0 start vector is v0_dev (3 arrays) or, if NULL, SplitMix64 draws keyed by
+ * (seed, canonical layout index, component); level h+1 starts from the restriction of level h's.
+ * Coarsest level: Jacobi-preconditioned CG from 0 until (r, D^-1 r) <= coarse_rtol^2 (r0, D^-1 r0)
+ * or coarse_max_iters; with free-slip on both surfaces the rigid rotations (an exact null space)
+ * are projected out of its right-hand side and solution.
+ * Transfers: restriction P^T then the coarse boundary projector; prolongation P then the fine
+ * boundary projector (tn_restrict / tn_prolong with apply_bc = 1).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+  int pre_smooth, post_smooth; /* Chebyshev steps per level (2, 2) */
+  int cheb_degree;             /* must be 2 */
+  double cheb_lo, cheb_hi;     /* interval factors (0.1, 1.1) */
+  int power_iters;             /* 15 */
+  int coarse_max_iters;        /* 50 */
+  double coarse_rtol;          /* 1e-3 (0: always run coarse_max_iters) */
+  int levels;                  /* levels used (0: whole hierarchy) */
+  uint64_t seed;               /* internal power-iteration start vector */
+} tn_mg_opts;
+
+tn_status tn_mg_default_opts(tn_mg_opts* opts);
+
+/* Diagonals, eigenvalue estimates and workspaces for precision prec (TN_F64 / TN_F32).
+ * Needs the viscosity; synchronises the stream; allocates device workspaces owned by the mesh.
+ * tn_set_viscosity / tn_set_temperature invalidate it (the next V-cycle or solve re-runs it). */
+tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const void* const* v0_dev, void* stream);
+/* lambda estimate of level h after tn_mg_setup (host). */
+tn_status tn_mg_lambda(const tn_mesh* mesh, tn_prec prec, int level, double* lambda);
+/* z = V(r): one V-cycle from zero on level 0 (3 arrays each, node layout of level 0, type by
+ * prec).  Runs tn_mg_setup with the last options if needed.  Stream-ordered, no host sync. */
+tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r_dev, void* const* z_dev, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Stokes solve (Sec. 7): FGMRES(restart) (Saad 1993) with right preconditioning by the block
+ * upper-triangular P^-1 = [[A^-1, -A^-1 B^T S^-1], [0, S^-1]] of Eq. (block-precond),
+ * S^-1 = -diag(M_1/eta)^-1 (Eq. pmass), A^-1 = one V-cycle; classical Gram-Schmidt with one
+ * re-orthogonalisation; inner products Euclidean over unique nodes (velocity components and
+ * pressure).  The rigid rotations are projected out of the returned velocity when both
+ * surfaces are free-slip; the pressure mean is not projected (under free-slip the constant
+ * pressure is not an exact null vector of the discrete system).
+ * Mode TN_SOLVE_MIXED: FP64 iterative refinement x += ||r|| d with r = b - K x in FP64 and d
+ * from an FP32 FGMRES / FP32 V-cycle solve of K d = r / ||r|| to inner_rtol.
+ * u, p are outputs (zero initial guess); g may be NULL (zero).  Synchronous.
+ * Returns TN_ENOTCONVERGED if ||b - K x|| / ||b|| > rtol on return (stats still filled).
+ * ---------------------------------------------------------------------------------------- */
+typedef enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED = 1 } tn_solve_mode;
+typedef struct {
+  double rtol;          /* 1e-8 relative residual */
+  int restart;          /* 10 (1..11) */
+  int max_iters;        /* total FGMRES iterations (1000) */
+  int mode;             /* tn_solve_mode */
+  double inner_rtol;    /* mixed: inner relative tolerance (1e-3) */
+  int inner_max_iters;  /* mixed: iterations per inner solve (100) */
+  int max_refinements;  /* mixed: outer steps (30) */
+} tn_solve_opts;
+typedef struct {
+  int iterations;       /* FGMRES iterations (summed over inner solves in mixed mode) */
+  int refinements;      /* mixed mode outer steps */
+  double rel_residual;  /* ||b - K x|| / ||b||, recomputed in FP64 at the end */
+  double seconds;       /* host wall time of the call */
+  int converged;
+} tn_solve_stats;
+
+tn_status tn_solve_default_opts(tn_solve_opts* opts);
+tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f_dev, const double* g_dev,
+                          double* const* u_dev, double* p_dev, tn_solve_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,145 @@
+"""Oracle geometric multigrid: the V-cycle of Sec. 7 on explicitly assembled level operators.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Algorithm (the paper gives the structure: two pre- and two post-smoothing steps of a
+degree-2 Chebyshev smoother per level, conjugate gradients on the coarsest level; the
+remaining choices are readings):
+* level operators K_h = P_h A_h P_h + (I - P_h), re-discretised with the coarse viscosity
+  (mean of the 8 children); D_h = diag(K_h);
+* transfers: prolongation P_h T_h (nested iso-interpolation, then the fine boundary
+  projector), restriction P_{h+1} T_h^T;
+* Chebyshev acceleration (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1) with
+  D^-1 preconditioning, two iterations per smoothing step, on [lo, hi] x lambda_h;
+  lambda_h from power iterations on D^-1 K_h started from the restricted start vector;
+* coarsest level: Jacobi-preconditioned CG from zero, stopping when
+  (r, D^-1 r) <= rtol^2 (r0, D^-1 r0) or after max_iters; with free-slip on both surfaces
+  the rigid rotations are projected out of its right-hand side and solution.
+Vectors are component-major flat arrays (3 n_nodes).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from . import operators as O
+from .fields import coarsen_viscosity
+from .mesh import ShellMesh
+
+
+def vec_prolongation(fine, coarse):
+    """Nested interpolation for 3-component fields in component-major numbering."""
+    T = O.prolongation(fine, coarse)
+    return sp.block_diag([T, T, T], format="csr")
+
+
+def rotation_basis(mesh):
+    """The three rigid rotations e_i x x as columns (3 n x 3)."""
+    X = mesh.node_xyz()
+    cols = []
+    for om in np.eye(3):
+        cols.append(np.cross(om[None, :], X).T.ravel())
+    return np.stack(cols, axis=1)
+
+
+class Hierarchy:
+    def __init__(self, level, n_r, r_in, r_out, eta0, bc=(O.FREE, O.FREE), nlev=None, div_term=True,
+                 lo=0.1, hi=1.1, power_iters=15, pre=2, post=2, coarse_max_iters=50, coarse_rtol=1e-3):
+        self.meshes = [ShellMesh(level, n_r, r_in, r_out)]
+        while True:
+            m = self.meshes[-1]
+            if m.level < 2 or (m.n_r - 1) % 2 != 0 or m.n_r < 3:
+                break
+            self.meshes.append(ShellMesh(m.level - 1, (m.n_r - 1) // 2 + 1, r_in, r_out))
+        if nlev is not None:
+            self.meshes = self.meshes[:nlev]
+        self.nlev = len(self.meshes)
+        self.bc = bc
+        self.eta = [np.asarray(eta0, dtype=np.float64)]
+        for h in range(1, self.nlev):
+            self.eta.append(coarsen_viscosity(self.meshes[h - 1], self.meshes[h], self.eta[h - 1]))
+        self.Pb = [O.projector_matrix(O.boundary_projectors(m, bc)) for m in self.meshes]
+        self.K = [O.constrain_A(O.assemble_A(m, e, div_term), Pb)
+                  for m, e, Pb in zip(self.meshes, self.eta, self.Pb)]
+        self.invD = [1.0 / K.diagonal() for K in self.K]
+        self.T = [vec_prolongation(self.meshes[h], self.meshes[h + 1]) for h in range(self.nlev - 1)]
+        self.lo, self.hi, self.power_iters = lo, hi, power_iters
+        self.pre, self.post = pre, post
+        self.coarse_max_iters, self.coarse_rtol = coarse_max_iters, coarse_rtol
+        self.singular = bc == (O.FREE, O.FREE)
+        R = rotation_basis(self.meshes[-1])
+        self.rotQ = np.linalg.qr(R)[0] if self.singular else None
+        self.lam = [None] * self.nlev
+
+    def prolong(self, h, xc):
+        return self.Pb[h] @ (self.T[h] @ xc)
+
+    def restrict(self, h, xf):
+        return self.Pb[h + 1] @ (self.T[h].T @ xf)
+
+    def setup(self, v0):
+        """Power iterations on D^-1 K_h from v0 (level 0) and its restrictions."""
+        v = np.asarray(v0, dtype=np.float64)
+        for h in range(self.nlev):
+            if h > 0:
+                v = self.restrict(h - 1, v)
+            if h == self.nlev - 1:
+                break
+            w = v / np.linalg.norm(v)
+            lam = None
+            for _ in range(self.power_iters):
+                z = self.invD[h] * (self.K[h] @ w)
+                lam = np.linalg.norm(z)
+                w = z / lam
+            self.lam[h] = lam
+
+    def chebyshev(self, h, x, b, zero_x):
+        a, bb = self.lo * self.lam[h], self.hi * self.lam[h]
+        theta, delta = 0.5 * (bb + a), 0.5 * (bb - a)
+        sigma = theta / delta
+        rho0 = 1.0 / sigma
+        rho1 = 1.0 / (2.0 * sigma - rho0)
+        r = b.copy() if zero_x else b - self.K[h] @ x
+        d = self.invD[h] * r / theta
+        x = d.copy() if zero_x else x + d
+        r = r - self.K[h] @ d
+        d = rho1 * rho0 * d + (2.0 * rho1 / delta) * (self.invD[h] * r)
+        return x + d
+
+    def coarse_cg(self, b):
+        h = self.nlev - 1
+        K, invD = self.K[h], self.invD[h]
+        if self.singular:
+            b = b - self.rotQ @ (self.rotQ.T @ b)
+        x = np.zeros_like(b)
+        r = b.copy()
+        z = invD * r
+        p = z.copy()
+        rz0 = rz = r @ z
+        if rz0 > 0:
+            for it in range(self.coarse_max_iters):
+                q = K @ p
+                alpha = rz / (p @ q)
+                x = x + alpha * p
+                r = r - alpha * q
+                z = invD * r
+                rzn = r @ z
+                beta = rzn / rz
+                rz = rzn
+                if not (rzn > self.coarse_rtol ** 2 * rz0) or it == self.coarse_max_iters - 1:
+                    break
+                p = z + beta * p
+        if self.singular:
+            x = x - self.rotQ @ (self.rotQ.T @ x)
+        return x
+
+    def vcycle(self, b, h=0):
+        if h == self.nlev - 1:
+            return self.coarse_cg(b)
+        x = np.zeros_like(b)
+        for s in range(self.pre):
+            x = self.chebyshev(h, x, b, s == 0)
+        r = b - self.K[h] @ x
+        xc = self.vcycle(self.restrict(h, r), h + 1)
+        x = x + self.prolong(h, xc)
+        for s in range(self.post):
+            x = self.chebyshev(h, x, b, False)
+        return x

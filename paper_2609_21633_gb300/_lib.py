@@ -40,6 +40,27 @@ class tn_visc_law(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("jump_r", ctypes.c_double), ("jump_factor", ctypes.c_double)]
 
 
+class tn_mg_opts(ctypes.Structure):
+    _fields_ = [("pre_smooth", ctypes.c_int), ("post_smooth", ctypes.c_int), ("cheb_degree", ctypes.c_int),
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double), ("power_iters", ctypes.c_int),
+                ("coarse_max_iters", ctypes.c_int), ("coarse_rtol", ctypes.c_double), ("levels", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class tn_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("mode", ctypes.c_int), ("inner_rtol", ctypes.c_double), ("inner_max_iters", ctypes.c_int),
+                ("max_refinements", ctypes.c_int)]
+
+
+class tn_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+TN_SOLVE_F64, TN_SOLVE_MIXED = 0, 1
+
+
 _lib = None
 P = ctypes.c_void_p
 PP = ctypes.POINTER(ctypes.c_void_p)
@@ -62,6 +83,13 @@ _SIGS = {
     "tn_prolong": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_restrict": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_buoyancy": ([P, P, ctypes.c_double, PP, P], ctypes.c_int),
+    "tn_mg_default_opts": ([ctypes.POINTER(tn_mg_opts)], ctypes.c_int),
+    "tn_mg_setup": ([P, ctypes.c_int, ctypes.POINTER(tn_mg_opts), PP, P], ctypes.c_int),
+    "tn_mg_lambda": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "tn_vcycle": ([P, ctypes.c_int, PP, PP, P], ctypes.c_int),
+    "tn_solve_default_opts": ([ctypes.POINTER(tn_solve_opts)], ctypes.c_int),
+    "tn_stokes_solve": ([P, ctypes.POINTER(tn_solve_opts), PP, P, PP, P, ctypes.POINTER(tn_solve_stats), P],
+                        ctypes.c_int),
 }
 
 
@@ -196,6 +224,57 @@ def tn_restrict(mesh, level, fine, coarse, apply_bc=False, stream=None):
 def tn_buoyancy(mesh, T, Ra, f, stream=None):
     pf, _a = _ptrs(f)
     _check(lib().tn_buoyancy(mesh, _ptr(T), Ra, pf, _stream(stream)))
+
+
+def tn_mg_default_opts(**kw):
+    o = tn_mg_opts()
+    _check(lib().tn_mg_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tn_mg_setup(mesh, dtype, opts=None, v0=None, stream=None):
+    import torch
+    prec = _prec(dtype if isinstance(dtype, torch.dtype) else torch.float64)
+    o = opts if opts is not None else tn_mg_default_opts()
+    if v0 is not None:
+        pv, _a = _ptrs(v0)
+    else:
+        pv, _a = None, None
+    _check(lib().tn_mg_setup(mesh, prec, ctypes.byref(o), pv, _stream(stream)))
+
+
+def tn_mg_lambda(mesh, dtype, level):
+    out = ctypes.c_double()
+    _check(lib().tn_mg_lambda(mesh, _prec(dtype), level, ctypes.byref(out)))
+    return out.value
+
+
+def tn_vcycle(mesh, r, z, stream=None):
+    pr, _a = _ptrs(r)
+    pz, _b = _ptrs(z)
+    _check(lib().tn_vcycle(mesh, _prec(r[0].dtype), pr, pz, _stream(stream)))
+
+
+def tn_solve_default_opts(**kw):
+    o = tn_solve_opts()
+    _check(lib().tn_solve_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tn_stokes_solve(mesh, f, g, u, p, opts=None, stream=None, check=True):
+    """Returns the stats as a dict; raises on failure (TN_ENOTCONVERGED only if check)."""
+    o = opts if opts is not None else tn_solve_default_opts()
+    st = tn_solve_stats()
+    pf, _a = _ptrs(f)
+    pu, _b = _ptrs(u)
+    status = lib().tn_stokes_solve(mesh, ctypes.byref(o), pf, _ptr(g), pu, _ptr(p), ctypes.byref(st), _stream(stream))
+    if status != TN_OK and (check or status != TN_ENOTCONVERGED):
+        _check(status)
+    return {f: getattr(st, f) for f, _ in tn_solve_stats._fields_}
 
 
 def header_entry_points():

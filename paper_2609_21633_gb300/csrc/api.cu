@@ -41,8 +41,8 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 }
 
 void free_level(Level& L) {
-  void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off,
-                  L.grp_s64, L.grp_s32, L.owned, L.eta64, L.eta32, L.scr64, L.scr32};
+  void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
+                  L.grp_s32, L.owned, L.eta64, L.eta32, L.scr64, L.scr32, L.wmask, L.rad64, L.rad32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -147,6 +147,31 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
     chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
     chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
     chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));
+    {
+      // weight mask (canonical copies), radii, rotation Gram matrix over unique nodes
+      std::vector<uint8_t> wm((size_t)L.n_layout, 0);
+      const int M = L.N + 1;
+      double G[3][3] = {};
+      for (int d = 0; d < 10; ++d)
+        for (int i = 0; i <= L.N; ++i)
+          for (int j = 0; j <= L.N; ++j) {
+            const int64_t lat = ((int64_t)d * M + i) * L.P + j;
+            if (!owned[lat]) continue;
+            const double* s = &L.lat_xyz[(((size_t)d * M + i) * M + j) * 3];
+            for (int k = 0; k < L.n_r; ++k) {
+              wm[(size_t)(d * L.diamond_stride + k * L.layer_stride + (int64_t)i * L.P + j)] = 1;
+              const double r2 = L.radii[k] * L.radii[k];
+              for (int a2 = 0; a2 < 3; ++a2)
+                for (int b2 = 0; b2 < 3; ++b2) G[a2][b2] += r2 * ((a2 == b2 ? 1.0 : 0.0) - s[a2] * s[b2]);
+            }
+          }
+      std::memcpy(L.inertia, G, sizeof(G));
+      chk(upload(L.wmask, wm));
+      chk(upload(L.rad64, L.radii));
+      chk(upload(L.rad32, to_f32(L.radii)));
+    }
+    chk(cudaMemset(L.scr64, 0, sizeof(double) * L.n_layout));
+    chk(cudaMemset(L.scr32, 0, sizeof(float) * L.n_layout));
     if (e != cudaSuccess) {
       tn_mesh_destroy(m);
       set_error(std::string("tn_mesh_create: device allocation failed: ") + cudaGetErrorString(e));
@@ -163,6 +188,8 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
 
 tn_status tn_mesh_destroy(tn_mesh* mesh) {
   if (!mesh) return TN_OK;
+  mg_free(mesh->mg);
+  mesh->mg = nullptr;
   for (auto& L : mesh->lv) free_level(L);
   delete mesh;
   return TN_OK;
@@ -223,6 +250,7 @@ static tn_status finish_eta(tn_mesh* m, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "viscosity conversion");
   }
   m->eta_set = true;
+  mg_invalidate(m);
   return TN_OK;
 }
 

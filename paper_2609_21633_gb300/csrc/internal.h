@@ -45,12 +45,33 @@ struct Level {
   // Scratch scalar field in this level's node layout (B / B^T intermediate).
   double* scr64 = nullptr;
   float* scr32 = nullptr;
+  // Weight mask over the node layout: 1 on the canonical copy of every node, 0 on other
+  // copies and on padding (Euclidean inner products over unique nodes).
+  uint8_t* wmask = nullptr;
+  double* rad64 = nullptr;  // node radii r_k
+  float* rad32 = nullptr;
+  double inertia[3][3] = {};  // sum over unique nodes of |x|^2 I - x x^T (rotation Gram matrix)
 };
+
+// Index sizes handed to kernels.
+struct Dims {
+  int N, n_r, P;
+  int64_t layer_stride, diamond_stride, n_tri, n_lat_layout;
+};
+inline Dims dims(const Level& L) {
+  return Dims{L.N, L.n_r, L.P, L.layer_stride, L.diamond_stride, L.n_tri, L.n_lat_layout};
+}
 
 }  // namespace tn
 
+namespace tn {
+struct MGState;
+void mg_free(MGState*);
+}
+
 struct tn_mesh {
   std::vector<tn::Level> lv;
+  tn::MGState* mg = nullptr;
   int bc_in = TN_BC_FREESLIP, bc_out = TN_BC_FREESLIP, div_term = 1;
   bool eta_set = false;
   int device = 0;
@@ -67,13 +88,15 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
                       std::string& err);
 
 void set_error(const std::string& msg);
+void mg_invalidate(tn_mesh* mesh);
 
 // ---- kernel launchers (kernels.cu) --------------------------------------------------------
 struct BC {
   int in, out;  // TN_BC_* at node layer 0 and n_r - 1
 };
 template <typename T>
-cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st);
+cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
+                           const int* skip = nullptr);
 template <typename T>
 cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st);
 template <typename T>
@@ -86,7 +109,7 @@ cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t
 // 2: + diag(I - P) at boundary layers.
 template <typename T>
 cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* const* y, const T* const* u,
-                             cudaStream_t st);
+                             cudaStream_t st, const int* skip = nullptr);
 template <typename T>
 cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* c,
                            T* const* f, cudaStream_t st);

@@ -54,13 +54,6 @@ struct Tab<float> {
   static const float* eta(const Level& L) { return L.eta32; }
 };
 
-struct Dims {
-  int N, n_r, P;
-  int64_t layer_stride, diamond_stride, n_tri, n_lat_layout;
-};
-Dims dims(const Level& L) {
-  return Dims{L.N, L.n_r, L.P, L.layer_stride, L.diamond_stride, L.n_tri, L.n_lat_layout};
-}
 
 // ------------------------------------------------------------------------------------ element ops
 // Viscous block: Eq. (epsq) then Eq. (localapply) at q_c.
@@ -168,9 +161,10 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1))
     k_tile(Dims D, Op op, const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
            T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
            const T* __restrict__ lay, const T* __restrict__ eta, const T* __restrict__ svec, int bc_in, int bc_out,
-           int kc) {
+           int kc, const int* __restrict__ skip) {
   constexpr int NIN = Op::NIN, NOUT = Op::NOUT, W = TT + 1;
   __shared__ T sm[4][NOUT][W][W];
+  if (skip && *skip) return;  // device-side early exit (uniform over the grid)
   const int N = D.N, n_r = D.n_r, P = D.P;
   const int ntj = N / TT;
   const int i0 = (blockIdx.x / ntj) * TT, j0 = (blockIdx.x % ntj) * TT;
@@ -325,7 +319,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1))
 
 template <typename T, typename Op, int FLAGS>
 cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const T* eta,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* skip = nullptr) {
   Dims D = dims(L);
   const int tt = L.N >= TILE ? TILE : L.N;
   const int ntiles = (L.N / tt) * (L.N / tt);
@@ -344,7 +338,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
 #define TN_TILE_CASE(TTv)                                                                                     \
   case TTv:                                                                                                   \
     k_tile<T, Op, TTv, FLAGS><<<grid, (TTv + 1) * (TTv + 1), 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, \
-                                                                       geo, lay, eta, sv, bc.in, bc.out, kc); \
+                                                                       geo, lay, eta, sv, bc.in, bc.out, kc, skip); \
     break;
   switch (tt) {
     TN_TILE_CASE(16)
@@ -364,7 +358,8 @@ template <typename T>
 __global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, const int64_t* __restrict__ goff,
                             const T* __restrict__ gs, int ncomp, int mode, T* y0, T* y1, T* y2,
                             const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
-                            int bc_in, int bc_out) {
+                            int bc_in, int bc_out, const int* __restrict__ skip) {
+  if (skip && *skip) return;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (gid >= (int64_t)n_groups * D.n_r) return;
   const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
@@ -704,11 +699,12 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 
 // ---------------------------------------------------------------------------------------- launchers
 template <typename T>
-cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st) {
+cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
+                           const int* skip) {
   OpA<T> op{div_term};
-  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, Tab<T>::eta(L), st);
+  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, Tab<T>::eta(L), st, skip);
   if (e != cudaSuccess) return e;
-  return launch_interface<T>(L, bc, 3, 1, y, u, st);
+  return launch_interface<T>(L, bc, 3, 1, y, u, st, skip);
 }
 
 template <typename T>
@@ -750,7 +746,7 @@ cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t
 
 template <typename T>
 cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* const* y, const T* const* u,
-                             cudaStream_t st) {
+                             cudaStream_t st, const int* skip) {
   const int64_t n = (int64_t)L.n_groups * L.n_r;
   if (n == 0) return cudaSuccess;
   T* y1 = ncomp > 1 ? y[1] : y[0];
@@ -759,7 +755,7 @@ cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* cons
   const T* u1 = u ? u[1] : nullptr;
   const T* u2 = u ? u[2] : nullptr;
   k_interface<T><<<nblk(n, 128), 128, 0, st>>>(dims(L), L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), ncomp, mode,
-                                               y[0], y1, y2, u0, u1, u2, bc.in, bc.out);
+                                               y[0], y1, y2, u0, u1, u2, bc.in, bc.out, skip);
   return cudaGetLastError();
 }
 
@@ -819,12 +815,14 @@ cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, d
 }
 
 #define TN_INST(T)                                                                                               \
-  template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t);      \
+  template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t,       \
+                                         const int*);                                                            \
   template cudaError_t launch_div_fine<T>(const Level&, BC, const T* const*, T*, cudaStream_t);                 \
   template cudaError_t launch_grad_fine<T>(const Level&, BC, const T*, T* const*, cudaStream_t);                \
   template cudaError_t launch_diag_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                        \
   template cudaError_t launch_diag_pmass<T>(const Level&, const Level&, T*, cudaStream_t);                      \
-  template cudaError_t launch_interface<T>(const Level&, BC, int, int, T* const*, const T* const*, cudaStream_t); \
+  template cudaError_t launch_interface<T>(const Level&, BC, int, int, T* const*, const T* const*, cudaStream_t,  \
+                                           const int*);                                                          \
   template cudaError_t launch_prolong<T>(const Level&, const Level&, BC, int, int, const T* const*, T* const*,   \
                                          cudaStream_t);                                                         \
   template cudaError_t launch_restrict<T>(const Level&, const Level&, BC, int, int, const T* const*, T* const*,  \

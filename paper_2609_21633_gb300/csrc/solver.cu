@@ -1,0 +1,1246 @@
+// Solver layer: deterministic reductions, Chebyshev / geometric-multigrid V-cycle and the
+// FGMRES Stokes solve with the block-triangular preconditioner (Sec. 7, Eq. block-precond,
+// Eq. pmass), in FP64 or as FP32 inner solves inside FP64 iterative refinement.
+//
+// Orchestration is host C++ enqueueing kernels on one stream.  Inner products always
+// accumulate in FP64 over unique nodes (the canonical copy of every diamond-edge node) and
+// reduce in a fixed order, so every result is bitwise reproducible.  The coarsest-level
+// conjugate-gradient loop keeps its scalars on the device and stops through a device flag
+// (later kernels of a converged loop return immediately), so a V-cycle needs no host sync.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace tn {
+
+namespace {
+
+constexpr int RG = 304;   // blocks of a reduction (fixed: the summation order never changes)
+constexpr int RB = 256;   // threads per reduction block
+constexpr int MAXV = 12;  // vectors per multi-dot / multi-axpy
+constexpr int EB = 256;   // elementwise block size
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + EB - 1) / EB); }
+
+template <typename T>
+struct Ptr4 {
+  const T* c[4];
+};
+template <typename T>
+struct MPtr4 {
+  T* c[4];
+};
+template <typename T>
+struct DotArgs {
+  const T* x[MAXV][4];
+  const T* y[4];
+};
+template <typename T>
+struct AxpyArgs {
+  const T* x[MAXV][4];
+  T* y[4];
+};
+
+// ------------------------------------------------------------------------------------- reductions
+// part[v * RG + block] = sum over masked entries of sum_c x[v][c] y[c]
+template <typename T>
+__global__ void __launch_bounds__(RB) k_dots(int64_t n, const uint8_t* __restrict__ mask, int nvec, int ncomp,
+                                             DotArgs<T> a, double* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  // FP64 accumulators; products are formed in T and, for FP32 vectors, summed in FP32 over
+  // at most 8 consecutive elements of a thread before they are added in FP64.
+  double acc[MAXV];
+  T pacc[MAXV];
+#pragma unroll
+  for (int v = 0; v < MAXV; ++v) acc[v] = 0.0, pacc[v] = (T)0;
+  int cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)RG * RB) {
+    if (!mask[i]) continue;
+    T yv[4];
+    for (int c = 0; c < ncomp; ++c) yv[c] = a.y[c][i];
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) {
+      if (v < nvec) {
+        T s = (T)0;
+        for (int c = 0; c < ncomp; ++c) s += a.x[v][c][i] * yv[c];
+        if (sizeof(T) == 8) acc[v] += (double)s;
+        else pacc[v] += s;
+      }
+    }
+    if (sizeof(T) != 8 && ++cnt == 8) {
+#pragma unroll
+      for (int v = 0; v < MAXV; ++v) acc[v] += (double)pacc[v], pacc[v] = (T)0;
+      cnt = 0;
+    }
+  }
+  if (sizeof(T) != 8) {
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) acc[v] += (double)pacc[v];
+  }
+  __shared__ double sh[RB / 32][MAXV];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < MAXV; ++v) {
+    if (v < nvec) {
+      double s = acc[v];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) sh[wid][v] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nvec) {
+    double s = 0.0;
+    for (int w = 0; w < RB / 32; ++w) s += sh[w][threadIdx.x];
+    part[threadIdx.x * RG + blockIdx.x] = s;
+  }
+}
+
+// out[v] = sum_b part0[v RG + b] (+ part1[v RG + b]) in a fixed order; block per vector.
+__global__ void k_dots_final(int nvec, const double* __restrict__ part0, const double* __restrict__ part1,
+                             double* __restrict__ out, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int v = blockIdx.x;
+  __shared__ double sh[RB];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < RG; b += RB) {
+    double t = part0[v * RG + b];
+    if (part1) t += part1[v * RG + b];
+    s += t;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = RB / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[v] = sh[0];
+}
+
+// Angular momentum sum over unique nodes of x cross u (three dots with the rigid rotations
+// e_i x x, since <u, e_i x x> = e_i . (x cross u)).
+template <typename T>
+__global__ void __launch_bounds__(RB) k_angmom(Dims D, const uint8_t* __restrict__ mask, const T* __restrict__ svec,
+                                               const T* __restrict__ rad, Ptr4<T> u, double* __restrict__ part,
+                                               const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t n = 10 * D.diamond_stride;
+  double acc[3] = {0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)RB + threadIdx.x; i < n; i += (int64_t)RG * RB) {
+    if (!mask[i]) continue;
+    const int64_t d = i / D.diamond_stride, rem = i % D.diamond_stride;
+    const int k = (int)(rem / D.layer_stride);
+    const int64_t lat = d * (int64_t)(D.N + 1) * D.P + rem % D.layer_stride;
+    const double r = rad[k];
+    const double x[3] = {r * svec[lat], r * svec[lat + D.n_lat_layout], r * svec[lat + 2 * D.n_lat_layout]};
+    const double w[3] = {u.c[0][i], u.c[1][i], u.c[2][i]};
+    acc[0] += x[1] * w[2] - x[2] * w[1];
+    acc[1] += x[2] * w[0] - x[0] * w[2];
+    acc[2] += x[0] * w[1] - x[1] * w[0];
+  }
+  __shared__ double sh[RB / 32][3];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int v = 0; v < 3; ++v) {
+    double s = acc[v];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[wid][v] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < RB / 32; ++w) s += sh[w][threadIdx.x];
+    part[threadIdx.x * RG + blockIdx.x] = s;
+  }
+}
+
+// u -= (Ginv L) x x at every layout entry (L = angular momentum in Lm[0..2]).
+struct M33 {
+  double a[3][3];
+};
+template <typename T>
+__global__ void k_sub_rotation(Dims D, const T* __restrict__ svec, const T* __restrict__ rad, MPtr4<T> u,
+                               const double* __restrict__ Lm, M33 Ginv, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  const int64_t n = 10 * D.diamond_stride;
+  if (i >= n) return;
+  const int64_t d = i / D.diamond_stride, rem = i % D.diamond_stride;
+  const int j = (int)(rem % D.P);
+  if (j > D.N) return;
+  const int k = (int)(rem / D.layer_stride);
+  const int64_t lat = d * (int64_t)(D.N + 1) * D.P + rem % D.layer_stride;
+  double w[3];
+  for (int a = 0; a < 3; ++a) w[a] = Ginv.a[a][0] * Lm[0] + Ginv.a[a][1] * Lm[1] + Ginv.a[a][2] * Lm[2];
+  const double r = rad[k];
+  const double x[3] = {r * svec[lat], r * svec[lat + D.n_lat_layout], r * svec[lat + 2 * D.n_lat_layout]};
+  u.c[0][i] -= (T)(w[1] * x[2] - w[2] * x[1]);
+  u.c[1][i] -= (T)(w[2] * x[0] - w[0] * x[2]);
+  u.c[2][i] -= (T)(w[0] * x[1] - w[1] * x[0]);
+}
+
+// --------------------------------------------------------------------------------- elementwise
+// y[c] += sign * sum_v coef[v] x[v][c]  (coef on the device)
+template <typename T>
+__global__ void k_axpy_multi(int64_t n, int nvec, int ncomp, const double* __restrict__ coef, double sign,
+                             AxpyArgs<T> a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  T cf[MAXV];
+  for (int v = 0; v < nvec; ++v) cf[v] = (T)(sign * coef[v]);
+  for (int c = 0; c < ncomp; ++c) {
+    T s = a.y[c][i];
+    for (int v = 0; v < nvec; ++v) s += cf[v] * a.x[v][c][i];
+    a.y[c][i] = s;
+  }
+}
+
+// y[c] = alpha x[c] + beta y[c] with host scalars
+template <typename T>
+__global__ void k_axpby(int64_t n, int ncomp, double alpha, Ptr4<T> x, double beta, MPtr4<T> y) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T a = (T)alpha, b = (T)beta;
+  for (int c = 0; c < ncomp; ++c) {
+    const T xv = alpha != 0.0 ? a * x.c[c][i] : (T)0;
+    const T yv = beta != 0.0 ? b * y.c[c][i] : (T)0;
+    y.c[c][i] = xv + yv;
+  }
+}
+
+// y[c] = x[c] * s, s = sqrt(1 / S[0]) (unit-normalise by a device squared norm)
+template <typename T>
+__global__ void k_normalize(int64_t n, int ncomp, Ptr4<T> x, MPtr4<T> y, const double* __restrict__ nrm2) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T s = (T)(1.0 / sqrt(nrm2[0]));
+  for (int c = 0; c < ncomp; ++c) y.c[c][i] = x.c[c][i] * s;
+}
+
+// y = inv * x  (Jacobi), componentwise
+template <typename T>
+__global__ void k_mul(int64_t n, int ncomp, Ptr4<T> inv, Ptr4<T> x, MPtr4<T> y) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < ncomp; ++c) y.c[c][i] = inv.c[c][i] * x.c[c][i];
+}
+
+template <typename T>
+__global__ void k_recip(int64_t n, const T* __restrict__ d, T* __restrict__ inv) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T v = d[i];
+  inv[i] = v != (T)0 ? (T)1 / v : (T)0;
+}
+
+// Chebyshev step, part 1 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1):
+// r = b - t (t = K x; zero_x: x = 0, t unused), d = D^-1 r / theta, x += d
+template <typename T>
+__global__ void k_cheb1(int64_t n, int zero_x, double inv_theta, Ptr4<T> b, Ptr4<T> t, Ptr4<T> invd, MPtr4<T> r,
+                        MPtr4<T> d, MPtr4<T> x) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < 3; ++c) {
+    const T rr = zero_x ? b.c[c][i] : b.c[c][i] - t.c[c][i];
+    const T dd = (T)inv_theta * (invd.c[c][i] * rr);
+    r.c[c][i] = rr;
+    d.c[c][i] = dd;
+    x.c[c][i] = zero_x ? dd : x.c[c][i] + dd;
+  }
+}
+// part 2: r -= t (t = K d), d = c1 d + c2 D^-1 r, x += d
+template <typename T>
+__global__ void k_cheb2(int64_t n, double c1, double c2, Ptr4<T> t, Ptr4<T> invd, MPtr4<T> r, MPtr4<T> d,
+                        MPtr4<T> x) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < 3; ++c) {
+    const T rr = r.c[c][i] - t.c[c][i];
+    const T dd = (T)c1 * d.c[c][i] + (T)c2 * (invd.c[c][i] * rr);
+    r.c[c][i] = rr;
+    d.c[c][i] = dd;
+    x.c[c][i] = x.c[c][i] + dd;
+  }
+}
+
+// ---- coarse CG (device scalars in S, stop flag) ----------------------------------------------
+enum { S_RZ0 = 0, S_RZ = 1, S_PQ = 2, S_RZN = 3, S_ALPHA = 4, S_BETA = 5, S_QR = 6, S_TMP = 8, S_L = 12, S_H = 16,
+       S_H2 = 32, S_NRM = 48, S_Y = 49, S_MAX = 64 };
+
+__global__ void k_cg_alpha(double* S, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  S[S_ALPHA] = S[S_RZ] / S[S_PQ];
+}
+// x += alpha p; r -= alpha q; z = D^-1 r
+template <typename T>
+__global__ void k_cg_update(int64_t n, const double* __restrict__ S, Ptr4<T> p, Ptr4<T> q, Ptr4<T> invd, MPtr4<T> x,
+                            MPtr4<T> r, MPtr4<T> z, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T al = (T)S[S_ALPHA];
+  for (int c = 0; c < 3; ++c) {
+    x.c[c][i] += al * p.c[c][i];
+    const T rr = r.c[c][i] - al * q.c[c][i];
+    r.c[c][i] = rr;
+    z.c[c][i] = invd.c[c][i] * rr;
+  }
+}
+__global__ void k_cg_beta(double* S, int* flag, double tol2, int last) {
+  if (*flag) return;
+  S[S_BETA] = S[S_RZN] / S[S_RZ];
+  S[S_RZ] = S[S_RZN];
+  if (!(S[S_RZN] > tol2 * S[S_RZ0]) || last) *flag = 1;
+}
+template <typename T>
+__global__ void k_cg_dir(int64_t n, const double* __restrict__ S, Ptr4<T> z, MPtr4<T> p, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T be = (T)S[S_BETA];
+  for (int c = 0; c < 3; ++c) p.c[c][i] = z.c[c][i] + be * p.c[c][i];
+}
+__global__ void k_set_int(int* f, int v) { *f = v; }
+__global__ void k_cg_start(double* S, int* flag) {
+  S[S_RZ] = S[S_RZ0];
+  *flag = S[S_RZ0] > 0.0 ? 0 : 1;
+}
+
+template <typename T, typename U>
+__global__ void k_convert(int64_t n, const T* __restrict__ a, U* __restrict__ b, double scale) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i < n) b[i] = (U)((double)a[i] * scale);
+}
+// x64 += scale * d32
+template <typename T>
+__global__ void k_accum(int64_t n, const T* __restrict__ d, double* __restrict__ x, double scale) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i < n) x[i] += scale * (double)d[i];
+}
+// z_p = -r_p / m (m = diag(M_1/eta); 0 on padding)
+template <typename T>
+__global__ void k_schur(int64_t n, const T* __restrict__ m, const T* __restrict__ r, T* __restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T mm = m[i];
+  z[i] = mm != (T)0 ? -r[i] / mm : (T)0;
+}
+
+// Deflated Schur step (DEF2 with the constant vector q, Tang, Nabben, Vuik, Erlangga 2009):
+// t = q^T r / q^T S q, z = -(r - S q t) / m + q t; q = 1, S q precomputed.
+template <typename T>
+__global__ void k_schur_defl(int64_t n, const T* __restrict__ m, const T* __restrict__ r, const T* __restrict__ sq,
+                             const double* __restrict__ qr, double inv_qsq, T* __restrict__ z) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i >= n) return;
+  const T mm = m[i];
+  const T t = (T)(qr[0] * inv_qsq);
+  z[i] = mm != (T)0 ? -(r[i] - sq[i] * t) / mm + t : (T)0;
+}
+template <typename T>
+__global__ void k_fill(int64_t n, T v, T* __restrict__ a) {
+  const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) -> uniform in [-1, 1)
+inline uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+}  // namespace
+
+// ============================================================================ multigrid state
+template <typename T>
+struct Vec3 {
+  T* c[3] = {nullptr, nullptr, nullptr};
+  const T* const* cc() const { return (const T* const*)c; }
+  T* const* mm() const { return (T* const*)c; }
+};
+
+template <typename T>
+struct MGLevelT {
+  Vec3<T> x, b, r, d, t, invd, p;  // p only on the coarsest level
+  double lam = 0.0;
+};
+
+template <typename T>
+struct KVec {  // composite (u on level 0, p on level 1)
+  T* u[3] = {nullptr, nullptr, nullptr};
+  T* p = nullptr;
+};
+
+template <typename T>
+struct PrecState {
+  bool ready = false;
+  std::vector<MGLevelT<T>> L;
+  T* mdiag = nullptr;                 // diag(M_1/eta) on level 1
+  T* ones_p = nullptr;                // 1 on every pressure layout entry (level 1)
+  T* sq = nullptr;                    // S 1 ~ -B A^-1 P B^T 1 (deflation of the constant pressure mode)
+  double qsq = 0.0;                   // 1^T S 1 over unique pressure nodes (0: deflation off)
+  Vec3<T> defl_w, defl_c;             // A^-1 c and c = P B^T 1 (set-up work vectors)
+  std::vector<KVec<T>> V, Z;          // FGMRES bases
+  KVec<T> w, tmp;                     // work vectors
+  KVec<T> ir_r, ir_c;                 // FP32 iterative refinement: inner rhs and correction
+  T* tu[3] = {nullptr, nullptr, nullptr};  // velocity scratch (level 0)
+};
+
+struct MGState {
+  tn_mg_opts opts;
+  int nlev = 0;
+  double* S = nullptr;     // device scalars
+  int* flag = nullptr;     // coarse CG stop flag
+  double* part = nullptr;  // reduction partials [2][MAXV][RG]
+  PrecState<double> p64;
+  PrecState<float> p32;
+  std::vector<void*> allocs;
+  int restart = 0;         // FGMRES bases allocated for this restart length
+};
+
+namespace {
+
+template <typename T>
+PrecState<T>& ps(MGState* m);
+template <>
+PrecState<double>& ps<double>(MGState* m) {
+  return m->p64;
+}
+template <>
+PrecState<float>& ps<float>(MGState* m) {
+  return m->p32;
+}
+template <typename T>
+const T* svec_of(const Level& L);
+template <>
+const double* svec_of<double>(const Level& L) {
+  return L.s64;
+}
+template <>
+const float* svec_of<float>(const Level& L) {
+  return L.s32;
+}
+template <typename T>
+const T* rad_of(const Level& L);
+template <>
+const double* rad_of<double>(const Level& L) {
+  return L.rad64;
+}
+template <>
+const float* rad_of<float>(const Level& L) {
+  return L.rad32;
+}
+
+cudaError_t g_err = cudaSuccess;
+inline void ck(cudaError_t e) {
+  if (g_err == cudaSuccess && e != cudaSuccess) g_err = e;
+}
+inline void ckl() { ck(cudaGetLastError()); }
+
+template <typename T>
+T* alloc_zero(MGState* m, int64_t n) {
+  void* p = nullptr;
+  ck(cudaMalloc(&p, sizeof(T) * (size_t)n));
+  if (p) {
+    ck(cudaMemset(p, 0, sizeof(T) * (size_t)n));
+    m->allocs.push_back(p);
+  }
+  return (T*)p;
+}
+
+template <typename T>
+Vec3<T> alloc3(MGState* m, int64_t n) {
+  Vec3<T> v;
+  for (int c = 0; c < 3; ++c) v.c[c] = alloc_zero<T>(m, n);
+  return v;
+}
+
+template <typename T>
+Ptr4<T> P4(const T* const* c, int n) {
+  Ptr4<T> p{};
+  for (int i = 0; i < 4; ++i) p.c[i] = i < n ? c[i] : nullptr;
+  return p;
+}
+template <typename T>
+MPtr4<T> M4(T* const* c, int n) {
+  MPtr4<T> p{};
+  for (int i = 0; i < 4; ++i) p.c[i] = i < n ? c[i] : nullptr;
+  return p;
+}
+
+// out[0..nvec) = dots of x[v] with y over unique nodes of level L (ncomp components).
+template <typename T>
+void dots(MGState* m, const Level& L, int nvec, int ncomp, const T* const* const* x, const T* const* y, double* out,
+          cudaStream_t st, const int* skip = nullptr) {
+  DotArgs<T> a{};
+  for (int v = 0; v < nvec; ++v)
+    for (int c = 0; c < ncomp; ++c) a.x[v][c] = x[v][c];
+  for (int c = 0; c < ncomp; ++c) a.y[c] = y[c];
+  k_dots<T><<<RG, RB, 0, st>>>(L.n_layout, L.wmask, nvec, ncomp, a, m->part, skip);
+  ckl();
+  k_dots_final<<<nvec, RB, 0, st>>>(nvec, m->part, nullptr, out, skip);
+  ckl();
+}
+
+// composite dots: velocity part on level 0 plus pressure part on level 1
+template <typename T>
+void kdots(MGState* m, const tn_mesh* mesh, int nvec, const KVec<T>* const* x, const KVec<T>& y, double* out,
+           cudaStream_t st) {
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  DotArgs<T> a{};
+  for (int v = 0; v < nvec; ++v)
+    for (int c = 0; c < 3; ++c) a.x[v][c] = x[v]->u[c];
+  for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
+  k_dots<T><<<RG, RB, 0, st>>>(L0.n_layout, L0.wmask, nvec, 3, a, m->part, nullptr);
+  ckl();
+  DotArgs<T> b{};
+  for (int v = 0; v < nvec; ++v) b.x[v][0] = x[v]->p;
+  b.y[0] = y.p;
+  k_dots<T><<<RG, RB, 0, st>>>(L1.n_layout, L1.wmask, nvec, 1, b, m->part + MAXV * RG, nullptr);
+  ckl();
+  k_dots_final<<<nvec, RB, 0, st>>>(nvec, m->part, m->part + MAXV * RG, out, nullptr);
+  ckl();
+}
+
+template <typename T>
+void kaxpy(const tn_mesh* mesh, int nvec, const KVec<T>* const* x, const double* coef, double sign, KVec<T>& y,
+           cudaStream_t st) {
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  AxpyArgs<T> a{};
+  for (int v = 0; v < nvec; ++v)
+    for (int c = 0; c < 3; ++c) a.x[v][c] = x[v]->u[c];
+  for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
+  k_axpy_multi<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, nvec, 3, coef, sign, a, nullptr);
+  ckl();
+  AxpyArgs<T> b{};
+  for (int v = 0; v < nvec; ++v) b.x[v][0] = x[v]->p;
+  b.y[0] = y.p;
+  k_axpy_multi<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, nvec, 1, coef, sign, b, nullptr);
+  ckl();
+}
+
+template <typename T>
+void kaxpby(const tn_mesh* mesh, double alpha, const KVec<T>& x, double beta, KVec<T>& y, cudaStream_t st) {
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, alpha, P4<T>(x.u, 3), beta, M4<T>(y.u, 3));
+  ckl();
+  const T* xp[1] = {x.p};
+  T* yp[1] = {y.p};
+  k_axpby<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, 1, alpha, P4<T>(xp, 1), beta, M4<T>(yp, 1));
+  ckl();
+}
+
+bool rotations_singular(const tn_mesh* mesh) {
+  return mesh->bc_in == TN_BC_FREESLIP && mesh->bc_out == TN_BC_FREESLIP;
+}
+
+M33 inverse33(const double (&a)[3][3]) {
+  M33 r{};
+  double c00 = a[1][1] * a[2][2] - a[1][2] * a[2][1], c01 = a[1][2] * a[2][0] - a[1][0] * a[2][2],
+         c02 = a[1][0] * a[2][1] - a[1][1] * a[2][0];
+  double det = a[0][0] * c00 + a[0][1] * c01 + a[0][2] * c02;
+  r.a[0][0] = c00 / det;
+  r.a[1][0] = c01 / det;
+  r.a[2][0] = c02 / det;
+  r.a[0][1] = (a[0][2] * a[2][1] - a[0][1] * a[2][2]) / det;
+  r.a[1][1] = (a[0][0] * a[2][2] - a[0][2] * a[2][0]) / det;
+  r.a[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
+  r.a[0][2] = (a[0][1] * a[1][2] - a[0][2] * a[1][1]) / det;
+  r.a[1][2] = (a[0][2] * a[1][0] - a[0][0] * a[1][2]) / det;
+  r.a[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
+  return r;
+}
+
+// u <- u - (rigid-rotation component of u), Euclidean over unique nodes of level L
+template <typename T>
+void project_rotations(MGState* m, const Level& L, T* const* u, cudaStream_t st, const int* skip = nullptr) {
+  k_angmom<T><<<RG, RB, 0, st>>>(dims(L), L.wmask, svec_of<T>(L), rad_of<T>(L), P4<T>((const T* const*)u, 3),
+                                 m->part, skip);
+  ckl();
+  k_dots_final<<<3, RB, 0, st>>>(3, m->part, nullptr, m->S + S_L, skip);
+  ckl();
+  k_sub_rotation<T><<<nb(L.n_layout), EB, 0, st>>>(dims(L), svec_of<T>(L), rad_of<T>(L), M4<T>(u, 3), m->S + S_L,
+                                                   inverse33(L.inertia), skip);
+  ckl();
+}
+
+template <typename T>
+void apply_K_level(const tn_mesh* mesh, int h, const T* const* x, T* const* y, cudaStream_t st,
+                   const int* skip = nullptr) {
+  ck(launch_apply_A<T>(mesh->lv[h], BC{mesh->bc_in, mesh->bc_out}, mesh->div_term, x, y, st, skip));
+}
+
+// Jacobi-preconditioned CG on the coarsest level: x = K^-1 b (x0 = 0); stops when
+// (r, D^-1 r) <= rtol^2 (r0, D^-1 r0) or after max_iters.
+template <typename T>
+void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
+  MGLevelT<T>& C = ps<T>(m).L[h];
+  const Level& L = mesh->lv[h];
+  const int64_t n = L.n_layout;
+  const bool proj = rotations_singular(mesh);
+  if (proj) project_rotations<T>(m, L, C.b.mm(), st);
+  // r = b, z = D^-1 r (stored in d), p = z, x = 0
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.b.cc(), 3), 0.0, M4<T>(C.r.mm(), 3));
+  ckl();
+  k_mul<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(C.invd.cc(), 3), P4<T>(C.r.cc(), 3), M4<T>(C.d.mm(), 3));
+  ckl();
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.d.cc(), 3), 0.0, M4<T>(C.p.mm(), 3));
+  ckl();
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(C.d.cc(), 3), 0.0, M4<T>(C.x.mm(), 3));
+  ckl();
+  k_set_int<<<1, 1, 0, st>>>(m->flag, 0);
+  ckl();
+  const T* const* rr[1] = {C.r.cc()};
+  dots<T>(m, L, 1, 3, rr, C.d.cc(), m->S + S_RZ0, st);
+  k_cg_start<<<1, 1, 0, st>>>(m->S, m->flag);
+  ckl();
+  const double tol2 = m->opts.coarse_rtol * m->opts.coarse_rtol;
+  const int maxit = m->opts.coarse_max_iters;
+  for (int it = 0; it < maxit; ++it) {
+    apply_K_level<T>(mesh, h, C.p.cc(), C.t.mm(), st, m->flag);
+    const T* const* pp[1] = {C.p.cc()};
+    dots<T>(m, L, 1, 3, pp, C.t.cc(), m->S + S_PQ, st, m->flag);
+    k_cg_alpha<<<1, 1, 0, st>>>(m->S, m->flag);
+    ckl();
+    k_cg_update<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.p.cc(), 3), P4<T>(C.t.cc(), 3), P4<T>(C.invd.cc(), 3),
+                                         M4<T>(C.x.mm(), 3), M4<T>(C.r.mm(), 3), M4<T>(C.d.mm(), 3), m->flag);
+    ckl();
+    dots<T>(m, L, 1, 3, rr, C.d.cc(), m->S + S_RZN, st, m->flag);
+    k_cg_beta<<<1, 1, 0, st>>>(m->S, m->flag, tol2, it == maxit - 1);
+    ckl();
+    k_cg_dir<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.d.cc(), 3), M4<T>(C.p.mm(), 3), m->flag);
+    ckl();
+  }
+  if (proj) project_rotations<T>(m, L, C.x.mm(), st);
+}
+
+// One degree-2 Chebyshev smoothing step on level h (x updated in place, rhs b).
+template <typename T>
+void cheb_step(MGState* m, const tn_mesh* mesh, int h, bool zero_x, cudaStream_t st) {
+  MGLevelT<T>& G = ps<T>(m).L[h];
+  const int64_t n = mesh->lv[h].n_layout;
+  const double a = m->opts.cheb_lo * G.lam, b = m->opts.cheb_hi * G.lam;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
+  if (!zero_x) apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
+  k_cheb1<T><<<nb(n), EB, 0, st>>>(n, zero_x ? 1 : 0, 1.0 / theta, P4<T>(G.b.cc(), 3), P4<T>(G.t.cc(), 3),
+                                   P4<T>(G.invd.cc(), 3), M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
+  ckl();
+  apply_K_level<T>(mesh, h, G.d.cc(), G.t.mm(), st);
+  k_cheb2<T><<<nb(n), EB, 0, st>>>(n, rho1 * rho0, 2.0 * rho1 / delta, P4<T>(G.t.cc(), 3), P4<T>(G.invd.cc(), 3),
+                                   M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
+  ckl();
+}
+
+// V-cycle on level h: x_h = V(b_h)
+template <typename T>
+void vcycle_level(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
+  if (h == m->nlev - 1) {
+    coarse_cg<T>(m, mesh, h, st);
+    return;
+  }
+  MGLevelT<T>& G = ps<T>(m).L[h];
+  MGLevelT<T>& C = ps<T>(m).L[h + 1];
+  const Level& F = mesh->lv[h];
+  const Level& Lc = mesh->lv[h + 1];
+  const BC bc{mesh->bc_in, mesh->bc_out};
+  const int64_t n = F.n_layout;
+  for (int s = 0; s < m->opts.pre_smooth; ++s) cheb_step<T>(m, mesh, h, s == 0, st);
+  if (m->opts.pre_smooth == 0)
+    k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(G.b.cc(), 3), 0.0, M4<T>(G.x.mm(), 3)), ckl();
+  // r = b - K x
+  apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(G.b.cc(), 3), 0.0, M4<T>(G.r.mm(), 3));
+  ckl();
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, -1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.r.mm(), 3));
+  ckl();
+  ck(launch_restrict<T>(F, Lc, bc, 3, 1, G.r.cc(), C.b.mm(), st));
+  vcycle_level<T>(m, mesh, h + 1, st);
+  ck(launch_prolong<T>(F, Lc, bc, 3, 1, C.x.cc(), G.t.mm(), st));
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.x.mm(), 3));
+  ckl();
+  for (int s = 0; s < m->opts.post_smooth; ++s) cheb_step<T>(m, mesh, h, false, st);
+}
+
+double host_scalar(MGState* m, int slot, cudaStream_t st) {
+  double v = 0;
+  ck(cudaMemcpyAsync(&v, m->S + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+  ck(cudaStreamSynchronize(st));
+  return v;
+}
+
+template <typename T>
+tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
+  MGState* m = mesh->mg;
+  PrecState<T>& P = ps<T>(m);
+  const BC bc{mesh->bc_in, mesh->bc_out};
+  if (P.L.empty()) {
+    P.L.resize(m->nlev);
+    for (int h = 0; h < m->nlev; ++h) {
+      const int64_t n = mesh->lv[h].n_layout;
+      MGLevelT<T>& G = P.L[h];
+      G.x = alloc3<T>(m, n), G.b = alloc3<T>(m, n), G.r = alloc3<T>(m, n), G.d = alloc3<T>(m, n);
+      G.t = alloc3<T>(m, n), G.invd = alloc3<T>(m, n);
+      if (h == m->nlev - 1) G.p = alloc3<T>(m, n);
+    }
+    P.mdiag = alloc_zero<T>(m, mesh->lv[1].n_layout);
+    P.ones_p = alloc_zero<T>(m, mesh->lv[1].n_layout);
+    P.sq = alloc_zero<T>(m, mesh->lv[1].n_layout);
+    P.defl_w = alloc3<T>(m, mesh->lv[0].n_layout);
+    P.defl_c = alloc3<T>(m, mesh->lv[0].n_layout);
+  }
+  if (g_err != cudaSuccess) return TN_ENOMEM;
+  // Jacobi diagonals
+  for (int h = 0; h < m->nlev; ++h) {
+    MGLevelT<T>& G = P.L[h];
+    const Level& L = mesh->lv[h];
+    ck(launch_diag_A<T>(L, bc, mesh->div_term, G.t.mm(), st));
+    for (int c = 0; c < 3; ++c) k_recip<T><<<nb(L.n_layout), EB, 0, st>>>(L.n_layout, G.t.c[c], G.invd.c[c]), ckl();
+  }
+  ck(launch_diag_pmass<T>(mesh->lv[0], mesh->lv[1], P.mdiag, st));
+  // power-iteration start vectors: level 0 given or SplitMix64, coarser levels restricted
+  {
+    const Level& L = mesh->lv[0];
+    MGLevelT<T>& G = P.L[0];
+    if (v0) {
+      for (int c = 0; c < 3; ++c)
+        ck(cudaMemcpyAsync(G.x.c[c], v0[c], sizeof(T) * L.n_layout, cudaMemcpyDeviceToDevice, st));
+    } else {
+      std::vector<int64_t> canon((size_t)L.n_layout);
+      tn_mesh_canonical_index(mesh, 0, canon.data());
+      std::vector<T> hv((size_t)L.n_layout);
+      for (int c = 0; c < 3; ++c) {
+        for (int64_t i = 0; i < L.n_layout; ++i) {
+          if (canon[i] < 0) {
+            hv[i] = 0;
+            continue;
+          }
+          uint64_t z = splitmix64(m->opts.seed ^ splitmix64((uint64_t)canon[i] * 3 + c));
+          hv[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+        }
+        ck(cudaMemcpyAsync(G.x.c[c], hv.data(), sizeof(T) * L.n_layout, cudaMemcpyHostToDevice, st));
+        ck(cudaStreamSynchronize(st));
+      }
+    }
+  }
+  for (int h = 1; h < m->nlev; ++h)
+    ck(launch_restrict<T>(mesh->lv[h - 1], mesh->lv[h], bc, 3, 1, P.L[h - 1].x.cc(), P.L[h].x.mm(), st));
+  // power iterations on D^-1 K of every smoothing level
+  std::vector<double> lam(m->nlev, 0.0);
+  for (int h = 0; h + 1 < m->nlev; ++h) {
+    MGLevelT<T>& G = P.L[h];
+    const Level& L = mesh->lv[h];
+    const int64_t n = L.n_layout;
+    const T* const* xx[1] = {G.x.cc()};
+    dots<T>(m, L, 1, 3, xx, G.x.cc(), m->S + S_TMP, st);
+    k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.x.cc(), 3), M4<T>(G.x.mm(), 3), m->S + S_TMP);
+    ckl();
+    for (int it = 0; it < m->opts.power_iters; ++it) {
+      apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
+      k_mul<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.invd.cc(), 3), P4<T>(G.t.cc(), 3), M4<T>(G.d.mm(), 3));
+      ckl();
+      const T* const* dd[1] = {G.d.cc()};
+      dots<T>(m, L, 1, 3, dd, G.d.cc(), m->S + S_TMP + h % 4, st);
+      k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.d.cc(), 3), M4<T>(G.x.mm(), 3), m->S + S_TMP + h % 4);
+      ckl();
+    }
+    double l2 = 0.0;
+    ck(cudaMemcpyAsync(&l2, m->S + S_TMP + h % 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    G.lam = std::sqrt(l2);
+  }
+  // Deflation of the constant pressure mode: under free-slip P B^T 1 != 0 at the boundary
+  // nodes, so the constant pressure is a near-null (not null) mode of the Schur complement that
+  // the diagonal Schur approximation misses.  S 1 = -B A^-1 c, c = P B^T 1, with A^-1 c from
+  // two stationary V-cycle iterations.
+  {
+    const Level& L0 = mesh->lv[0];
+    const Level& L1 = mesh->lv[1];
+    MGLevelT<T>& G = P.L[0];
+    const int64_t n0 = L0.n_layout, n1 = L1.n_layout;
+    k_fill<T><<<nb(n1), EB, 0, st>>>(n1, (T)1, P.ones_p);
+    ckl();
+    T* scr = sizeof(T) == 8 ? (T*)L0.scr64 : (T*)L0.scr32;
+    const T* cin[1] = {P.ones_p};
+    T* fout[1] = {scr};
+    ck(launch_prolong<T>(L0, L1, bc, 1, 0, cin, fout, st));
+    ck(launch_grad_fine<T>(L0, bc, scr, G.r.mm(), st));  // c in G.r
+    Vec3<T>& wv = P.defl_w;
+    Vec3<T>& cc = P.defl_c;
+    for (int q = 0; q < 3; ++q) ck(cudaMemcpyAsync(cc.c[q], G.r.c[q], sizeof(T) * n0, cudaMemcpyDeviceToDevice, st));
+    for (int q = 0; q < 3; ++q) ck(cudaMemsetAsync(wv.c[q], 0, sizeof(T) * n0, st));
+    for (int cyc = 0; cyc < 2; ++cyc) {
+      // b = c - A w
+      apply_K_level<T>(mesh, 0, wv.cc(), G.t.mm(), st);
+      k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, 1.0, P4<T>(cc.cc(), 3), 0.0, M4<T>(G.b.mm(), 3));
+      ckl();
+      k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, -1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.b.mm(), 3));
+      ckl();
+      vcycle_level<T>(m, mesh, 0, st);
+      k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, 1.0, P4<T>(G.x.cc(), 3), 1.0, M4<T>(wv.mm(), 3));
+      ckl();
+    }
+    ck(launch_div_fine<T>(L0, bc, wv.cc(), scr, st));
+    const T* fin[1] = {scr};
+    T* cout[1] = {P.sq};
+    ck(launch_restrict<T>(L0, L1, bc, 1, 0, fin, cout, st));
+    k_axpby<T><<<nb(n1), EB, 0, st>>>(n1, 1, 0.0, P4<T>((const T* const*)&P.sq, 1), -1.0, M4<T>(&P.sq, 1));
+    ckl();
+    const T* sqa[1] = {P.sq};
+    const T* const* sqp[1] = {sqa};
+    const T* on[1] = {P.ones_p};
+    dots<T>(m, L1, 1, 1, sqp, on, m->S + S_TMP, st);
+    const double qsq = host_scalar(m, S_TMP, st);
+    // off when the constant pressure is (numerically) an exact null vector (no-slip on both surfaces)
+    double cn = 0.0;
+    const T* const* ccp[1] = {cc.cc()};
+    dots<T>(m, L0, 1, 3, ccp, cc.cc(), m->S + S_TMP, st);
+    cn = host_scalar(m, S_TMP, st);
+    P.qsq = (cn > 0.0 && qsq != 0.0) ? qsq : 0.0;
+  }
+  ck(cudaStreamSynchronize(st));
+  if (g_err != cudaSuccess) return TN_ECUDA;
+  P.ready = true;
+  return TN_OK;
+}
+
+template <typename T>
+void vcycle_t(tn_mesh* mesh, const T* const* r, T* const* z, cudaStream_t st) {
+  MGState* m = mesh->mg;
+  MGLevelT<T>& G = ps<T>(m).L[0];
+  const int64_t n = mesh->lv[0].n_layout;
+  for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(G.b.c[c], r[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+  vcycle_level<T>(m, mesh, 0, st);
+  for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(z[c], G.x.c[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+}
+
+// ============================================================================ FGMRES
+template <typename T>
+void alloc_kvec(MGState* m, const tn_mesh* mesh, KVec<T>& v) {
+  for (int c = 0; c < 3; ++c) v.u[c] = alloc_zero<T>(m, mesh->lv[0].n_layout);
+  v.p = alloc_zero<T>(m, mesh->lv[1].n_layout);
+}
+
+template <typename T>
+void ensure_krylov(MGState* m, const tn_mesh* mesh, int restart) {
+  PrecState<T>& P = ps<T>(m);
+  if ((int)P.Z.size() >= restart && !P.V.empty()) return;
+  P.V.resize(restart + 1);
+  P.Z.resize(restart);
+  for (auto& v : P.V)
+    if (!v.p) alloc_kvec<T>(m, mesh, v);
+  for (auto& v : P.Z)
+    if (!v.p) alloc_kvec<T>(m, mesh, v);
+  if (!P.w.p) alloc_kvec<T>(m, mesh, P.w);
+  if (!P.tmp.p) alloc_kvec<T>(m, mesh, P.tmp);
+  if (sizeof(T) == 4 && !P.ir_r.p) alloc_kvec<T>(m, mesh, P.ir_r), alloc_kvec<T>(m, mesh, P.ir_c);
+  if (!P.tu[0])
+    for (int c = 0; c < 3; ++c) P.tu[c] = alloc_zero<T>(m, mesh->lv[0].n_layout);
+}
+
+// y = K x  (K = [[P A P + I - P, P B^T], [B P, 0]])
+template <typename T>
+void apply_K(MGState* m, tn_mesh* mesh, const KVec<T>& x, KVec<T>& y, cudaStream_t st) {
+  PrecState<T>& P = ps<T>(m);
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  const BC bc{mesh->bc_in, mesh->bc_out};
+  ck(launch_apply_A<T>(L0, bc, mesh->div_term, (const T* const*)x.u, (T* const*)y.u, st));
+  T* scr = sizeof(T) == 8 ? (T*)L0.scr64 : (T*)L0.scr32;
+  const T* cin[1] = {x.p};
+  T* fout[1] = {scr};
+  ck(launch_prolong<T>(L0, L1, bc, 1, 0, cin, fout, st));
+  ck(launch_grad_fine<T>(L0, bc, scr, (T* const*)P.tu, st));
+  k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, 1.0, P4<T>((const T* const*)P.tu, 3), 1.0,
+                                             M4<T>((T* const*)y.u, 3));
+  ckl();
+  ck(launch_div_fine<T>(L0, bc, (const T* const*)x.u, scr, st));
+  const T* fin[1] = {scr};
+  T* cout[1] = {y.p};
+  ck(launch_restrict<T>(L0, L1, bc, 1, 0, fin, cout, st));
+}
+
+// z = P^-1 r: z_p = -r_p / diag(M_1/eta), z_u = V(r_u - B^T z_p)
+template <typename T>
+void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStream_t st) {
+  PrecState<T>& P = ps<T>(m);
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  const BC bc{mesh->bc_in, mesh->bc_out};
+  if (P.qsq != 0.0) {
+    const T* rr[1] = {r.p};
+    const T* const* rp[1] = {rr};
+    const T* on[1] = {P.ones_p};
+    dots<T>(m, L1, 1, 1, rp, on, m->S + S_QR, st);
+    k_schur_defl<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, P.mdiag, r.p, P.sq, m->S + S_QR, 1.0 / P.qsq, z.p);
+  } else {
+    k_schur<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, P.mdiag, r.p, z.p);
+  }
+  ckl();
+  T* scr = sizeof(T) == 8 ? (T*)L0.scr64 : (T*)L0.scr32;
+  const T* cin[1] = {z.p};
+  T* fout[1] = {scr};
+  ck(launch_prolong<T>(L0, L1, bc, 1, 0, cin, fout, st));
+  ck(launch_grad_fine<T>(L0, bc, scr, (T* const*)P.tu, st));
+  MGLevelT<T>& G = P.L[0];
+  k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, 1.0, P4<T>((const T* const*)r.u, 3), 0.0,
+                                             M4<T>(G.b.mm(), 3));
+  ckl();
+  k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, -1.0, P4<T>((const T* const*)P.tu, 3), 1.0,
+                                             M4<T>(G.b.mm(), 3));
+  ckl();
+  vcycle_level<T>(m, mesh, 0, st);
+  for (int c = 0; c < 3; ++c)
+    ck(cudaMemcpyAsync(z.u[c], G.x.c[c], sizeof(T) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
+}
+
+
+// Restarted FGMRES(m) with right preconditioning and CGS2 orthogonalisation (Saad 1993).
+// Solves K x = b from the given x; stops when ||b - K x|| <= abstol (recurrence estimate,
+// confirmed by the true residual at every restart) or after max_iters.  Returns the
+// iterations used; *res gets the final true residual norm.
+template <typename T>
+int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double abstol, int restart, int max_iters,
+           double* res, cudaStream_t st) {
+  PrecState<T>& P = ps<T>(m);
+  ensure_krylov<T>(m, mesh, restart);
+  int its = 0;
+  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
+  double beta = 0;
+  while (true) {
+    // r = b - K x  -> V[0]
+    apply_K<T>(m, mesh, x, P.w, st);
+    kaxpby<T>(mesh, 1.0, b, 0.0, P.V[0], st);
+    kaxpby<T>(mesh, -1.0, P.w, 1.0, P.V[0], st);
+    const KVec<T>* v0[1] = {&P.V[0]};
+    kdots<T>(m, mesh, 1, v0, P.V[0], m->S + S_NRM, st);
+    beta = std::sqrt(host_scalar(m, S_NRM, st));
+    *res = beta;
+    if (beta <= abstol || its >= max_iters || g_err != cudaSuccess) break;
+    kaxpby<T>(mesh, 0.0, P.V[0], 1.0 / beta, P.V[0], st);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < restart && its < max_iters; ++j) {
+      apply_prec<T>(m, mesh, P.V[j], P.Z[j], st);
+      apply_K<T>(m, mesh, P.Z[j], P.w, st);
+      std::vector<const KVec<T>*> vb(j + 1);
+      for (int i = 0; i <= j; ++i) vb[i] = &P.V[i];
+      kdots<T>(m, mesh, j + 1, vb.data(), P.w, m->S + S_H, st);
+      kaxpy<T>(mesh, j + 1, vb.data(), m->S + S_H, -1.0, P.w, st);
+      kdots<T>(m, mesh, j + 1, vb.data(), P.w, m->S + S_H2, st);
+      kaxpy<T>(mesh, j + 1, vb.data(), m->S + S_H2, -1.0, P.w, st);
+      const KVec<T>* wv[1] = {&P.w};
+      kdots<T>(m, mesh, 1, wv, P.w, m->S + S_NRM, st);
+      double hs[S_MAX];
+      ck(cudaMemcpyAsync(hs, m->S, sizeof(double) * S_MAX, cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      double* col = &H[j * (restart + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = hs[S_H + i] + hs[S_H2 + i];
+      const double hn = std::sqrt(hs[S_NRM]);
+      col[j + 1] = hn;
+      if (hn > 0) kaxpby<T>(mesh, 1.0 / hn, P.w, 0.0, P.V[j + 1], st);
+      for (int i = 0; i < j; ++i) {  // previous Givens rotations
+        const double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t0;
+      }
+      const double den = std::sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+      cs[j] = den > 0 ? col[j] / den : 1.0;
+      sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      if (std::fabs(g[j + 1]) <= abstol || hn == 0.0 || g_err != cudaSuccess) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^-1 g, x += Z y
+    for (int i = j - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < j; ++k) s -= H[k * (restart + 1) + i] * y[k];
+      y[i] = s / H[i * (restart + 1) + i];
+    }
+    ck(cudaMemcpyAsync(m->S + S_Y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
+    std::vector<const KVec<T>*> zb(j);
+    for (int i = 0; i < j; ++i) zb[i] = &P.Z[i];
+    kaxpy<T>(mesh, j, zb.data(), m->S + S_Y, 1.0, x, st);
+    ck(cudaStreamSynchronize(st));
+  }
+  return its;
+}
+
+template <typename T>
+KVec<T> wrap(T* const* u, T* p) {
+  KVec<T> v;
+  for (int c = 0; c < 3; ++c) v.u[c] = u[c];
+  v.p = p;
+  return v;
+}
+
+}  // namespace
+
+void mg_free(MGState* m) {
+  if (!m) return;
+  for (void* p : m->allocs) cudaFree(p);
+  if (m->S) cudaFree(m->S);
+  if (m->flag) cudaFree(m->flag);
+  if (m->part) cudaFree(m->part);
+  delete m;
+}
+
+void mg_invalidate(tn_mesh* mesh) {
+  if (mesh->mg) mesh->mg->p64.ready = mesh->mg->p32.ready = false;
+}
+
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+tn_status tn_mg_default_opts(tn_mg_opts* o) {
+  if (!o) return TN_EINVAL;
+  o->pre_smooth = 2;
+  o->post_smooth = 2;
+  o->cheb_degree = 2;
+  o->cheb_lo = 0.1;
+  o->cheb_hi = 1.1;
+  o->power_iters = 15;
+  o->coarse_max_iters = 50;
+  o->coarse_rtol = 1e-3;
+  o->levels = 0;
+  o->seed = 0x5eedull;
+  return TN_OK;
+}
+
+tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const void* const* v0, void* stream) {
+  if (!mesh) return TN_EINVAL;
+  if (!mesh->eta_set) {
+    set_error("tn_mg_setup: viscosity not set");
+    return TN_ESTATE;
+  }
+  if (mesh->lv.size() < 2) {
+    set_error("tn_mg_setup: the mesh hierarchy has a single level");
+    return TN_EINVAL;
+  }
+  tn_mg_opts o;
+  tn_mg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.cheb_degree != 2 || o.pre_smooth < 0 || o.post_smooth < 0 || o.power_iters < 1 || o.coarse_max_iters < 1 ||
+      !(o.cheb_hi > o.cheb_lo) || !(o.cheb_lo > 0)) {
+    set_error("tn_mg_setup: invalid multigrid options");
+    return TN_EINVAL;
+  }
+  const int avail = (int)mesh->lv.size();
+  const int nlev = o.levels <= 0 ? avail : std::min(o.levels, avail);
+  if (nlev < 2) {
+    set_error("tn_mg_setup: need at least two levels");
+    return TN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  g_err = cudaSuccess;
+  MGState* m = mesh->mg;
+  if (m && (m->nlev != nlev)) {
+    mg_free(m);
+    mesh->mg = m = nullptr;
+  }
+  if (!m) {
+    m = new MGState();
+    m->nlev = nlev;
+    ck(cudaMalloc((void**)&m->S, sizeof(double) * S_MAX));
+    ck(cudaMemset(m->S, 0, sizeof(double) * S_MAX));
+    ck(cudaMalloc((void**)&m->flag, sizeof(int)));
+    ck(cudaMalloc((void**)&m->part, sizeof(double) * 2 * MAXV * RG));
+    mesh->mg = m;
+    if (g_err != cudaSuccess) {
+      set_error("tn_mg_setup: device allocation failed");
+      return TN_ENOMEM;
+    }
+  }
+  m->opts = o;
+  tn_status s = prec == TN_F64 ? mg_setup_t<double>(mesh, v0, st) : mg_setup_t<float>(mesh, v0, st);
+  if (s != TN_OK) set_error(std::string("tn_mg_setup: ") + cudaGetErrorString(g_err));
+  return s;
+}
+
+tn_status tn_mg_lambda(const tn_mesh* mesh, tn_prec prec, int level, double* lam) {
+  if (!mesh || !mesh->mg || !lam || level < 0 || level >= mesh->mg->nlev) return TN_EINVAL;
+  if (prec == TN_F64) {
+    if (mesh->mg->p64.L.empty()) return TN_ESTATE;
+    *lam = mesh->mg->p64.L[level].lam;
+  } else {
+    if (mesh->mg->p32.L.empty()) return TN_ESTATE;
+    *lam = mesh->mg->p32.L[level].lam;
+  }
+  return TN_OK;
+}
+
+tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r, void* const* z, void* stream) {
+  if (!mesh || !r || !z) return TN_EINVAL;
+  for (int c = 0; c < 3; ++c)
+    if (!r[c] || !z[c] || r[c] == z[c]) {
+      set_error("tn_vcycle: NULL or aliased vectors");
+      return TN_EINVAL;
+    }
+  if (!mesh->mg || !(prec == TN_F64 ? mesh->mg->p64.ready : mesh->mg->p32.ready)) {
+    tn_status s = tn_mg_setup(mesh, prec, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
+    if (s != TN_OK) return s;
+  }
+  g_err = cudaSuccess;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == TN_F64) vcycle_t<double>(mesh, (const double* const*)r, (double* const*)z, st);
+  else vcycle_t<float>(mesh, (const float* const*)r, (float* const*)z, st);
+  if (g_err != cudaSuccess) {
+    set_error(std::string("tn_vcycle: ") + cudaGetErrorString(g_err));
+    return TN_ECUDA;
+  }
+  return TN_OK;
+}
+
+tn_status tn_solve_default_opts(tn_solve_opts* o) {
+  if (!o) return TN_EINVAL;
+  o->rtol = 1e-8;
+  o->restart = 10;
+  o->max_iters = 1000;
+  o->mode = TN_SOLVE_F64;
+  o->inner_rtol = 1e-3;
+  o->inner_max_iters = 100;
+  o->max_refinements = 30;
+  return TN_OK;
+}
+
+tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f, const double* g,
+                          double* const* u, double* p, tn_solve_stats* stats, void* stream) {
+  if (!mesh || !f || !u || !p) return TN_EINVAL;
+  for (int c = 0; c < 3; ++c)
+    if (!f[c] || !u[c]) {
+      set_error("tn_stokes_solve: NULL vector");
+      return TN_EINVAL;
+    }
+  if (mesh->lv.size() < 2) {
+    set_error("tn_stokes_solve: the mesh hierarchy has a single level");
+    return TN_EINVAL;
+  }
+  tn_solve_opts o;
+  tn_solve_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > MAXV - 1 || !(o.rtol > 0) || o.max_iters < 1) {
+    set_error("tn_stokes_solve: invalid options (restart must be in [1, 11])");
+    return TN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  const bool mixed = o.mode == TN_SOLVE_MIXED;
+  tn_status s;
+  if (!mesh->mg || !mesh->mg->p64.ready) {
+    s = tn_mg_setup(mesh, TN_F64, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
+    if (s != TN_OK) return s;
+  }
+  if (mixed && !mesh->mg->p32.ready) {
+    s = tn_mg_setup(mesh, TN_F32, &mesh->mg->opts, nullptr, stream);
+    if (s != TN_OK) return s;
+  }
+  g_err = cudaSuccess;
+  MGState* m = mesh->mg;
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  ensure_krylov<double>(m, mesh, o.restart);
+  if (mixed) ensure_krylov<float>(m, mesh, o.restart);
+  if (g_err != cudaSuccess) {
+    set_error("tn_stokes_solve: workspace allocation failed");
+    return TN_ENOMEM;
+  }
+  // b = (f, g) in the FP64 temporary; x = (u, p) = 0
+  PrecState<double>& D = m->p64;
+  KVec<double> b = D.tmp;
+  for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(b.u[c], f[c], sizeof(double) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
+  if (g) ck(cudaMemcpyAsync(b.p, g, sizeof(double) * L1.n_layout, cudaMemcpyDeviceToDevice, st));
+  else ck(cudaMemsetAsync(b.p, 0, sizeof(double) * L1.n_layout, st));
+  KVec<double> x = wrap<double>(u, p);
+  for (int c = 0; c < 3; ++c) ck(cudaMemsetAsync(u[c], 0, sizeof(double) * L0.n_layout, st));
+  ck(cudaMemsetAsync(p, 0, sizeof(double) * L1.n_layout, st));
+  const KVec<double>* bb[1] = {&b};
+  kdots<double>(m, mesh, 1, bb, b, m->S + S_NRM, st);
+  const double bnorm = std::sqrt(host_scalar(m, S_NRM, st));
+  int its = 0, refs = 0;
+  double res = bnorm;
+  if (bnorm > 0) {
+    if (!mixed) {
+      its = fgmres<double>(m, mesh, b, x, o.rtol * bnorm, o.restart, o.max_iters, &res, st);
+    } else {
+      // FP64 iterative refinement around FP32 FGMRES / V-cycle inner solves
+      PrecState<float>& F = m->p32;
+      KVec<double>& r = D.V[0];
+      KVec<float>& rr32 = F.ir_r;
+      KVec<float>& c32 = F.ir_c;
+      while (refs < o.max_refinements && its < o.max_iters) {
+        apply_K<double>(m, mesh, x, D.w, st);
+        kaxpby<double>(mesh, 1.0, b, 0.0, r, st);
+        kaxpby<double>(mesh, -1.0, D.w, 1.0, r, st);
+        const KVec<double>* rv[1] = {&r};
+        kdots<double>(m, mesh, 1, rv, r, m->S + S_NRM, st);
+        res = std::sqrt(host_scalar(m, S_NRM, st));
+        if (res <= o.rtol * bnorm || g_err != cudaSuccess) break;
+        for (int c = 0; c < 3; ++c) {
+          k_convert<double, float><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, r.u[c], rr32.u[c], 1.0 / res);
+          ckl();
+          ck(cudaMemsetAsync(c32.u[c], 0, sizeof(float) * L0.n_layout, st));
+        }
+        k_convert<double, float><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, r.p, rr32.p, 1.0 / res);
+        ckl();
+        ck(cudaMemsetAsync(c32.p, 0, sizeof(float) * L1.n_layout, st));
+        double ires = 0;
+        its += fgmres<float>(m, mesh, rr32, c32, o.inner_rtol, o.restart, o.inner_max_iters, &ires, st);
+        for (int c = 0; c < 3; ++c) {
+          k_accum<float><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, c32.u[c], x.u[c], res);
+          ckl();
+        }
+        k_accum<float><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, c32.p, x.p, res);
+        ckl();
+        ++refs;
+      }
+    }
+    if (rotations_singular(mesh)) project_rotations<double>(m, L0, x.u, st);
+    // true residual of the returned solution
+    KVec<double>& r = D.V[0];
+    apply_K<double>(m, mesh, x, D.w, st);
+    kaxpby<double>(mesh, 1.0, b, 0.0, r, st);
+    kaxpby<double>(mesh, -1.0, D.w, 1.0, r, st);
+    const KVec<double>* rv[1] = {&r};
+    kdots<double>(m, mesh, 1, rv, r, m->S + S_NRM, st);
+    res = std::sqrt(host_scalar(m, S_NRM, st));
+  }
+  ck(cudaStreamSynchronize(st));
+  auto t1 = std::chrono::steady_clock::now();
+  const double rel = bnorm > 0 ? res / bnorm : 0.0;
+  if (stats) {
+    stats->iterations = its;
+    stats->refinements = refs;
+    stats->rel_residual = rel;
+    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+    stats->converged = rel <= o.rtol;
+  }
+  if (g_err != cudaSuccess) {
+    set_error(std::string("tn_stokes_solve: ") + cudaGetErrorString(g_err));
+    return TN_ECUDA;
+  }
+  if (rel > o.rtol) {
+    set_error("tn_stokes_solve: not converged");
+    return TN_ENOTCONVERGED;
+  }
+  return TN_OK;
+}
+
+}  // extern "C"
