@@ -162,6 +162,23 @@ tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* 
  * (nested iso-interpolation of the coarse W1 function, Sec. 3).  Stream-ordered. */
 tn_status tn_apply_B(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev, void* stream);
 
+/* q = B P u exactly as tn_apply_B (same kernels, same result), but without mesh-owned or
+ * per-call scratch: the fine-level divergence field between the element kernel and the
+ * restriction lives in a static device array compiled into the library (8 MiB, held by every
+ * GPU that loads the library until the process exits).  For callers that cannot allocate
+ * device memory at the point of the call, e.g. code running under an allocator that forbids
+ * cudaMalloc after start-up; this call makes no cudaMalloc, cudaFree or other allocating call.
+ * The paper has no counterpart; it is an addition of this library.
+ * Limit: level h's node layout times the element size (8 B for TN_F64, 4 B for TN_F32) must
+ * fit in 8 MiB, else TN_EINVAL with the sizes in tn_last_error().  The mesh's device must be
+ * current.  The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads, other meshes) race on it.  Nothing in it
+ * needs to start at zero (each call writes every entry it reads).  Stream-ordered. */
+tn_status tn_apply_B_static(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev,
+                            void* stream);
+
+
 /* y = P B^T p: gradient of a pressure field (node layout of level h+1) onto the velocity
  * space of level h.  Stream-ordered. */
 tn_status tn_apply_BT(tn_mesh* mesh, int level, tn_prec prec, const void* p_dev, void* const* y_dev, void* stream);

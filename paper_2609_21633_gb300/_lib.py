@@ -78,6 +78,7 @@ _SIGS = {
     "tn_apply_A": ([P, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_apply_B": ([P, ctypes.c_int, ctypes.c_int, PP, P, P], ctypes.c_int),
     "tn_apply_BT": ([P, ctypes.c_int, ctypes.c_int, P, PP, P], ctypes.c_int),
+    "tn_apply_B_static": ([P, ctypes.c_int, ctypes.c_int, PP, P, P], ctypes.c_int),
     "tn_diag_A": ([P, ctypes.c_int, ctypes.c_int, PP, P], ctypes.c_int),
     "tn_diag_pmass": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
     "tn_prolong": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
@@ -193,6 +194,11 @@ def tn_apply_A(mesh, level, u, y, stream=None):
 def tn_apply_B(mesh, level, u, q, stream=None):
     pu, _a = _ptrs(u)
     _check(lib().tn_apply_B(mesh, level, _prec(u[0].dtype), pu, _ptr(q), _stream(stream)))
+
+
+def tn_apply_B_static(mesh, level, u, q, stream=None):
+    pu, _a = _ptrs(u)
+    _check(lib().tn_apply_B_static(mesh, level, _prec(u[0].dtype), pu, _ptr(q), _stream(stream)))
 
 
 def tn_apply_BT(mesh, level, p, y, stream=None):
