@@ -33,6 +33,9 @@ LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, 
 # per wedge 33 (differences) + 9 (scaling) + 45 (grad u) + 20 (stress) + 54 (stress x M^-T)
 # + 21 (test-gradient combination) + 18 (accumulation) = 200.
 A_FLOPS_PER_CELL = 400.0
+# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 164.5 MB for
+# 2,621,440 cells), scaled to the bench size by cells; None once the kernel changes.
+A_TRAFFIC_BYTES_PER_CELL = None
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -46,6 +49,8 @@ def parse():
     ap.add_argument("--level", type=int, default=7)
     ap.add_argument("--n_r", type=int, default=129)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-solve", dest="no_solve", action="store_true",
+                    help="do not run the Stokes-solve measurements after the operator steps")
     return ap.parse_args()
 
 
@@ -156,6 +161,51 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------------- GPU arm
+def layout_temperature(tn, m, noise_seed=None, noise_scale=0.01):
+    """Prescribed temperature (degree 3, order 2, amplitude 0.01) at every layout node of level 0,
+    plus optional seeded nodal noise that is identical on all copies of a node; 0 on padding."""
+    from paper_2609_21633_gb300 import inputs
+    info = tn.tn_mesh_info(m, 0)
+    canon = tn.tn_mesh_canonical_index(m, 0)
+    valid = canon >= 0
+    pts = tn.tn_mesh_lateral_points(m, 0)
+    N, P, n_r = info["N"], info["pitch"], info["n_r"]
+    radii = R_IN + ((R_OUT - R_IN) * np.arange(n_r)) / (n_r - 1)
+    lat = np.zeros((10, N + 1, P, 3))
+    lat[:, :, : N + 1] = pts
+    xyz = (radii[None, :, None, None, None] * lat[:, None]).reshape(-1, 3)
+    T = np.zeros(info["n_layout"])
+    T[valid] = inputs.temperature(xyz[valid], R_IN, R_OUT)
+    if noise_seed is not None:
+        noise = inputs.normal(info["n_layout"], noise_seed, noise_scale)
+        T[valid] += noise[canon[valid]]
+    return T
+
+
+def solve_case(tn, torch, dev, level, n_r, E, Ra, mode):
+    """One Stokes solve to 1e-8 (multigrid set-up excluded from the time)."""
+    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT)
+    try:
+        info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
+        Td = torch.tensor(layout_temperature(tn, m), device=dev)
+        tn.tn_set_temperature(m, Td, E)
+        f = [torch.zeros(info["n_layout"], device=dev, dtype=torch.float64) for _ in range(3)]
+        tn.tn_buoyancy(m, Td, Ra, f)
+        u = [torch.zeros_like(f[0]) for _ in range(3)]
+        p = torch.zeros(pinfo["n_layout"], device=dev, dtype=torch.float64)
+        tn.tn_mg_setup(m, torch.float64)
+        if mode == tn.TN_SOLVE_MIXED:
+            tn.tn_mg_setup(m, torch.float32)
+        torch.cuda.synchronize()
+        st = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(mode=mode), check=False)
+        nv = 3 * info["n_unique_nodes"]
+        npr = pinfo["n_unique_nodes"]
+        return {"iterations": st["iterations"], "refinements": st["refinements"], "seconds": st["seconds"],
+                "rel_residual": st["rel_residual"], "converged": bool(st["converged"]), "dofs": nv + npr}
+    finally:
+        tn.tn_mesh_destroy(m)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -179,18 +229,7 @@ def main():
     info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
     n = info["n_layout"]
     canon = torch.from_numpy(tn.tn_mesh_canonical_index(m, 0))
-    valid = canon >= 0
-    # node coordinates of the layout, for the prescribed temperature field
-    pts = tn.tn_mesh_lateral_points(m, 0)
-    N, P, n_r = info["N"], info["pitch"], info["n_r"]
-    radii = R_IN + ((R_OUT - R_IN) * np.arange(n_r)) / (n_r - 1)
-    lat = np.zeros((10, N + 1, P, 3))
-    lat[:, :, : N + 1] = pts
-    xyz = (radii[None, :, None, None, None] * lat[:, None]).reshape(-1, 3)
-    T = inputs.temperature(xyz, R_IN, R_OUT)
-    noise = inputs.normal(n, args.seed + 100 * rank, 0.01)
-    T = np.where(valid.numpy(), T + noise[np.maximum(canon.numpy(), 0)], 0.0)
-    Td = torch.tensor(T, device=dev)
+    Td = torch.tensor(layout_temperature(tn, m, args.seed + 100 * rank), device=dev)
     tn.tn_set_temperature(m, Td, LAW["E"], LAW["jump_r"], LAW["jump_factor"])
 
     def field(seed, size, can=None):
@@ -207,42 +246,55 @@ def main():
     dA = [torch.empty(n, device=dev, dtype=torch.float64) for _ in range(3)]
     q = torch.empty(pinfo["n_layout"], device=dev, dtype=torch.float64)
 
-    ev = {k: [] for k in ("A", "B", "BT", "diag")}
+    def timed_steps(uu, pp, yy, qq, bb, dd, steps, warmup, sample_clocks):
+        """Warm-up, then `steps` timed steps; returns (ms total, per-op mean ms, clocks)."""
+        ev = {k: [] for k in ("A", "B", "BT", "diag")}
 
-    def step(record=False):
-        for name, fn in (("A", lambda: tn.tn_apply_A(m, 0, u, yA, st)), ("B", lambda: tn.tn_apply_B(m, 0, u, q, st)),
-                         ("BT", lambda: tn.tn_apply_BT(m, 0, p, yBT, st)), ("diag", lambda: tn.tn_diag_A(m, 0, dA, st))):
-            if record:
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                fn()
-                e1.record(st)
-                ev[name].append((e0, e1))
-            else:
-                fn()
+        def step(record):
+            for name, fn in (("A", lambda: tn.tn_apply_A(m, 0, uu, yy, st)),
+                             ("B", lambda: tn.tn_apply_B(m, 0, uu, qq, st)),
+                             ("BT", lambda: tn.tn_apply_BT(m, 0, pp, bb, st)),
+                             ("diag", lambda: tn.tn_diag_A(m, 0, dd, st))):
+                if record:
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(st)
+                    fn()
+                    e1.record(st)
+                    ev[name].append((e0, e1))
+                else:
+                    fn()
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record(st)
-    for _ in range(args.steps):
-        step(record=True)
-    t1.record(st)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = t0.elapsed_time(t1)
+        for _ in range(warmup):
+            step(False)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        if sample_clocks:
+            clocks.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(st)
+        for _ in range(steps):
+            step(True)
+        t1.record(st)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if sample_clocks else None
+        per = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in ev.items()}
+        return t0.elapsed_time(t1), per, clk, step
+
+    ms, per_op, clk, step = timed_steps(u, p, yA, q, yBT, dA, args.steps, max(3, args.warmup), True)
     if dist:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = tt.item()
         dist.barrier()
-    per_op = {k: sum(a.elapsed_time(b) for a, b in v) / len(v) for k, v in ev.items()}
+    # the same step in FP32 (the inner-solve precision of the mixed path)
+    u32 = [t.float() for t in u]
+    p32, q32 = p.float(), q.float()
+    yA32, yBT32, dA32 = [[t.float() for t in v] for v in (yA, yBT, dA)]
+    ms32, per32, _, _ = timed_steps(u32, p32, yA32, q32, yBT32, dA32, args.steps, max(3, args.warmup), False)
+    del u32, p32, q32, yA32, yBT32, dA32
 
     nv, npr, ndof = dof_counts(args.level, args.n_r)
     value = world * ndof * args.steps / (ms / 1e3) / 1e9
@@ -259,7 +311,7 @@ def main():
         for a, b in zip(u, hu):
             a.copy_(b, non_blocking=True)
         p.copy_(hp, non_blocking=True)
-        step()
+        step(False)
         for a, b in zip(hout, outs):
             a.copy_(b, non_blocking=True)
 
@@ -295,13 +347,26 @@ def main():
             "per_op_ms": per_op,
             "roofline": {"bound": "alu", "kernel": "A apply (tile kernel + interface sum)", "achieved": achieved,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None, "peak_note": "FP64 DFMA peak from unit counts x max clock",
+                         "traffic": A_TRAFFIC_BYTES_PER_CELL * cells if A_TRAFFIC_BYTES_PER_CELL else None,
+                         "peak_note": "FP64 DFMA peak from unit counts x max clock",
                          "hbm_frac_of_measured": (64.0 * cells) / (per_op["A"] / 1e3) / 6771.8e9},
+            "f32_step": {"ms_per_step": ms32 / args.steps, "per_op_ms": per32,
+                         "value": ndof / (ms32 / args.steps / 1e3) / 1e9, "unit": "GDoF/s",
+                         "A_hbm_frac_of_measured": (32.0 * cells) / (per32["A"] / 1e3) / 6771.8e9},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": 11 * args.steps,
         }
+        if world == 1 and not args.no_solve:
+            # Stokes solves to 1e-8: FP64 against FP32 inner solves with FP64 refinement
+            solves = {}
+            for name, lvl, nr, E in (("l4_17_contrast1e1", 4, 17, math.log(10.0)),
+                                     ("l6_65_contrast1e4", 6, 65, math.log(1e4))):
+                r64 = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64)
+                rmx = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED)
+                solves[name] = {"fp64": r64, "mixed": rmx, "mixed_speedup": r64["seconds"] / rmx["seconds"]}
+            line["solves"] = solves
         if world == 1:
             dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
             line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

@@ -260,8 +260,8 @@ tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r_dev, void*
 typedef enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED = 1 } tn_solve_mode;
 typedef struct {
   double rtol;          /* 1e-8 relative residual */
-  int restart;          /* 10 (1..11) */
-  int max_iters;        /* total FGMRES iterations (1000) */
+  int restart;          /* 30 (1..30) */
+  int max_iters;        /* total FGMRES iterations (2000) */
   int mode;             /* tn_solve_mode */
   double inner_rtol;    /* mixed: inner relative tolerance (1e-3) */
   int inner_max_iters;  /* mixed: iterations per inner solve (100) */

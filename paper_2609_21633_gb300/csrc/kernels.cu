@@ -35,6 +35,30 @@ namespace {
 
 constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
 
+// Resident CTAs per SM requested from the register allocator for the tile kernel, per precision.
+#ifndef TN_MINB_F64
+#define TN_MINB_F64 2
+#endif
+#ifndef TN_MINB_F32
+#define TN_MINB_F32 2
+#endif
+// Radial chunking: the grid is split radially until it has at least this many CTAs
+// (chunks never shorter than TN_KC_MIN cells).
+#ifndef TN_CTA_TARGET
+#define TN_CTA_TARGET (32 * 152)
+#endif
+#ifndef TN_KC_MIN
+#define TN_KC_MIN 8
+#endif
+// 1: load node layer k+2 while cell layer k is computed
+#ifndef TN_PREFETCH
+#define TN_PREFETCH 0
+#endif
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = sizeof(T) == 8 ? TN_MINB_F64 : TN_MINB_F32;
+};
+
 template <typename T>
 struct Tab;  // precision-selected views of a level's tables
 template <>
@@ -157,7 +181,7 @@ __device__ __forceinline__ void project_vec(T (&v)[3], const T* s, int64_t soff,
 }
 
 template <typename T, typename Op, int TT, int FLAGS>
-__global__ void __launch_bounds__((TT + 1) * (TT + 1))
+__global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
     k_tile(Dims D, Op op, const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
            T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
            const T* __restrict__ lay, const T* __restrict__ eta, const T* __restrict__ svec, int bc_in, int bc_out,
@@ -274,8 +298,15 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1))
 
   const int kstart = kc0 > 0 ? kc0 - 1 : 0;
   load_level(kstart, ub);
+  if (TN_PREFETCH) load_level(kstart + 1, ut);
   for (int k = kstart; k < kc1; ++k) {
-    load_level(k + 1, ut);
+    // prefetch the next node layer while this cell layer is computed
+    T un[4][NIN];
+    if (TN_PREFETCH) {
+      if (k + 2 <= kc1) load_level(k + 2, un);
+    } else {
+      load_level(k + 1, ut);
+    }
     T accb[4][NOUT], acct[4][NOUT];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -311,7 +342,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1))
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) carry[q][c] = acct[q][c];
 #pragma unroll
-      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c];
+      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c], ut[q][c] = TN_PREFETCH ? un[q][c] : ut[q][c];
     }
   }
   if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
@@ -326,7 +357,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   const int ncells = L.n_r - 1;
   // radial chunks: enough CTAs to fill the GPU a few times over
   int kc = ncells;
-  while (kc > 8 && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < 4 * 152) kc = (kc + 1) / 2;
+  while (kc > TN_KC_MIN && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < TN_CTA_TARGET) kc = (kc + 1) / 2;
   dim3 grid(ntiles, (ncells + kc - 1) / kc, 10);
   const T* i1 = Op::NIN > 1 ? in[1] : in[0];
   const T* i2 = Op::NIN > 2 ? in[2] : in[0];

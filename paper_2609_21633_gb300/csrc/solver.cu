@@ -7,6 +7,7 @@
 // reduce in a fixed order, so every result is bitwise reproducible.  The coarsest-level
 // conjugate-gradient loop keeps its scalars on the device and stops through a device flag
 // (later kernels of a converged loop return immediately), so a V-cycle needs no host sync.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -267,8 +268,9 @@ __global__ void k_cheb2(int64_t n, double c1, double c2, Ptr4<T> t, Ptr4<T> invd
 }
 
 // ---- coarse CG (device scalars in S, stop flag) ----------------------------------------------
+constexpr int MAX_RESTART = 30;
 enum { S_RZ0 = 0, S_RZ = 1, S_PQ = 2, S_RZN = 3, S_ALPHA = 4, S_BETA = 5, S_QR = 6, S_TMP = 8, S_L = 12, S_H = 16,
-       S_H2 = 32, S_NRM = 48, S_Y = 49, S_MAX = 64 };
+       S_H2 = S_H + MAX_RESTART + 1, S_NRM = S_H2 + MAX_RESTART + 1, S_Y = S_NRM + 1, S_MAX = S_Y + MAX_RESTART + 1 };
 
 __global__ void k_cg_alpha(double* S, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -487,25 +489,28 @@ void dots(MGState* m, const Level& L, int nvec, int ncomp, const T* const* const
   ckl();
 }
 
-// composite dots: velocity part on level 0 plus pressure part on level 1
+// composite dots: velocity part on level 0 plus pressure part on level 1 (chunks of MAXV vectors)
 template <typename T>
 void kdots(MGState* m, const tn_mesh* mesh, int nvec, const KVec<T>* const* x, const KVec<T>& y, double* out,
            cudaStream_t st) {
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
-  DotArgs<T> a{};
-  for (int v = 0; v < nvec; ++v)
-    for (int c = 0; c < 3; ++c) a.x[v][c] = x[v]->u[c];
-  for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
-  k_dots<T><<<RG, RB, 0, st>>>(L0.n_layout, L0.wmask, nvec, 3, a, m->part, nullptr);
-  ckl();
-  DotArgs<T> b{};
-  for (int v = 0; v < nvec; ++v) b.x[v][0] = x[v]->p;
-  b.y[0] = y.p;
-  k_dots<T><<<RG, RB, 0, st>>>(L1.n_layout, L1.wmask, nvec, 1, b, m->part + MAXV * RG, nullptr);
-  ckl();
-  k_dots_final<<<nvec, RB, 0, st>>>(nvec, m->part, m->part + MAXV * RG, out, nullptr);
-  ckl();
+  for (int v0 = 0; v0 < nvec; v0 += MAXV) {
+    const int nv = std::min(MAXV, nvec - v0);
+    DotArgs<T> a{};
+    for (int v = 0; v < nv; ++v)
+      for (int c = 0; c < 3; ++c) a.x[v][c] = x[v0 + v]->u[c];
+    for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
+    k_dots<T><<<RG, RB, 0, st>>>(L0.n_layout, L0.wmask, nv, 3, a, m->part, nullptr);
+    ckl();
+    DotArgs<T> b{};
+    for (int v = 0; v < nv; ++v) b.x[v][0] = x[v0 + v]->p;
+    b.y[0] = y.p;
+    k_dots<T><<<RG, RB, 0, st>>>(L1.n_layout, L1.wmask, nv, 1, b, m->part + MAXV * RG, nullptr);
+    ckl();
+    k_dots_final<<<nv, RB, 0, st>>>(nv, m->part, m->part + MAXV * RG, out + v0, nullptr);
+    ckl();
+  }
 }
 
 template <typename T>
@@ -513,17 +518,20 @@ void kaxpy(const tn_mesh* mesh, int nvec, const KVec<T>* const* x, const double*
            cudaStream_t st) {
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
-  AxpyArgs<T> a{};
-  for (int v = 0; v < nvec; ++v)
-    for (int c = 0; c < 3; ++c) a.x[v][c] = x[v]->u[c];
-  for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
-  k_axpy_multi<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, nvec, 3, coef, sign, a, nullptr);
-  ckl();
-  AxpyArgs<T> b{};
-  for (int v = 0; v < nvec; ++v) b.x[v][0] = x[v]->p;
-  b.y[0] = y.p;
-  k_axpy_multi<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, nvec, 1, coef, sign, b, nullptr);
-  ckl();
+  for (int v0 = 0; v0 < nvec; v0 += MAXV) {
+    const int nv = std::min(MAXV, nvec - v0);
+    AxpyArgs<T> a{};
+    for (int v = 0; v < nv; ++v)
+      for (int c = 0; c < 3; ++c) a.x[v][c] = x[v0 + v]->u[c];
+    for (int c = 0; c < 3; ++c) a.y[c] = y.u[c];
+    k_axpy_multi<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, nv, 3, coef + v0, sign, a, nullptr);
+    ckl();
+    AxpyArgs<T> b{};
+    for (int v = 0; v < nv; ++v) b.x[v][0] = x[v0 + v]->p;
+    b.y[0] = y.p;
+    k_axpy_multi<T><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, nv, 1, coef + v0, sign, b, nullptr);
+    ckl();
+  }
 }
 
 template <typename T>
@@ -1112,8 +1120,8 @@ tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r, void* con
 tn_status tn_solve_default_opts(tn_solve_opts* o) {
   if (!o) return TN_EINVAL;
   o->rtol = 1e-8;
-  o->restart = 10;
-  o->max_iters = 1000;
+  o->restart = 30;
+  o->max_iters = 2000;
   o->mode = TN_SOLVE_F64;
   o->inner_rtol = 1e-3;
   o->inner_max_iters = 100;
@@ -1136,8 +1144,8 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   tn_solve_opts o;
   tn_solve_default_opts(&o);
   if (opts) o = *opts;
-  if (o.restart < 1 || o.restart > MAXV - 1 || !(o.rtol > 0) || o.max_iters < 1) {
-    set_error("tn_stokes_solve: invalid options (restart must be in [1, 11])");
+  if (o.restart < 1 || o.restart > MAX_RESTART || !(o.rtol > 0) || o.max_iters < 1) {
+    set_error("tn_stokes_solve: invalid options (restart must be in [1, 30])");
     return TN_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
