@@ -206,8 +206,9 @@ tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double
 
 /* ------------------------------------------------------------------------------------------
  * Geometric multigrid (Sec. 7): V-cycle over the mesh hierarchy, two pre- and two
- * post-smoothing steps of a degree-2 Chebyshev polynomial in D^-1 K per level (D = diag of
- * the constrained operator K = P A P + I - P), coarsest level solved by conjugate gradients.
+ * post-smoothing steps of a degree-2 Chebyshev polynomial in D^-1 K per level (D = the 3x3
+ * node-block diagonal of the constrained operator K = P A P + I - P, i.e. block Jacobi),
+ * coarsest level solved by conjugate gradients preconditioned with the same D.
  *
  * Chebyshev step (Chebyshev acceleration, Saad, Iterative Methods for Sparse Linear Systems,
  * Alg. 12.1, two iterations) on the interval [cheb_lo, cheb_hi] x lambda, lambda the estimate
@@ -215,7 +216,7 @@ tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double
  * (v <- D^-1 K v / ||D^-1 K v||, lambda = ||D^-1 K v||, Euclidean over unique nodes).
  * The level-0 start vector is v0_dev (3 arrays) or, if NULL, SplitMix64 draws keyed by
  * (seed, canonical layout index, component); level h+1 starts from the restriction of level h's.
- * Coarsest level: Jacobi-preconditioned CG from 0 until (r, D^-1 r) <= coarse_rtol^2 (r0, D^-1 r0)
+ * Coarsest level: D-preconditioned CG from 0 until (r, D^-1 r) <= coarse_rtol^2 (r0, D^-1 r0)
  * or coarse_max_iters; with free-slip on both surfaces the rigid rotations (an exact null space)
  * are projected out of its right-hand side and solution.
  * Transfers: restriction P^T then the coarse boundary projector; prolongation P then the fine

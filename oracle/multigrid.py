@@ -6,13 +6,14 @@ Algorithm (the paper gives the structure: two pre- and two post-smoothing steps 
 degree-2 Chebyshev smoother per level, conjugate gradients on the coarsest level; the
 remaining choices are readings):
 * level operators K_h = P_h A_h P_h + (I - P_h), re-discretised with the coarse viscosity
-  (mean of the 8 children); D_h = diag(K_h);
+  (mean of the 8 children); D_h = the 3x3 node-block diagonal of K_h (block Jacobi; reading:
+  the paper does not say which diagonal its Chebyshev smoother uses);
 * transfers: prolongation P_h T_h (nested iso-interpolation, then the fine boundary
   projector), restriction P_{h+1} T_h^T;
 * Chebyshev acceleration (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1) with
   D^-1 preconditioning, two iterations per smoothing step, on [lo, hi] x lambda_h;
   lambda_h from power iterations on D^-1 K_h started from the restricted start vector;
-* coarsest level: Jacobi-preconditioned CG from zero, stopping when
+* coarsest level: D-preconditioned CG from zero, stopping when
   (r, D^-1 r) <= rtol^2 (r0, D^-1 r0) or after max_iters; with free-slip on both surfaces
   the rigid rotations are projected out of its right-hand side and solution.
 Vectors are component-major flat arrays (3 n_nodes).
@@ -29,6 +30,22 @@ def vec_prolongation(fine, coarse):
     """Nested interpolation for 3-component fields in component-major numbering."""
     T = O.prolongation(fine, coarse)
     return sp.block_diag([T, T, T], format="csr")
+
+
+def block_jacobi_inverse(K):
+    """Sparse inverse of the 3x3 node-block diagonal of K (component-major numbering)."""
+    K = K.tocsr()
+    n = K.shape[0] // 3
+    idx = np.arange(n)
+    Bk = np.zeros((n, 3, 3))
+    for a in range(3):
+        for c in range(3):
+            Bk[:, a, c] = np.asarray(K[a * n + idx, c * n + idx]).ravel()
+    Bi = np.linalg.inv(Bk)
+    rows = [a * n + idx for a in range(3) for c in range(3)]
+    cols = [c * n + idx for a in range(3) for c in range(3)]
+    vals = [Bi[:, a, c] for a in range(3) for c in range(3)]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=K.shape)
 
 
 def rotation_basis(mesh):
@@ -59,7 +76,7 @@ class Hierarchy:
         self.Pb = [O.projector_matrix(O.boundary_projectors(m, bc)) for m in self.meshes]
         self.K = [O.constrain_A(O.assemble_A(m, e, div_term), Pb)
                   for m, e, Pb in zip(self.meshes, self.eta, self.Pb)]
-        self.invD = [1.0 / K.diagonal() for K in self.K]
+        self.Dinv = [block_jacobi_inverse(K) for K in self.K]
         self.T = [vec_prolongation(self.meshes[h], self.meshes[h + 1]) for h in range(self.nlev - 1)]
         self.lo, self.hi, self.power_iters = lo, hi, power_iters
         self.pre, self.post = pre, post
@@ -86,7 +103,7 @@ class Hierarchy:
             w = v / np.linalg.norm(v)
             lam = None
             for _ in range(self.power_iters):
-                z = self.invD[h] * (self.K[h] @ w)
+                z = self.Dinv[h] @ (self.K[h] @ w)
                 lam = np.linalg.norm(z)
                 w = z / lam
             self.lam[h] = lam
@@ -98,20 +115,20 @@ class Hierarchy:
         rho0 = 1.0 / sigma
         rho1 = 1.0 / (2.0 * sigma - rho0)
         r = b.copy() if zero_x else b - self.K[h] @ x
-        d = self.invD[h] * r / theta
+        d = (self.Dinv[h] @ r) / theta
         x = d.copy() if zero_x else x + d
         r = r - self.K[h] @ d
-        d = rho1 * rho0 * d + (2.0 * rho1 / delta) * (self.invD[h] * r)
+        d = rho1 * rho0 * d + (2.0 * rho1 / delta) * (self.Dinv[h] @ r)
         return x + d
 
     def coarse_cg(self, b):
         h = self.nlev - 1
-        K, invD = self.K[h], self.invD[h]
+        K, Dinv = self.K[h], self.Dinv[h]
         if self.singular:
             b = b - self.rotQ @ (self.rotQ.T @ b)
         x = np.zeros_like(b)
         r = b.copy()
-        z = invD * r
+        z = Dinv @ r
         p = z.copy()
         rz0 = rz = r @ z
         if rz0 > 0:
@@ -120,7 +137,7 @@ class Hierarchy:
                 alpha = rz / (p @ q)
                 x = x + alpha * p
                 r = r - alpha * q
-                z = invD * r
+                z = Dinv @ r
                 rzn = r @ z
                 beta = rzn / rz
                 rz = rzn

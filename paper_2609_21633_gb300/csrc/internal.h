@@ -103,6 +103,9 @@ template <typename T>
 cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cudaStream_t st);
 template <typename T>
 cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cudaStream_t st);
+// Inverse of the 3x3 node blocks of P A P + I - P (6 arrays: xx, yy, zz, xy, xz, yz).
+template <typename T>
+cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b, cudaStream_t st);
 template <typename T>
 cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st);
 // Interface sum over shared copies; mode 0: plain sum; 1: + (I - P) u at boundary layers;

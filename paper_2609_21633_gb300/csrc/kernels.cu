@@ -495,6 +495,123 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
   d0[idx] = out[0], d1[idx] = out[1], d2[idx] = out[2];
 }
 
+// ------------------------------------------------------------------------------------ node blocks
+// Thread per layout node: the 3x3 node block of the constrained operator, P_j A_jj P_j + I - P_j,
+// as 6 entries (xx, yy, zz, xy, xz, yz).  Same gather as k_diag_A; nodes on diamond edges get
+// P A_partial P per diamond and the identity part is added once by k_interface_block.
+template <typename T>
+__global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, const T* __restrict__ eta,
+                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* b0, T* b1, T* b2, T* b3,
+                          T* b4, T* b5) {
+  const int N = D.N, M = N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)10 * D.n_r * M * M;
+  if (tid >= total) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
+            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
+  const T gxi[3] = {-1, 1, 0}, geta[3] = {-1, 0, 1};
+  const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
+  T B[6] = {0, 0, 0, 0, 0, 0};
+  T alpha = 0;
+  for (int q = 0; q < 6; ++q) {
+    const int ci = i + tri[q][0], cj = j + tri[q][1], w = tri[q][2], a = tri[q][3];
+    if (ci < 0 || cj < 0 || ci >= N || cj >= N) continue;
+    const int64_t t = (((int64_t)d * N + ci) * N + cj) * 2 + w;
+    T Mi[9];
+    for (int r = 0; r < 9; ++r) Mi[r] = geo[(int64_t)r * D.n_tri + t];
+    const T dM = geo[(int64_t)9 * D.n_tri + t];
+    for (int side = 0; side < 2; ++side) {
+      const int kk = side == 0 ? k : k - 1;
+      if (kk < 0 || kk >= D.n_r - 1) continue;
+      const T w0 = lay[4 * kk], w1 = lay[4 * kk + 1], vol = lay[4 * kk + 2];
+      const T gz = side == 0 ? (T)-1 : (T)1;
+      T g[3];
+      for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
+      const T ve = vol * dM * eta[((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w];
+      alpha += ve * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      const T tv = ve * third;
+      B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
+      B[3] += tv * g[0] * g[1], B[4] += tv * g[0] * g[2], B[5] += tv * g[1] * g[2];
+    }
+  }
+  T A[3][3] = {{alpha + B[0], B[3], B[4]}, {B[3], alpha + B[1], B[5]}, {B[4], B[5], alpha + B[2]}};
+  const bool shared = i == 0 || i == N || j == 0 || j == N;
+  if (k == 0 || k == D.n_r - 1) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    const int64_t so = ((int64_t)d * M + i) * D.P + j;
+    T Pm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    T s[3] = {0, 0, 0};
+    if (bc != TN_BC_NOSLIP) {
+      for (int c = 0; c < 3; ++c) s[c] = svec[so + c * D.n_lat_layout];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Pm[r][c] = (r == c ? (T)1 : (T)0) - s[r] * s[c];
+    }
+    T PA[3][3], PAP[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) PA[r][c] = Pm[r][0] * A[0][c] + Pm[r][1] * A[1][c] + Pm[r][2] * A[2][c];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) PAP[r][c] = PA[r][0] * Pm[0][c] + PA[r][1] * Pm[1][c] + PA[r][2] * Pm[2][c];
+    if (!shared)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) PAP[r][c] += bc == TN_BC_NOSLIP ? (r == c ? (T)1 : (T)0) : s[r] * s[c];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) A[r][c] = PAP[r][c];
+  }
+  const int64_t idx = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j;
+  b0[idx] = A[0][0], b1[idx] = A[1][1], b2[idx] = A[2][2], b3[idx] = A[0][1], b4[idx] = A[0][2], b5[idx] = A[1][2];
+}
+
+// Sum the 6 block entries over the copies of shared nodes; add I - P once at boundary layers.
+template <typename T>
+__global__ void k_interface_block(Dims D, int n_groups, const int* __restrict__ gptr, const int64_t* __restrict__ goff,
+                                  const T* __restrict__ gs, T* b0, T* b1, T* b2, T* b3, T* b4, T* b5, int bc_in,
+                                  int bc_out) {
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)n_groups * D.n_r) return;
+  const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
+  T* y[6] = {b0, b1, b2, b3, b4, b5};
+  const int b = gptr[g], e = gptr[g + 1];
+  const int64_t lo = (int64_t)k * D.layer_stride;
+  T v[6] = {0, 0, 0, 0, 0, 0};
+  for (int q = b; q < e; ++q)
+    for (int c = 0; c < 6; ++c) v[c] += y[c][goff[q] + lo];
+  if (k == 0 || k == D.n_r - 1) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    if (bc == TN_BC_NOSLIP) {
+      v[0] += 1, v[1] += 1, v[2] += 1;
+    } else {
+      const T s[3] = {gs[g], gs[n_groups + g], gs[2 * n_groups + g]};
+      v[0] += s[0] * s[0], v[1] += s[1] * s[1], v[2] += s[2] * s[2];
+      v[3] += s[0] * s[1], v[4] += s[0] * s[2], v[5] += s[1] * s[2];
+    }
+  }
+  for (int q = b; q < e; ++q)
+    for (int c = 0; c < 6; ++c) y[c][goff[q] + lo] = v[c];
+}
+
+// In place: symmetric 3x3 block (xx, yy, zz, xy, xz, yz) -> its inverse (0 where singular / padding).
+template <typename T>
+__global__ void k_block_inv(int64_t n, T* b0, T* b1, T* b2, T* b3, T* b4, T* b5) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const T a = b0[i], e = b1[i], f = b2[i], bb = b3[i], c = b4[i], dd = b5[i];
+  // [[a, bb, c], [bb, e, dd], [c, dd, f]]
+  const T c00 = e * f - dd * dd, c01 = c * dd - bb * f, c02 = bb * dd - c * e;
+  const T det = a * c00 + bb * c01 + c * c02;
+  if (det == (T)0) {
+    b0[i] = b1[i] = b2[i] = b3[i] = b4[i] = b5[i] = (T)0;
+    return;
+  }
+  const T id = (T)1 / det;
+  b0[i] = c00 * id;
+  b1[i] = (a * f - c * c) * id;
+  b2[i] = (a * e - bb * bb) * id;
+  b3[i] = c01 * id;
+  b4[i] = c02 * id;
+  b5[i] = (bb * c - a * dd) * id;
+}
+
 // ------------------------------------------------------------------------------------ transfers
 // Nested iso-interpolation (Sec. 3): weight 1 at coincident nodes, 1/2 at lateral or radial
 // edge midpoints, 1/4 where both apply.  Lateral parents of fine lattice position (i, j):
@@ -766,6 +883,25 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
 }
 
 template <typename T>
+cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b, cudaStream_t st) {
+  Dims D = dims(L);
+  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
+  k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), Tab<T>::eta(L), Tab<T>::s(L), bc.in,
+                                             bc.out, div_term, b[0], b[1], b[2], b[3], b[4], b[5]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t ng = (int64_t)L.n_groups * L.n_r;
+  if (ng > 0) {
+    k_interface_block<T><<<nblk(ng, 128), 128, 0, st>>>(D, L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), b[0], b[1],
+                                                        b[2], b[3], b[4], b[5], bc.in, bc.out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_block_inv<T><<<nblk(L.n_layout, 256), 256, 0, st>>>(L.n_layout, b[0], b[1], b[2], b[3], b[4], b[5]);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st) {
   const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
   k_diag_pmass<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), Tab<T>::eta(F), m);
@@ -851,6 +987,7 @@ cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, d
   template cudaError_t launch_div_fine<T>(const Level&, BC, const T* const*, T*, cudaStream_t);                 \
   template cudaError_t launch_grad_fine<T>(const Level&, BC, const T*, T* const*, cudaStream_t);                \
   template cudaError_t launch_diag_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                        \
+  template cudaError_t launch_block_inv_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                   \
   template cudaError_t launch_diag_pmass<T>(const Level&, const Level&, T*, cudaStream_t);                      \
   template cudaError_t launch_interface<T>(const Level&, BC, int, int, T* const*, const T* const*, cudaStream_t,  \
                                            const int*);                                                          \

@@ -36,6 +36,17 @@ struct MPtr4 {
   T* c[4];
 };
 template <typename T>
+struct B6 {  // inverse 3x3 node blocks (xx, yy, zz, xy, xz, yz)
+  const T* c[6];
+};
+template <typename T>
+__device__ __forceinline__ void bmul(const B6<T>& b, int64_t i, const T (&r)[3], T (&z)[3]) {
+  const T a = b.c[0][i], e = b.c[1][i], f = b.c[2][i], xy = b.c[3][i], xz = b.c[4][i], yz = b.c[5][i];
+  z[0] = a * r[0] + xy * r[1] + xz * r[2];
+  z[1] = xy * r[0] + e * r[1] + yz * r[2];
+  z[2] = xz * r[0] + yz * r[1] + f * r[2];
+}
+template <typename T>
 struct DotArgs {
   const T* x[MAXV][4];
   const T* y[4];
@@ -221,12 +232,15 @@ __global__ void k_normalize(int64_t n, int ncomp, Ptr4<T> x, MPtr4<T> y, const d
   for (int c = 0; c < ncomp; ++c) y.c[c][i] = x.c[c][i] * s;
 }
 
-// y = inv * x  (Jacobi), componentwise
+// y = Binv x (block Jacobi)
 template <typename T>
-__global__ void k_mul(int64_t n, int ncomp, Ptr4<T> inv, Ptr4<T> x, MPtr4<T> y) {
+__global__ void k_bmul(int64_t n, B6<T> binv, Ptr4<T> x, MPtr4<T> y) {
   const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
   if (i >= n) return;
-  for (int c = 0; c < ncomp; ++c) y.c[c][i] = inv.c[c][i] * x.c[c][i];
+  const T r[3] = {x.c[0][i], x.c[1][i], x.c[2][i]};
+  T z[3];
+  bmul(binv, i, r, z);
+  for (int c = 0; c < 3; ++c) y.c[c][i] = z[c];
 }
 
 template <typename T>
@@ -237,31 +251,36 @@ __global__ void k_recip(int64_t n, const T* __restrict__ d, T* __restrict__ inv)
   inv[i] = v != (T)0 ? (T)1 / v : (T)0;
 }
 
-// Chebyshev step, part 1 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1):
+// Chebyshev step, part 1 (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1, with the
+// block-Jacobi preconditioner D^-1 = inverse 3x3 node blocks):
 // r = b - t (t = K x; zero_x: x = 0, t unused), d = D^-1 r / theta, x += d
 template <typename T>
-__global__ void k_cheb1(int64_t n, int zero_x, double inv_theta, Ptr4<T> b, Ptr4<T> t, Ptr4<T> invd, MPtr4<T> r,
+__global__ void k_cheb1(int64_t n, int zero_x, double inv_theta, Ptr4<T> b, Ptr4<T> t, B6<T> binv, MPtr4<T> r,
                         MPtr4<T> d, MPtr4<T> x) {
   const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
   if (i >= n) return;
+  T rr[3], z[3];
+  for (int c = 0; c < 3; ++c) rr[c] = zero_x ? b.c[c][i] : b.c[c][i] - t.c[c][i];
+  bmul(binv, i, rr, z);
   for (int c = 0; c < 3; ++c) {
-    const T rr = zero_x ? b.c[c][i] : b.c[c][i] - t.c[c][i];
-    const T dd = (T)inv_theta * (invd.c[c][i] * rr);
-    r.c[c][i] = rr;
+    const T dd = (T)inv_theta * z[c];
+    r.c[c][i] = rr[c];
     d.c[c][i] = dd;
     x.c[c][i] = zero_x ? dd : x.c[c][i] + dd;
   }
 }
 // part 2: r -= t (t = K d), d = c1 d + c2 D^-1 r, x += d
 template <typename T>
-__global__ void k_cheb2(int64_t n, double c1, double c2, Ptr4<T> t, Ptr4<T> invd, MPtr4<T> r, MPtr4<T> d,
+__global__ void k_cheb2(int64_t n, double c1, double c2, Ptr4<T> t, B6<T> binv, MPtr4<T> r, MPtr4<T> d,
                         MPtr4<T> x) {
   const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
   if (i >= n) return;
+  T rr[3], z[3];
+  for (int c = 0; c < 3; ++c) rr[c] = r.c[c][i] - t.c[c][i];
+  bmul(binv, i, rr, z);
   for (int c = 0; c < 3; ++c) {
-    const T rr = r.c[c][i] - t.c[c][i];
-    const T dd = (T)c1 * d.c[c][i] + (T)c2 * (invd.c[c][i] * rr);
-    r.c[c][i] = rr;
+    const T dd = (T)c1 * d.c[c][i] + (T)c2 * z[c];
+    r.c[c][i] = rr[c];
     d.c[c][i] = dd;
     x.c[c][i] = x.c[c][i] + dd;
   }
@@ -278,18 +297,20 @@ __global__ void k_cg_alpha(double* S, const int* __restrict__ skip) {
 }
 // x += alpha p; r -= alpha q; z = D^-1 r
 template <typename T>
-__global__ void k_cg_update(int64_t n, const double* __restrict__ S, Ptr4<T> p, Ptr4<T> q, Ptr4<T> invd, MPtr4<T> x,
+__global__ void k_cg_update(int64_t n, const double* __restrict__ S, Ptr4<T> p, Ptr4<T> q, B6<T> binv, MPtr4<T> x,
                             MPtr4<T> r, MPtr4<T> z, const int* __restrict__ skip) {
   if (skip && *skip) return;
   const int64_t i = blockIdx.x * (int64_t)EB + threadIdx.x;
   if (i >= n) return;
   const T al = (T)S[S_ALPHA];
+  T rr[3], zz[3];
   for (int c = 0; c < 3; ++c) {
     x.c[c][i] += al * p.c[c][i];
-    const T rr = r.c[c][i] - al * q.c[c][i];
-    r.c[c][i] = rr;
-    z.c[c][i] = invd.c[c][i] * rr;
+    rr[c] = r.c[c][i] - al * q.c[c][i];
+    r.c[c][i] = rr[c];
   }
+  bmul(binv, i, rr, zz);
+  for (int c = 0; c < 3; ++c) z.c[c][i] = zz[c];
 }
 __global__ void k_cg_beta(double* S, int* flag, double tol2, int last) {
   if (*flag) return;
@@ -368,8 +389,14 @@ struct Vec3 {
 
 template <typename T>
 struct MGLevelT {
-  Vec3<T> x, b, r, d, t, invd, p;  // p only on the coarsest level
+  Vec3<T> x, b, r, d, t, p;  // p only on the coarsest level
+  T* binv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // inverse node blocks
   double lam = 0.0;
+  B6<T> bi() const {
+    B6<T> b;
+    for (int q = 0; q < 6; ++q) b.c[q] = binv[q];
+    return b;
+  }
 };
 
 template <typename T>
@@ -586,7 +613,7 @@ void apply_K_level(const tn_mesh* mesh, int h, const T* const* x, T* const* y, c
   ck(launch_apply_A<T>(mesh->lv[h], BC{mesh->bc_in, mesh->bc_out}, mesh->div_term, x, y, st, skip));
 }
 
-// Jacobi-preconditioned CG on the coarsest level: x = K^-1 b (x0 = 0); stops when
+// Block-Jacobi-preconditioned CG on the coarsest level: x = K^-1 b (x0 = 0); stops when
 // (r, D^-1 r) <= rtol^2 (r0, D^-1 r0) or after max_iters.
 template <typename T>
 void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
@@ -598,7 +625,7 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   // r = b, z = D^-1 r (stored in d), p = z, x = 0
   k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.b.cc(), 3), 0.0, M4<T>(C.r.mm(), 3));
   ckl();
-  k_mul<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(C.invd.cc(), 3), P4<T>(C.r.cc(), 3), M4<T>(C.d.mm(), 3));
+  k_bmul<T><<<nb(n), EB, 0, st>>>(n, C.bi(), P4<T>(C.r.cc(), 3), M4<T>(C.d.mm(), 3));
   ckl();
   k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.d.cc(), 3), 0.0, M4<T>(C.p.mm(), 3));
   ckl();
@@ -618,7 +645,7 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
     dots<T>(m, L, 1, 3, pp, C.t.cc(), m->S + S_PQ, st, m->flag);
     k_cg_alpha<<<1, 1, 0, st>>>(m->S, m->flag);
     ckl();
-    k_cg_update<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.p.cc(), 3), P4<T>(C.t.cc(), 3), P4<T>(C.invd.cc(), 3),
+    k_cg_update<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.p.cc(), 3), P4<T>(C.t.cc(), 3), C.bi(),
                                          M4<T>(C.x.mm(), 3), M4<T>(C.r.mm(), 3), M4<T>(C.d.mm(), 3), m->flag);
     ckl();
     dots<T>(m, L, 1, 3, rr, C.d.cc(), m->S + S_RZN, st, m->flag);
@@ -640,10 +667,10 @@ void cheb_step(MGState* m, const tn_mesh* mesh, int h, bool zero_x, cudaStream_t
   const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
   if (!zero_x) apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
   k_cheb1<T><<<nb(n), EB, 0, st>>>(n, zero_x ? 1 : 0, 1.0 / theta, P4<T>(G.b.cc(), 3), P4<T>(G.t.cc(), 3),
-                                   P4<T>(G.invd.cc(), 3), M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
+                                   G.bi(), M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
   ckl();
   apply_K_level<T>(mesh, h, G.d.cc(), G.t.mm(), st);
-  k_cheb2<T><<<nb(n), EB, 0, st>>>(n, rho1 * rho0, 2.0 * rho1 / delta, P4<T>(G.t.cc(), 3), P4<T>(G.invd.cc(), 3),
+  k_cheb2<T><<<nb(n), EB, 0, st>>>(n, rho1 * rho0, 2.0 * rho1 / delta, P4<T>(G.t.cc(), 3), G.bi(),
                                    M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
   ckl();
 }
@@ -696,7 +723,8 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
       const int64_t n = mesh->lv[h].n_layout;
       MGLevelT<T>& G = P.L[h];
       G.x = alloc3<T>(m, n), G.b = alloc3<T>(m, n), G.r = alloc3<T>(m, n), G.d = alloc3<T>(m, n);
-      G.t = alloc3<T>(m, n), G.invd = alloc3<T>(m, n);
+      G.t = alloc3<T>(m, n);
+      for (int q = 0; q < 6; ++q) G.binv[q] = alloc_zero<T>(m, n);
       if (h == m->nlev - 1) G.p = alloc3<T>(m, n);
     }
     P.mdiag = alloc_zero<T>(m, mesh->lv[1].n_layout);
@@ -706,13 +734,8 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
     P.defl_c = alloc3<T>(m, mesh->lv[0].n_layout);
   }
   if (g_err != cudaSuccess) return TN_ENOMEM;
-  // Jacobi diagonals
-  for (int h = 0; h < m->nlev; ++h) {
-    MGLevelT<T>& G = P.L[h];
-    const Level& L = mesh->lv[h];
-    ck(launch_diag_A<T>(L, bc, mesh->div_term, G.t.mm(), st));
-    for (int c = 0; c < 3; ++c) k_recip<T><<<nb(L.n_layout), EB, 0, st>>>(L.n_layout, G.t.c[c], G.invd.c[c]), ckl();
-  }
+  // block-Jacobi: inverse 3x3 node blocks of P A P + I - P on every level
+  for (int h = 0; h < m->nlev; ++h) ck(launch_block_inv_A<T>(mesh->lv[h], bc, mesh->div_term, P.L[h].binv, st));
   ck(launch_diag_pmass<T>(mesh->lv[0], mesh->lv[1], P.mdiag, st));
   // power-iteration start vectors: level 0 given or SplitMix64, coarser levels restricted
   {
@@ -753,7 +776,7 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
     ckl();
     for (int it = 0; it < m->opts.power_iters; ++it) {
       apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
-      k_mul<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.invd.cc(), 3), P4<T>(G.t.cc(), 3), M4<T>(G.d.mm(), 3));
+      k_bmul<T><<<nb(n), EB, 0, st>>>(n, G.bi(), P4<T>(G.t.cc(), 3), M4<T>(G.d.mm(), 3));
       ckl();
       const T* const* dd[1] = {G.d.cc()};
       dots<T>(m, L, 1, 3, dd, G.d.cc(), m->S + S_TMP + h % 4, st);

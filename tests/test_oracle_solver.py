@@ -23,7 +23,7 @@ def test_chebyshev_step_is_the_scaled_chebyshev_polynomial(hier):
     (two Chebyshev-acceleration iterations = the degree-2 Chebyshev polynomial)."""
     h = hier.nlev - 1
     K = hier.K[h].toarray()
-    Dinv = np.diag(hier.invD[h])
+    Dinv = hier.Dinv[h].toarray()
     lam = np.max(np.abs(np.linalg.eigvals(Dinv @ K)))
     hier.lam[h] = lam
     b = inputs.normal(K.shape[0], 5)
@@ -39,7 +39,7 @@ def test_chebyshev_step_is_the_scaled_chebyshev_polynomial(hier):
 
 def test_power_iteration_estimates_the_largest_eigenvalue(hier):
     for h in range(hier.nlev - 1):
-        ev = np.linalg.eigvals(np.diag(hier.invD[h]) @ hier.K[h].toarray()) if hier.K[h].shape[0] < 6000 else None
+        ev = np.linalg.eigvals(hier.Dinv[h].toarray() @ hier.K[h].toarray()) if hier.K[h].shape[0] < 6000 else None
         if ev is None:
             continue
         lmax = np.max(np.abs(ev))
@@ -58,8 +58,8 @@ def test_coarse_cg_solves_the_coarsest_system(hier):
 
 def test_vcycle_is_a_convergent_iteration(hier):
     """Stand-alone V-cycle iteration converges.  With the one-point rule its rate is slow
-    (about 0.8 here, also with an exact coarse solve and eta = 1): the hourglass modes of
-    Sec. 4 degrade stand-alone multigrid, as Fig. 2 (left) reports; FGMRES absorbs it."""
+    (point Jacobi: about 0.8 here, also with an exact coarse solve and eta = 1): the hourglass
+    modes of Sec. 4 degrade stand-alone multigrid, as Fig. 2 (left) reports."""
     K = hier.K[0]
     b = inputs.normal(K.shape[0], 7)
     x = np.zeros_like(b)
