@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--n_r", type=int, default=129)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-solve", dest="no_solve", action="store_true",
-                    help="do not run the Stokes-solve measurements after the operator steps")
+                    help="do not run the Stokes-solve and serving measurements after the operator steps")
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=256)
     return ap.parse_args()
 
 
@@ -204,6 +205,54 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode):
                 "rel_residual": st["rel_residual"], "converged": bool(st["converged"]), "dofs": nv + npr}
     finally:
         tn.tn_mesh_destroy(m)
+
+
+def serving_stream(tn, n_req=256, seed=0, load=0.7):
+    """Serving workload: seeded Stokes requests (lateral level U{3..6}, radial layers U{9,17,33,65},
+    viscosity contrast log-uniform in [1, 1e4], temperature perturbation degree U{2..8}, order
+    U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), FP32 inner solves with FP64 refinement to 1e-8.
+    Phase 1 submits all requests at once (saturated throughput); phase 2 submits them with
+    Poisson arrivals at `load` x the saturated rate and reports latency percentiles."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(n_req):
+        l = int(rng.integers(3, 7))
+        nr = int(rng.choice([9, 17, 33, 65]))
+        contrast = 10.0 ** rng.uniform(0.0, 4.0)
+        deg = int(rng.integers(2, 9))
+        order = int(rng.integers(0, deg + 1))
+        amp = float(rng.uniform(0.01, 0.05))
+        reqs.append(dict(lateral_level=l, radial_layers=nr, E=math.log(contrast), Ra=7e3, t_degree=deg,
+                         t_order=order, t_amplitude=amp))
+    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4))
+    try:
+        tickets = [tn.tn_server_submit(srv, **q) for q in reqs]
+        res = [tn.tn_server_wait(srv, t) for t in tickets]
+        t_first = min(r["t_submit"] for r in res)
+        sat = n_req / (max(r["t_end"] for r in res) - t_first)
+        ok_sat = sum(1 for r in res if r["status"] == tn.TN_OK)
+        rate = load * sat
+        gaps = rng.exponential(1.0 / rate, size=n_req)
+        due = np.cumsum(gaps)
+        t0 = time.perf_counter()
+        tickets = []
+        for q, d in zip(reqs, due):
+            wait = d - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets.append(tn.tn_server_submit(srv, **q))
+        res = [tn.tn_server_wait(srv, t) for t in tickets]
+        lat = np.array([r["t_end"] - r["t_submit"] for r in res])
+        span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
+        ok = sum(1 for r in res if r["status"] == tn.TN_OK)
+        its = [r["iterations"] for r in res]
+        return {"requests": n_req, "saturated_solves_per_s": sat, "saturated_converged": ok_sat,
+                "poisson_rate_per_s": rate, "solves_per_s": n_req / span, "p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)), "converged": ok,
+                "max_rel_residual": max(r["rel_residual"] for r in res), "median_iterations": float(np.median(its)),
+                "max_active": 4, "mode": "FP32 inner + FP64 refinement, rtol 1e-8"}
+    finally:
+        tn.tn_server_destroy(srv)
 
 
 def main():
@@ -367,6 +416,7 @@ def main():
                 rmx = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED)
                 solves[name] = {"fp64": r64, "mixed": rmx, "mixed_speedup": r64["seconds"] / rmx["seconds"]}
             line["solves"] = solves
+            line["serving"] = serving_stream(tn, args.serve_requests, args.seed)
         if world == 1:
             dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
             line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

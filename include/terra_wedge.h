@@ -280,6 +280,59 @@ tn_status tn_solve_default_opts(tn_solve_opts* opts);
 tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f_dev, const double* g_dev,
                           double* const* u_dev, double* p_dev, tn_solve_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Serving: continuous batching of Stokes solves (the paper has no serving layer).
+ * tn_server_submit queues a request and returns at once.  max_active worker threads, each
+ * with its own stream, take the first queued request that fits the device-memory budget
+ * (memory_fraction x free memory when the server was created) and run tn_stokes_solve on it,
+ * so solves of different requests overlap on the GPU.  Mesh hierarchies stay resident per
+ * shape and are reused; idle ones are evicted least recently used when a new shape needs
+ * room.  A request larger than the whole budget completes at once with status TN_ENOMEM.
+ * Each request's result is independent of the other requests running (own mesh, vectors and
+ * stream, fixed-order reductions).
+ * Request temperature: T = r_in (r - r_out) / (r (r_in - r_out))
+ *   + t_amplitude cos(t_order phi) P_l^m(cos theta) / max|P_l^m| sin(pi (r - r_in) / (r_out - r_in)),
+ * l = t_degree, m = t_order; viscosity exp(E (1/2 - T)); buoyancy Ra T r_hat; free-slip.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct tn_server tn_server;
+typedef struct {
+  int max_active;          /* concurrent solves (4) */
+  double memory_fraction;  /* share of the free device memory the server may hold (0.8) */
+  int mode;                /* tn_solve_mode of every solve (TN_SOLVE_MIXED) */
+  double rtol;             /* 1e-8 */
+  int keep_solutions;      /* 1: keep a host copy of every solution for tn_server_solution (0) */
+} tn_server_opts;
+typedef struct {
+  int lateral_level, radial_layers;
+  double r_in, r_out;
+  double E;                /* ln(viscosity contrast) */
+  double Ra;
+  int t_degree, t_order;
+  double t_amplitude;
+} tn_request;
+typedef struct {
+  int state;               /* 0 queued, 1 running, 2 done */
+  int status;              /* result of the solve once done (TN_OK, TN_ENOTCONVERGED, TN_ENOMEM, ...) */
+  int iterations, refinements;
+  double rel_residual;
+  double t_submit, t_start, t_end;  /* seconds since tn_server_create (host clock) */
+} tn_result;
+
+tn_status tn_server_default_opts(tn_server_opts* opts);
+/* Starts the worker threads on the current device.  opts may be NULL. */
+tn_status tn_server_create(const tn_server_opts* opts, tn_server** out);
+tn_status tn_server_submit(tn_server* srv, const tn_request* req, uint64_t* ticket);
+/* TN_OK and the result if the request is done, TN_EBUSY (result holds its state) otherwise. */
+tn_status tn_server_poll(tn_server* srv, uint64_t ticket, tn_result* res);
+/* Blocks until the request is done. */
+tn_status tn_server_wait(tn_server* srv, uint64_t ticket, tn_result* res);
+/* Host copy of a finished solution (keep_solutions = 1): u_host 3 x n_layout of level 0
+ * (component-major), p_host n_layout of level 1, layouts as for a mesh of the request's shape. */
+tn_status tn_server_solution(tn_server* srv, uint64_t ticket, double* u_host, double* p_host);
+tn_status tn_server_stats(tn_server* srv, int* queued, int* running, int* resident, double* reserved_bytes);
+/* Finishes every queued request, then stops the workers and frees everything. */
+tn_status tn_server_destroy(tn_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

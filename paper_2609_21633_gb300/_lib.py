@@ -61,6 +61,23 @@ class tn_solve_stats(ctypes.Structure):
 TN_SOLVE_F64, TN_SOLVE_MIXED = 0, 1
 
 
+class tn_server_opts(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("mode", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("keep_solutions", ctypes.c_int)]
+
+
+class tn_request(ctypes.Structure):
+    _fields_ = [("lateral_level", ctypes.c_int), ("radial_layers", ctypes.c_int), ("r_in", ctypes.c_double),
+                ("r_out", ctypes.c_double), ("E", ctypes.c_double), ("Ra", ctypes.c_double),
+                ("t_degree", ctypes.c_int), ("t_order", ctypes.c_int), ("t_amplitude", ctypes.c_double)]
+
+
+class tn_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
 _lib = None
 P = ctypes.c_void_p
 PP = ctypes.POINTER(ctypes.c_void_p)
@@ -91,6 +108,15 @@ _SIGS = {
     "tn_solve_default_opts": ([ctypes.POINTER(tn_solve_opts)], ctypes.c_int),
     "tn_stokes_solve": ([P, ctypes.POINTER(tn_solve_opts), PP, P, PP, P, ctypes.POINTER(tn_solve_stats), P],
                         ctypes.c_int),
+    "tn_server_default_opts": ([ctypes.POINTER(tn_server_opts)], ctypes.c_int),
+    "tn_server_create": ([ctypes.POINTER(tn_server_opts), ctypes.POINTER(P)], ctypes.c_int),
+    "tn_server_submit": ([P, ctypes.POINTER(tn_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "tn_server_poll": ([P, ctypes.c_uint64, ctypes.POINTER(tn_result)], ctypes.c_int),
+    "tn_server_wait": ([P, ctypes.c_uint64, ctypes.POINTER(tn_result)], ctypes.c_int),
+    "tn_server_solution": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
+    "tn_server_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "tn_server_destroy": ([P], ctypes.c_int),
 }
 
 
@@ -281,6 +307,65 @@ def tn_stokes_solve(mesh, f, g, u, p, opts=None, stream=None, check=True):
     if status != TN_OK and (check or status != TN_ENOTCONVERGED):
         _check(status)
     return {f: getattr(st, f) for f, _ in tn_solve_stats._fields_}
+
+
+def _result(r):
+    return {f: getattr(r, f) for f, _ in tn_result._fields_}
+
+
+def tn_server_default_opts(**kw):
+    o = tn_server_opts()
+    _check(lib().tn_server_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tn_server_create(opts=None):
+    o = opts if opts is not None else tn_server_default_opts()
+    out = P()
+    _check(lib().tn_server_create(ctypes.byref(o), ctypes.byref(out)))
+    return out
+
+
+def tn_server_submit(srv, lateral_level, radial_layers, E, Ra, t_degree, t_order, t_amplitude, r_in=0.55, r_out=1.0):
+    req = tn_request(lateral_level, radial_layers, r_in, r_out, E, Ra, t_degree, t_order, t_amplitude)
+    t = ctypes.c_uint64()
+    _check(lib().tn_server_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def tn_server_poll(srv, ticket):
+    """(done, result dict)"""
+    r = tn_result()
+    st = lib().tn_server_poll(srv, ticket, ctypes.byref(r))
+    if st not in (TN_OK, TN_EBUSY):
+        _check(st)
+    return st == TN_OK, _result(r)
+
+
+def tn_server_wait(srv, ticket):
+    r = tn_result()
+    _check(lib().tn_server_wait(srv, ticket, ctypes.byref(r)))
+    return _result(r)
+
+
+def tn_server_solution(srv, ticket, n_layout0, n_layout1):
+    import numpy as np
+    u = np.empty(3 * n_layout0)
+    p = np.empty(n_layout1)
+    _check(lib().tn_server_solution(srv, ticket, u.ctypes.data_as(P), p.ctypes.data_as(P)))
+    return u.reshape(3, -1), p
+
+
+def tn_server_stats(srv):
+    q, r, res, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().tn_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(res), ctypes.byref(b)))
+    return {"queued": q.value, "running": r.value, "resident": res.value, "reserved_bytes": b.value}
+
+
+def tn_server_destroy(srv):
+    _check(lib().tn_server_destroy(srv))
 
 
 def header_entry_points():

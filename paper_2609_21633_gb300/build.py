@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libterra_wedge.so"
-SOURCES = ["kernels.cu", "solver.cu", "api.cu", "noalloc.cu", "mesh.cpp"]
+SOURCES = ["kernels.cu", "solver.cu", "server.cu", "api.cu", "noalloc.cu", "mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

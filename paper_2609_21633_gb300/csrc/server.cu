@@ -1,0 +1,413 @@
+// Continuous-batching Stokes solve server.
+//
+// Requests (shell size, viscosity contrast, buoyancy and an analytic temperature
+// perturbation) are queued on submit.  max_active worker threads, each with its own CUDA
+// stream, take the first queued request that can be admitted and solve it with
+// tn_stokes_solve; solves of different requests therefore overlap on the device.
+// Admission is by device memory: every mesh hierarchy the server holds (in use or idle)
+// counts against a budget fixed at creation (memory_fraction x free memory); idle hierarchies
+// are kept resident per shape and reused by later requests of the same shape, and evicted,
+// least recently used first, when a new shape needs the room.  A request whose estimated
+// footprint exceeds the whole budget completes at once with TN_ENOMEM.
+// Every request runs on its own mesh, vectors and stream with fixed-order reductions, so its
+// result does not depend on what else is running.
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace tn {
+namespace {
+
+// Prescribed temperature at every node of level 0: conductive profile plus
+// amp * cos(m phi) * P_l^m(cos theta) / pmax * sin(pi (r - r_in) / (r_out - r_in)).
+__global__ void k_temperature(Dims D, const double* __restrict__ svec, const double* __restrict__ rad, double r_in,
+                              double r_out, int l, int m, double amp_over_pmax, double* T) {
+  const int M = D.N + 1;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)10 * D.n_r * M * M) return;
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
+            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int64_t so = ((int64_t)d * M + i) * D.P + j;
+  const double sx = svec[so], sy = svec[so + D.n_lat_layout], sz = svec[so + 2 * D.n_lat_layout];
+  const double r = rad[k];
+  const double x = fmin(1.0, fmax(-1.0, sz));
+  const double phi = atan2(sy, sx);
+  // associated Legendre P_l^m(x), unnormalised, no Condon-Shortley phase (standard recurrence)
+  double pmm = 1.0, somx2 = sqrt(fmax(0.0, (1.0 - x) * (1.0 + x))), fact = 1.0;
+  for (int q = 0; q < m; ++q) pmm *= fact * somx2, fact += 2.0;
+  double plm = pmm;
+  if (l > m) {
+    double pmmp1 = x * (2 * m + 1) * pmm;
+    plm = pmmp1;
+    for (int ll = m + 2; ll <= l; ++ll) {
+      const double pll = (x * (2 * ll - 1) * pmmp1 - (ll + m - 1) * pmm) / (ll - m);
+      pmm = pmmp1, pmmp1 = pll, plm = pll;
+    }
+  }
+  const double Tc = r_in * (r - r_out) / (r * (r_in - r_out));
+  const double pi = 3.14159265358979323846;
+  T[(int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j] =
+      Tc + amp_over_pmax * cos(m * phi) * plm * sin(pi * (r - r_in) / (r_out - r_in));
+}
+
+double pmax_of(int l, int m) {
+  double best = 0.0;
+  for (int s = 0; s <= 4000; ++s) {
+    const double x = -1.0 + 2.0 * s / 4000.0;
+    double pmm = 1.0, somx2 = std::sqrt(std::max(0.0, (1.0 - x) * (1.0 + x))), fact = 1.0;
+    for (int q = 0; q < m; ++q) pmm *= fact * somx2, fact += 2.0;
+    double plm = pmm;
+    if (l > m) {
+      double pmmp1 = x * (2 * m + 1) * pmm;
+      plm = pmmp1;
+      for (int ll = m + 2; ll <= l; ++ll) {
+        const double pll = (x * (2 * ll - 1) * pmmp1 - (ll + m - 1) * pmm) / (ll - m);
+        pmm = pmmp1, pmmp1 = pll, plm = pll;
+      }
+    }
+    best = std::max(best, std::fabs(plm));
+  }
+  return best > 0 ? best : 1.0;
+}
+
+struct Shape {
+  int l, nr;
+  double r_in, r_out;
+  bool operator<(const Shape& o) const {
+    if (l != o.l) return l < o.l;
+    if (nr != o.nr) return nr < o.nr;
+    if (r_in != o.r_in) return r_in < o.r_in;
+    return r_out < o.r_out;
+  }
+};
+
+// Device bytes a resident hierarchy may hold (tables, viscosity, multigrid and FGMRES(30)
+// workspaces in FP64 and FP32), estimated from the finest node layout.
+size_t footprint(const Shape& s) {
+  const int N = 1 << s.l;
+  const size_t P = (size_t)(N + 4) / 4 * 4;
+  const size_t n0 = (size_t)10 * s.nr * (N + 1) * P;
+  // per layout entry: 3 components x (63 Krylov + 30 multigrid / work vectors) x (8 + 4) bytes,
+  // plus geometry, viscosity and masks; the coarser levels add about 1/7.
+  return (size_t)((double)n0 * 3.0 * 93.0 * 12.0 * 8.0 / 7.0) + ((size_t)64 << 20);
+}
+
+struct Job {
+  uint64_t ticket;
+  tn_request req;
+  tn_result res;
+  std::vector<double> u, p;  // host copy of the solution (keep_solutions)
+  bool done = false;
+};
+
+struct Pooled {
+  tn_mesh* mesh;
+  Shape shape;
+  uint64_t last_use;
+};
+
+}  // namespace
+}  // namespace tn
+
+struct tn_server {
+  tn_server_opts opts;
+  int device = 0;
+  size_t budget = 0, reserved = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<tn::Job*> queue;
+  std::map<uint64_t, tn::Job*> jobs;
+  std::vector<tn::Pooled> idle;
+  uint64_t next_ticket = 1, use_clock = 0;
+  int running = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::chrono::steady_clock::time_point t0;
+  double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace tn {
+namespace {
+
+// Under the lock: find a mesh for s (idle of the same shape, or room for a new one after evicting
+// idle meshes of other shapes).  Returns 1 and sets *out (nullptr: create a new one) on success.
+int acquire_locked(tn_server* S, const Shape& s, tn_mesh** out, std::vector<tn_mesh*>& to_free) {
+  for (size_t q = 0; q < S->idle.size(); ++q) {
+    const Shape& t = S->idle[q].shape;
+    if (!(t < s) && !(s < t)) {
+      *out = S->idle[q].mesh;
+      S->idle.erase(S->idle.begin() + q);
+      return 1;
+    }
+  }
+  const size_t need = footprint(s);
+  while (S->reserved + need > S->budget && !S->idle.empty()) {
+    size_t lru = 0;
+    for (size_t q = 1; q < S->idle.size(); ++q)
+      if (S->idle[q].last_use < S->idle[lru].last_use) lru = q;
+    S->reserved -= footprint(S->idle[lru].shape);
+    to_free.push_back(S->idle[lru].mesh);
+    S->idle.erase(S->idle.begin() + lru);
+  }
+  if (S->reserved + need > S->budget) return 0;
+  S->reserved += need;
+  *out = nullptr;
+  return 1;
+}
+
+void run_job(tn_server* S, Job* J, tn_mesh* mesh, cudaStream_t st) {
+  const tn_request& R = J->req;
+  tn_status s = TN_OK;
+  if (!mesh) s = tn_mesh_create(R.lateral_level, R.radial_layers, R.r_in, R.r_out, nullptr, &mesh);
+  J->res.status = s;
+  if (s != TN_OK) {
+    mesh = nullptr;
+  } else {
+    const Level& L0 = mesh->lv[0];
+    const Level& L1 = mesh->lv[1];
+    double *T = nullptr, *f[3] = {nullptr, nullptr, nullptr}, *u[3] = {nullptr, nullptr, nullptr}, *p = nullptr;
+    // per-request vectors come from the stream-ordered pool (no device-wide synchronisation)
+    cudaError_t e = cudaMallocAsync((void**)&T, sizeof(double) * L0.n_layout, st);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&f[c], sizeof(double) * L0.n_layout, st);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&u[c], sizeof(double) * L0.n_layout, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&p, sizeof(double) * L1.n_layout, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(T, 0, sizeof(double) * L0.n_layout, st);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMemsetAsync(f[c], 0, sizeof(double) * L0.n_layout, st);
+    if (e == cudaSuccess) {
+      const int64_t n = (int64_t)10 * L0.n_r * (L0.N + 1) * (L0.N + 1);
+      const double amp = R.t_amplitude / pmax_of(R.t_degree, R.t_order);
+      k_temperature<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dims(L0), L0.s64, L0.rad64, R.r_in, R.r_out,
+                                                                  R.t_degree, R.t_order, amp, T);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      s = TN_ECUDA;
+    } else {
+      tn_visc_law law{R.E, 0.0, 1.0};
+      s = tn_set_temperature(mesh, T, &law, st);
+      if (s == TN_OK) s = tn_buoyancy(mesh, T, R.Ra, f, st);
+      tn_solve_opts so;
+      tn_solve_default_opts(&so);
+      so.mode = S->opts.mode;
+      so.rtol = S->opts.rtol;
+      tn_solve_stats stats{};
+      if (s == TN_OK) {
+        s = tn_stokes_solve(mesh, &so, (const double* const*)f, nullptr, u, p, &stats, st);
+        J->res.iterations = stats.iterations;
+        J->res.refinements = stats.refinements;
+        J->res.rel_residual = stats.rel_residual;
+      }
+      if ((s == TN_OK || s == TN_ENOTCONVERGED) && S->opts.keep_solutions) {
+        J->u.resize((size_t)3 * L0.n_layout);
+        J->p.resize((size_t)L1.n_layout);
+        for (int c = 0; c < 3; ++c)
+          cudaMemcpyAsync(J->u.data() + (size_t)c * L0.n_layout, u[c], sizeof(double) * L0.n_layout,
+                          cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(J->p.data(), p, sizeof(double) * L1.n_layout, cudaMemcpyDeviceToHost, st);
+      }
+    }
+    for (double* q : {T, f[0], f[1], f[2], u[0], u[1], u[2], p})
+      if (q) cudaFreeAsync(q, st);
+    cudaStreamSynchronize(st);
+    J->res.status = s;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (mesh) S->idle.push_back(Pooled{mesh, Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, ++S->use_clock});
+    else S->reserved -= footprint(Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out});
+    J->res.t_end = S->now();
+    J->res.state = 2;
+    J->done = true;
+    --S->running;
+  }
+  S->cv_done.notify_all();
+  S->cv_work.notify_all();
+}
+
+void worker(tn_server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  while (true) {
+    Job* J = nullptr;
+    tn_mesh* mesh = nullptr;
+    std::vector<tn_mesh*> to_free;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      while (true) {
+        if (S->stop && S->queue.empty()) break;
+        for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+          const tn_request& R = (*it)->req;
+          if (acquire_locked(S, Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, &mesh, to_free)) {
+            J = *it;
+            S->queue.erase(it);
+            break;
+          }
+        }
+        if (J) break;
+        S->cv_work.wait(lk);
+      }
+      if (!J) break;
+      ++S->running;
+      J->res.state = 1;
+      J->res.t_start = S->now();
+    }
+    for (tn_mesh* m : to_free) tn_mesh_destroy(m);
+    run_job(S, J, mesh, st);
+  }
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+}  // namespace tn
+
+using namespace tn;
+
+extern "C" {
+
+tn_status tn_server_default_opts(tn_server_opts* o) {
+  if (!o) return TN_EINVAL;
+  o->max_active = 4;
+  o->memory_fraction = 0.8;
+  o->mode = TN_SOLVE_MIXED;
+  o->rtol = 1e-8;
+  o->keep_solutions = 0;
+  return TN_OK;
+}
+
+tn_status tn_server_create(const tn_server_opts* opts, tn_server** out) {
+  if (!out) return TN_EINVAL;
+  tn_server_opts o;
+  tn_server_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_active < 1 || o.max_active > 64 || !(o.memory_fraction > 0.0) || o.memory_fraction > 1.0 ||
+      !(o.rtol > 0.0)) {
+    set_error("tn_server_create: invalid options");
+    return TN_EINVAL;
+  }
+  tn_server* S = new tn_server();
+  S->opts = o;
+  cudaGetDevice(&S->device);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    delete S;
+    set_error("tn_server_create: cudaMemGetInfo failed");
+    return TN_ECUDA;
+  }
+  S->budget = (size_t)(o.memory_fraction * (double)free_b);
+  S->t0 = std::chrono::steady_clock::now();
+  for (int w = 0; w < o.max_active; ++w) S->workers.emplace_back(worker, S);
+  *out = S;
+  return TN_OK;
+}
+
+tn_status tn_server_submit(tn_server* S, const tn_request* req, uint64_t* ticket) {
+  if (!S || !req || !ticket) return TN_EINVAL;
+  if (req->lateral_level < 1 || req->radial_layers < 3 || (req->radial_layers - 1) % 2 != 0 ||
+      !(req->r_in > 0) || !(req->r_out > req->r_in) || req->t_degree < 0 || req->t_order < 0 ||
+      req->t_order > req->t_degree) {
+    set_error("tn_server_submit: invalid request");
+    return TN_EINVAL;
+  }
+  Job* J = new Job();
+  J->req = *req;
+  std::memset(&J->res, 0, sizeof(J->res));
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      delete J;
+      set_error("tn_server_submit: server is shutting down");
+      return TN_ESTATE;
+    }
+    J->ticket = S->next_ticket++;
+    J->res.t_submit = S->now();
+    J->res.state = 0;
+    S->jobs[J->ticket] = J;
+    const Shape s{req->lateral_level, req->radial_layers, req->r_in, req->r_out};
+    if (footprint(s) > S->budget) {  // can never be admitted
+      J->res.status = TN_ENOMEM;
+      J->res.state = 2;
+      J->res.t_start = J->res.t_end = J->res.t_submit;
+      J->done = true;
+    } else {
+      S->queue.push_back(J);
+    }
+    *ticket = J->ticket;
+  }
+  S->cv_work.notify_all();
+  return TN_OK;
+}
+
+tn_status tn_server_poll(tn_server* S, uint64_t ticket, tn_result* res) {
+  if (!S || !res) return TN_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) {
+    set_error("tn_server_poll: unknown ticket");
+    return TN_EINVAL;
+  }
+  *res = it->second->res;
+  return it->second->done ? TN_OK : TN_EBUSY;
+}
+
+tn_status tn_server_wait(tn_server* S, uint64_t ticket, tn_result* res) {
+  if (!S || !res) return TN_EINVAL;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) {
+    set_error("tn_server_wait: unknown ticket");
+    return TN_EINVAL;
+  }
+  Job* J = it->second;
+  S->cv_done.wait(lk, [&] { return J->done; });
+  *res = J->res;
+  return TN_OK;
+}
+
+tn_status tn_server_solution(tn_server* S, uint64_t ticket, double* u_host, double* p_host) {
+  if (!S || !u_host || !p_host) return TN_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end() || !it->second->done || it->second->u.empty()) {
+    set_error("tn_server_solution: no stored solution for this ticket (unknown, pending, or keep_solutions = 0)");
+    return TN_EINVAL;
+  }
+  std::memcpy(u_host, it->second->u.data(), sizeof(double) * it->second->u.size());
+  std::memcpy(p_host, it->second->p.data(), sizeof(double) * it->second->p.size());
+  return TN_OK;
+}
+
+tn_status tn_server_stats(tn_server* S, int* queued, int* running, int* resident, double* reserved_bytes) {
+  if (!S) return TN_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (queued) *queued = (int)S->queue.size();
+  if (running) *running = S->running;
+  if (resident) *resident = (int)S->idle.size() + S->running;
+  if (reserved_bytes) *reserved_bytes = (double)S->reserved;
+  return TN_OK;
+}
+
+tn_status tn_server_destroy(tn_server* S) {
+  if (!S) return TN_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (auto& q : S->idle) tn_mesh_destroy(q.mesh);
+  for (auto& kv : S->jobs) delete kv.second;
+  delete S;
+  return TN_OK;
+}
+
+}  // extern "C"

@@ -465,7 +465,7 @@ const float* rad_of<float>(const Level& L) {
   return L.rad32;
 }
 
-cudaError_t g_err = cudaSuccess;
+thread_local cudaError_t g_err = cudaSuccess;
 inline void ck(cudaError_t e) {
   if (g_err == cudaSuccess && e != cudaSuccess) g_err = e;
 }
