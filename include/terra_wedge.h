@@ -220,7 +220,12 @@ tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double
  * or coarse_max_iters; with free-slip on both surfaces the rigid rotations (an exact null space)
  * are projected out of its right-hand side and solution.
  * Transfers: restriction P^T then the coarse boundary projector; prolongation P then the fine
- * boundary projector (tn_restrict / tn_prolong with apply_bc = 1).
+ * boundary projector (as tn_restrict / tn_prolong with apply_bc = 1).
+ * Multigrid levels (semi-coarsening): with q = (r_out - r_in) 2^l / (atan(2) r_mid (N_r - 1)) the
+ * ratio of radial to lateral cell size, the next level coarsens laterally only if q >= 2,
+ * radially only if q <= 1/2, both directions otherwise (or the one still possible); the
+ * hierarchy ends when the preferred direction cannot coarsen.  Levels are numbered 0 (finest)
+ * upwards; while they coincide with the mesh's levels the mesh's tables are shared.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
   int pre_smooth, post_smooth; /* Chebyshev steps per level (2, 2) */

@@ -8,8 +8,12 @@ remaining choices are readings):
 * level operators K_h = P_h A_h P_h + (I - P_h), re-discretised with the coarse viscosity
   (mean of the 8 children); D_h = the 3x3 node-block diagonal of K_h (block Jacobi; reading:
   the paper does not say which diagonal its Chebyshev smoother uses);
-* transfers: prolongation P_h T_h (nested iso-interpolation, then the fine boundary
-  projector), restriction P_{h+1} T_h^T;
+* level shapes: each coarser level halves the lateral and / or radial resolution according
+  to the cells' radial / lateral size ratio q (semi-coarsening where the cells are
+  anisotropic; see ``mg_shapes``, a reading: the paper states no coarsening rule);
+* transfers: prolongation P_h T_h (nested iso-interpolation in the coarsened directions,
+  identity in a direction that is not coarsened, then the fine boundary projector),
+  restriction P_{h+1} T_h^T;
 * Chebyshev acceleration (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1) with
   D^-1 preconditioning, two iterations per smoothing step, on [lo, hi] x lambda_h;
   lambda_h from power iterations on D^-1 K_h started from the restricted start vector;
@@ -26,10 +30,75 @@ from .fields import coarsen_viscosity
 from .mesh import ShellMesh
 
 
+def mg_shapes(level, n_r, r_in, r_out):
+    """(lateral level, node layers) of every multigrid level.  q = radial / lateral cell size
+    = (r_out - r_in) 2^l / (atan(2) r_mid (n_r - 1)); q >= 2: coarsen laterally only,
+    q <= 1/2: radially only, otherwise both (or the one still possible); stop when the
+    preferred direction cannot coarsen (lateral needs l >= 2, radial an even cell count)."""
+    out = [(level, n_r)]
+    edge = 1.1071487177940904
+    while True:
+        l, nr = out[-1]
+        R = nr - 1
+        can_lat, can_rad = l >= 2, R % 2 == 0 and R >= 2
+        q = (r_out - r_in) * float(1 << l) / (edge * (0.5 * (r_in + r_out)) * float(R))
+        if q >= 2.0:
+            if not can_lat:
+                break
+            nxt = (l - 1, nr)
+        elif q <= 0.5:
+            if not can_rad:
+                break
+            nxt = (l, R // 2 + 1)
+        elif can_lat and can_rad:
+            nxt = (l - 1, R // 2 + 1)
+        elif can_lat:
+            nxt = (l - 1, nr)
+        elif can_rad:
+            nxt = (l, R // 2 + 1)
+        else:
+            break
+        out.append(nxt)
+    return out
+
+
 def vec_prolongation(fine, coarse):
-    """Nested interpolation for 3-component fields in component-major numbering."""
-    T = O.prolongation(fine, coarse)
+    """Nested interpolation for 3-component fields in component-major numbering; identity in a
+    direction the pair does not coarsen."""
+    if fine.N == coarse.N:
+        Pl = sp.identity(fine.n_lat, format="csr")
+    else:
+        Pl = O.lateral_prolongation(fine, coarse)
+    if fine.n_r == coarse.n_r:
+        Pr = sp.identity(fine.n_r, format="csr")
+    else:
+        Pr = O.radial_prolongation(fine.n_r, coarse.n_r)
+    T = sp.kron(Pl, Pr, format="csr")
     return sp.block_diag([T, T, T], format="csr")
+
+
+def coarsen_viscosity_semi(fine, coarse, eta_fine):
+    """Mean of the child wedges: 8 for full coarsening, 4 (lateral only) or 2 (radial only)."""
+    if fine.N != coarse.N and fine.n_r != coarse.n_r:
+        return coarsen_viscosity(fine, coarse, eta_fine)
+    lab = coarse.wedge_labels()
+    d, I, J, w, K = lab.T
+    Nf, nkf = fine.N, fine.n_r - 1
+
+    def fid(d, i, j, ww, k):
+        return (((d * Nf + i) * Nf + j) * 2 + ww) * nkf + k
+
+    if fine.N == coarse.N:  # radial only: the two layers 2K, 2K+1
+        return 0.5 * (eta_fine[fid(d, I, J, w, 2 * K)] + eta_fine[fid(d, I, J, w, 2 * K + 1)])
+    kids0 = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    kids1 = [(1, 1, 1), (0, 1, 1), (1, 0, 1), (1, 1, 0)]
+    acc = np.zeros(coarse.n_wedges)
+    for (a0, b0, w0), (a1, b1, w1) in zip(kids0, kids1):
+        di = np.where(w == 0, a0, a1)
+        dj = np.where(w == 0, b0, b1)
+        ww = np.where(w == 0, w0, w1)
+        acc += eta_fine[fid(d, 2 * I + di, 2 * J + dj, ww, K)]
+    return acc / 4.0
 
 
 def block_jacobi_inverse(K):
@@ -60,19 +129,14 @@ def rotation_basis(mesh):
 class Hierarchy:
     def __init__(self, level, n_r, r_in, r_out, eta0, bc=(O.FREE, O.FREE), nlev=None, div_term=True,
                  lo=0.1, hi=1.1, power_iters=15, pre=2, post=2, coarse_max_iters=50, coarse_rtol=1e-3):
-        self.meshes = [ShellMesh(level, n_r, r_in, r_out)]
-        while True:
-            m = self.meshes[-1]
-            if m.level < 2 or (m.n_r - 1) % 2 != 0 or m.n_r < 3:
-                break
-            self.meshes.append(ShellMesh(m.level - 1, (m.n_r - 1) // 2 + 1, r_in, r_out))
+        self.meshes = [ShellMesh(l, nr, r_in, r_out) for l, nr in mg_shapes(level, n_r, r_in, r_out)]
         if nlev is not None:
             self.meshes = self.meshes[:nlev]
         self.nlev = len(self.meshes)
         self.bc = bc
         self.eta = [np.asarray(eta0, dtype=np.float64)]
         for h in range(1, self.nlev):
-            self.eta.append(coarsen_viscosity(self.meshes[h - 1], self.meshes[h], self.eta[h - 1]))
+            self.eta.append(coarsen_viscosity_semi(self.meshes[h - 1], self.meshes[h], self.eta[h - 1]))
         self.Pb = [O.projector_matrix(O.boundary_projectors(m, bc)) for m in self.meshes]
         self.K = [O.constrain_A(O.assemble_A(m, e, div_term), Pb)
                   for m, e, Pb in zip(self.meshes, self.eta, self.Pb)]

@@ -80,6 +80,71 @@ cudaError_t apply_BT_t(tn_mesh* m, int level, const void* p, void* const* y, cud
 
 
 }  // namespace
+
+// Host tables and device arrays of one level (lateral level l, nr node layers).
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out) {
+  std::vector<double> geo, lay, s, grp_s;
+  std::vector<int> gptr;
+  std::vector<int64_t> goff;
+  std::vector<uint8_t> owned;
+  std::string err;
+  build_level_host(L, l, nr, r_in, r_out, geo, lay, s, gptr, goff, grp_s, owned, err);
+  if (!err.empty()) return inval("tn_mesh_create: " + err);
+  L.h_grp_ptr = gptr;
+  L.h_grp_off = goff;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(upload(L.geo64, geo));
+  chk(upload(L.geo32, to_f32(geo)));
+  chk(upload(L.lay64, lay));
+  chk(upload(L.lay32, to_f32(lay)));
+  chk(upload(L.s64, s));
+  chk(upload(L.s32, to_f32(s)));
+  chk(upload(L.grp_ptr, gptr));
+  chk(upload(L.grp_off, goff));
+  chk(upload(L.grp_s64, grp_s));
+  chk(upload(L.grp_s32, to_f32(grp_s)));
+  chk(upload(L.owned, owned));
+  chk(cudaMalloc((void**)&L.eta64, sizeof(double) * L.n_wedges));
+  chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
+  chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
+  chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));
+  {
+    // weight mask (canonical copies), radii, rotation Gram matrix over unique nodes
+    std::vector<uint8_t> wm((size_t)L.n_layout, 0);
+    const int M = L.N + 1;
+    double G[3][3] = {};
+    for (int d = 0; d < 10; ++d)
+      for (int i = 0; i <= L.N; ++i)
+        for (int j = 0; j <= L.N; ++j) {
+          const int64_t lat = ((int64_t)d * M + i) * L.P + j;
+          if (!owned[lat]) continue;
+          const double* s = &L.lat_xyz[(((size_t)d * M + i) * M + j) * 3];
+          for (int k = 0; k < L.n_r; ++k) {
+            wm[(size_t)(d * L.diamond_stride + k * L.layer_stride + (int64_t)i * L.P + j)] = 1;
+            const double r2 = L.radii[k] * L.radii[k];
+            for (int a2 = 0; a2 < 3; ++a2)
+              for (int b2 = 0; b2 < 3; ++b2) G[a2][b2] += r2 * ((a2 == b2 ? 1.0 : 0.0) - s[a2] * s[b2]);
+          }
+        }
+    std::memcpy(L.inertia, G, sizeof(G));
+    chk(upload(L.wmask, wm));
+    chk(upload(L.rad64, L.radii));
+    chk(upload(L.rad32, to_f32(L.radii)));
+  }
+  chk(cudaMemset(L.scr64, 0, sizeof(double) * L.n_layout));
+  chk(cudaMemset(L.scr32, 0, sizeof(float) * L.n_layout));
+  if (e != cudaSuccess) {
+    set_error(std::string("tn_mesh_create: device allocation failed: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+  }
+  return TN_OK;
+}
+
+void destroy_level(Level& L) { free_level(L); }
+
 }  // namespace tn
 
 using namespace tn;
@@ -115,67 +180,12 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   int l = lateral_level, nr = radial_layers;
   while (true) {
     m->lv.emplace_back();
-    Level& L = m->lv.back();
-    std::vector<double> geo, lay, s, grp_s;
-    std::vector<int> gptr;
-    std::vector<int64_t> goff;
-    std::vector<uint8_t> owned;
-    std::string err;
-    build_level_host(L, l, nr, r_in, r_out, geo, lay, s, gptr, goff, grp_s, owned, err);
-    if (!err.empty()) {
+    tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out);
+    if (s != TN_OK) {
+      std::string msg = tn_last_error();
       tn_mesh_destroy(m);
-      return inval("tn_mesh_create: " + err);
-    }
-    L.h_grp_ptr = gptr;
-    L.h_grp_off = goff;
-    cudaError_t e = cudaSuccess;
-    auto chk = [&](cudaError_t x) {
-      if (e == cudaSuccess) e = x;
-    };
-    chk(upload(L.geo64, geo));
-    chk(upload(L.geo32, to_f32(geo)));
-    chk(upload(L.lay64, lay));
-    chk(upload(L.lay32, to_f32(lay)));
-    chk(upload(L.s64, s));
-    chk(upload(L.s32, to_f32(s)));
-    chk(upload(L.grp_ptr, gptr));
-    chk(upload(L.grp_off, goff));
-    chk(upload(L.grp_s64, grp_s));
-    chk(upload(L.grp_s32, to_f32(grp_s)));
-    chk(upload(L.owned, owned));
-    chk(cudaMalloc((void**)&L.eta64, sizeof(double) * L.n_wedges));
-    chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
-    chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
-    chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));
-    {
-      // weight mask (canonical copies), radii, rotation Gram matrix over unique nodes
-      std::vector<uint8_t> wm((size_t)L.n_layout, 0);
-      const int M = L.N + 1;
-      double G[3][3] = {};
-      for (int d = 0; d < 10; ++d)
-        for (int i = 0; i <= L.N; ++i)
-          for (int j = 0; j <= L.N; ++j) {
-            const int64_t lat = ((int64_t)d * M + i) * L.P + j;
-            if (!owned[lat]) continue;
-            const double* s = &L.lat_xyz[(((size_t)d * M + i) * M + j) * 3];
-            for (int k = 0; k < L.n_r; ++k) {
-              wm[(size_t)(d * L.diamond_stride + k * L.layer_stride + (int64_t)i * L.P + j)] = 1;
-              const double r2 = L.radii[k] * L.radii[k];
-              for (int a2 = 0; a2 < 3; ++a2)
-                for (int b2 = 0; b2 < 3; ++b2) G[a2][b2] += r2 * ((a2 == b2 ? 1.0 : 0.0) - s[a2] * s[b2]);
-            }
-          }
-      std::memcpy(L.inertia, G, sizeof(G));
-      chk(upload(L.wmask, wm));
-      chk(upload(L.rad64, L.radii));
-      chk(upload(L.rad32, to_f32(L.radii)));
-    }
-    chk(cudaMemset(L.scr64, 0, sizeof(double) * L.n_layout));
-    chk(cudaMemset(L.scr32, 0, sizeof(float) * L.n_layout));
-    if (e != cudaSuccess) {
-      tn_mesh_destroy(m);
-      set_error(std::string("tn_mesh_create: device allocation failed: ") + cudaGetErrorString(e));
-      return e == cudaErrorMemoryAllocation ? TN_ENOMEM : TN_ECUDA;
+      set_error(msg);
+      return s;
     }
     const bool can_coarsen = l >= 2 && (nr - 1) % 2 == 0 && nr >= 3;
     if (!can_coarsen || (o.max_levels > 0 && (int)m->lv.size() >= o.max_levels)) break;

@@ -88,6 +88,9 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
                       std::string& err);
 
 void set_error(const std::string& msg);
+// Tables and device arrays of one level (api.cu); destroy_level frees them.
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out);
+void destroy_level(Level& L);
 void mg_invalidate(tn_mesh* mesh);
 
 // ---- kernel launchers (kernels.cu) --------------------------------------------------------

@@ -617,8 +617,10 @@ __global__ void k_block_inv(int64_t n, T* b0, T* b1, T* b2, T* b3, T* b4, T* b5)
 // edge midpoints, 1/4 where both apply.  Lateral parents of fine lattice position (i, j):
 // even/even -> (i/2, j/2); odd i -> ((i-1)/2, j/2), ((i+1)/2, j/2); odd j -> (i/2, (j-1)/2),
 // (i/2, (j+1)/2); odd/odd -> midpoint of the coarse anti-diagonal ((i+1)/2, (j-1)/2), ((i-1)/2, (j+1)/2).
+// Semi-coarsened level pairs (lateral factor lf or radial factor rf equal to 1) keep the
+// index in that direction (weight 1).
 template <typename T>
-__global__ void k_prolong(Dims F, Dims C, int ncomp, int apply_bc, const T* __restrict__ c0,
+__global__ void k_prolong(Dims F, Dims C, int lf, int rf, int ncomp, int apply_bc, const T* __restrict__ c0,
                           const T* __restrict__ c1, const T* __restrict__ c2, T* f0, T* f1, T* f2,
                           const T* __restrict__ svec, int bc_in, int bc_out) {
   const int N = F.N, M = N + 1;
@@ -627,8 +629,8 @@ __global__ void k_prolong(Dims F, Dims C, int ncomp, int apply_bc, const T* __re
   const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % F.n_r),
             d = (int)(tid / ((int64_t)M * M * F.n_r));
   int li[2], lj[2], nl;
-  if (!(i & 1) && !(j & 1)) {
-    li[0] = i / 2, lj[0] = j / 2, nl = 1;
+  if (lf == 1 || (!(i & 1) && !(j & 1))) {
+    li[0] = lf == 1 ? i : i / 2, lj[0] = lf == 1 ? j : j / 2, nl = 1;
   } else if ((i & 1) && !(j & 1)) {
     li[0] = (i - 1) / 2, lj[0] = j / 2, li[1] = (i + 1) / 2, lj[1] = j / 2, nl = 2;
   } else if (!(i & 1) && (j & 1)) {
@@ -637,7 +639,8 @@ __global__ void k_prolong(Dims F, Dims C, int ncomp, int apply_bc, const T* __re
     li[0] = (i + 1) / 2, lj[0] = (j - 1) / 2, li[1] = (i - 1) / 2, lj[1] = (j + 1) / 2, nl = 2;
   }
   int rk[2], nrk;
-  if (!(k & 1)) rk[0] = k / 2, nrk = 1;
+  if (rf == 1) rk[0] = k, nrk = 1;
+  else if (!(k & 1)) rk[0] = k / 2, nrk = 1;
   else rk[0] = (k - 1) / 2, rk[1] = (k + 1) / 2, nrk = 2;
   const T* cs[3] = {c0, c1, c2};
   T* fs[3] = {f0, f1, f2};
@@ -657,13 +660,15 @@ __global__ void k_prolong(Dims F, Dims C, int ncomp, int apply_bc, const T* __re
   for (int c = 0; c < ncomp; ++c) fs[c][idx] = v[c];
 }
 
-// Restriction P^T: coarse node (I, J, K) gathers the fine nodes it interpolates to: lateral
+// Restriction P^T: coarse node (I, J, K) gathers the fine nodes it interpolates to (semi-coarsened
+// pairs keep the index in the direction with factor 1): lateral
 // (2I, 2J) with weight 1 and its six lattice neighbours with weight 1/2, radial 2K (1) and
 // 2K +- 1 (1/2).  Fine nodes shared by several diamonds are counted by their canonical copy
 // only; the coarse copies are then summed by launch_interface.
 template <typename T>
-__global__ void k_restrict(Dims F, Dims C, int ncomp, const uint8_t* __restrict__ owned, const T* __restrict__ f0,
-                           const T* __restrict__ f1, const T* __restrict__ f2, T* c0, T* c1, T* c2) {
+__global__ void k_restrict(Dims F, Dims C, int lf, int rf, int ncomp, const uint8_t* __restrict__ owned,
+                           const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2, T* c0, T* c1,
+                           T* c2) {
   const int NC = C.N, MC = NC + 1, NF = F.N, MF = NF + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
@@ -674,12 +679,13 @@ __global__ void k_restrict(Dims F, Dims C, int ncomp, const uint8_t* __restrict_
   T* cs[3] = {c0, c1, c2};
   T v[3] = {0, 0, 0};
   for (int r = -1; r <= 1; ++r) {
-    const int kf = 2 * K + r;
+    if (rf == 1 && r != 0) continue;
+    const int kf = rf * K + r;
     if (kf < 0 || kf >= F.n_r) continue;
     const T wr = r == 0 ? (T)1 : (T)0.5;
     T lat[3] = {0, 0, 0};
-    for (int q = 0; q < 7; ++q) {
-      const int fi = 2 * I + nb[q][0], fj = 2 * J + nb[q][1];
+    for (int q = 0; q < (lf == 1 ? 1 : 7); ++q) {
+      const int fi = lf * I + nb[q][0], fj = lf * J + nb[q][1];
       if (fi < 0 || fj < 0 || fi > NF || fj > NF) continue;
       if (!owned[((int64_t)d * MF + fi) * F.P + fj]) continue;
       const T wl = q == 0 ? (T)1 : (T)0.5;
@@ -774,7 +780,7 @@ __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, dou
   eta[tid] = e;
 }
 
-__global__ void k_eta_coarsen(Dims F, Dims C, const double* __restrict__ ef, double* ec) {
+__global__ void k_eta_coarsen(Dims F, Dims C, int lf, int rf, const double* __restrict__ ef, double* ec) {
   const int NC = C.N, NF = F.N;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nw = (int64_t)10 * (C.n_r - 1) * NC * NC * 2;
@@ -784,12 +790,14 @@ __global__ void k_eta_coarsen(Dims F, Dims C, const double* __restrict__ ef, dou
             d = (int)(tid / (2 * (int64_t)NC * NC * (C.n_r - 1)));
   const int kid[2][4][3] = {{{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}}};
   double s = 0;
-  for (int c = 0; c < 4; ++c)
-    for (int r = 0; r < 2; ++r) {
-      const int fi = 2 * I + kid[w][c][0], fj = 2 * J + kid[w][c][1], fw = kid[w][c][2], kf = 2 * K + r;
+  const int nlat = lf == 2 ? 4 : 1;
+  for (int c = 0; c < nlat; ++c)
+    for (int r = 0; r < rf; ++r) {
+      const int fi = lf == 2 ? 2 * I + kid[w][c][0] : I, fj = lf == 2 ? 2 * J + kid[w][c][1] : J;
+      const int fw = lf == 2 ? kid[w][c][2] : w, kf = rf * K + r;
       s += ef[((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw];
     }
-  ec[tid] = s / 8.0;
+  ec[tid] = s / (double)(nlat * rf);
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* b, int64_t n) {
@@ -934,7 +942,8 @@ cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int
   const T* c2 = ncomp > 2 ? c[2] : c[0];
   T* f1 = ncomp > 1 ? f[1] : f[0];
   T* f2 = ncomp > 2 ? f[2] : f[0];
-  k_prolong<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), ncomp, apply_bc, c[0], c1, c2, f[0], f1, f2,
+  const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
+  k_prolong<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, apply_bc, c[0], c1, c2, f[0], f1, f2,
                                              Tab<T>::s(F), bc.in, bc.out);
   return cudaGetLastError();
 }
@@ -947,7 +956,8 @@ cudaError_t launch_restrict(const Level& F, const Level& C, BC bc, int ncomp, in
   const T* f2 = ncomp > 2 ? f[2] : f[0];
   T* c1 = ncomp > 1 ? c[1] : c[0];
   T* c2 = ncomp > 2 ? c[2] : c[0];
-  k_restrict<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), ncomp, F.owned, f[0], f1, f2, c[0], c1, c2);
+  const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
+  k_restrict<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, F.owned, f[0], f1, f2, c[0], c1, c2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_interface<T>(C, bc, ncomp, 0, c, nullptr, st);
@@ -964,7 +974,8 @@ cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double 
 }
 
 cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st) {
-  k_eta_coarsen<<<nblk(C.n_wedges, 256), 256, 0, st>>>(dims(F), dims(C), ef, ec);
+  const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
+  k_eta_coarsen<<<nblk(C.n_wedges, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ef, ec);
   return cudaGetLastError();
 }
 

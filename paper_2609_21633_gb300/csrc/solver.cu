@@ -417,12 +417,17 @@ struct PrecState {
   std::vector<KVec<T>> V, Z;          // FGMRES bases
   KVec<T> w, tmp;                     // work vectors
   KVec<T> ir_r, ir_c;                 // FP32 iterative refinement: inner rhs and correction
+  cudaGraphExec_t vgraph = nullptr;   // the V-cycle (level-0 b -> level-0 x) captured after set-up
   T* tu[3] = {nullptr, nullptr, nullptr};  // velocity scratch (level 0)
 };
 
 struct MGState {
   tn_mg_opts opts;
   int nlev = 0;
+  // Multigrid levels: geo[0] is the mesh's level 0; coarser levels are owned here and may be
+  // semi-coarsened (lateral only or radial only) where the cells are anisotropic.
+  std::vector<Level*> geo;
+  std::vector<Level*> owned_levels;
   double* S = nullptr;     // device scalars
   int* flag = nullptr;     // coarse CG stop flag
   double* part = nullptr;  // reduction partials [2][MAXV][RG]
@@ -430,6 +435,7 @@ struct MGState {
   PrecState<float> p32;
   std::vector<void*> allocs;
   int restart = 0;         // FGMRES bases allocated for this restart length
+  cudaStream_t cap = nullptr;  // stream used to capture the V-cycle graphs
 };
 
 namespace {
@@ -610,7 +616,7 @@ void project_rotations(MGState* m, const Level& L, T* const* u, cudaStream_t st,
 template <typename T>
 void apply_K_level(const tn_mesh* mesh, int h, const T* const* x, T* const* y, cudaStream_t st,
                    const int* skip = nullptr) {
-  ck(launch_apply_A<T>(mesh->lv[h], BC{mesh->bc_in, mesh->bc_out}, mesh->div_term, x, y, st, skip));
+  ck(launch_apply_A<T>(*mesh->mg->geo[h], BC{mesh->bc_in, mesh->bc_out}, mesh->div_term, x, y, st, skip));
 }
 
 // Block-Jacobi-preconditioned CG on the coarsest level: x = K^-1 b (x0 = 0); stops when
@@ -618,7 +624,7 @@ void apply_K_level(const tn_mesh* mesh, int h, const T* const* x, T* const* y, c
 template <typename T>
 void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   MGLevelT<T>& C = ps<T>(m).L[h];
-  const Level& L = mesh->lv[h];
+  const Level& L = *m->geo[h];
   const int64_t n = L.n_layout;
   const bool proj = rotations_singular(mesh);
   if (proj) project_rotations<T>(m, L, C.b.mm(), st);
@@ -661,7 +667,7 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
 template <typename T>
 void cheb_step(MGState* m, const tn_mesh* mesh, int h, bool zero_x, cudaStream_t st) {
   MGLevelT<T>& G = ps<T>(m).L[h];
-  const int64_t n = mesh->lv[h].n_layout;
+  const int64_t n = m->geo[h]->n_layout;
   const double a = m->opts.cheb_lo * G.lam, b = m->opts.cheb_hi * G.lam;
   const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
   const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
@@ -684,8 +690,8 @@ void vcycle_level(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   }
   MGLevelT<T>& G = ps<T>(m).L[h];
   MGLevelT<T>& C = ps<T>(m).L[h + 1];
-  const Level& F = mesh->lv[h];
-  const Level& Lc = mesh->lv[h + 1];
+  const Level& F = *m->geo[h];
+  const Level& Lc = *m->geo[h + 1];
   const BC bc{mesh->bc_in, mesh->bc_out};
   const int64_t n = F.n_layout;
   for (int s = 0; s < m->opts.pre_smooth; ++s) cheb_step<T>(m, mesh, h, s == 0, st);
@@ -712,6 +718,37 @@ double host_scalar(MGState* m, int slot, cudaStream_t st) {
   return v;
 }
 
+// One V-cycle on level 0 (G.b -> G.x of level 0) on stream st: the captured graph if there is
+// one, else the kernels directly.
+template <typename T>
+void run_vcycle(MGState* m, const tn_mesh* mesh, cudaStream_t st) {
+  PrecState<T>& P = ps<T>(m);
+  if (P.vgraph) ck(cudaGraphLaunch(P.vgraph, st));
+  else vcycle_level<T>(m, mesh, 0, st);
+}
+
+// Capture the V-cycle into a graph (kernel parameters such as the Chebyshev coefficients are
+// fixed at capture, so this runs at the end of every set-up).
+template <typename T>
+void capture_vcycle(MGState* m, const tn_mesh* mesh) {
+  PrecState<T>& P = ps<T>(m);
+  if (P.vgraph) {
+    cudaGraphExecDestroy(P.vgraph);
+    P.vgraph = nullptr;
+  }
+  if (!m->cap) ck(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
+  if (g_err != cudaSuccess) return;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return;
+  vcycle_level<T>(m, mesh, 0, m->cap);
+  cudaError_t e = cudaStreamEndCapture(m->cap, &g);
+  if (e == cudaSuccess && g_err == cudaSuccess) {
+    if (cudaGraphInstantiate(&P.vgraph, g, 0) != cudaSuccess) P.vgraph = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+}
+
 template <typename T>
 tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
   MGState* m = mesh->mg;
@@ -720,7 +757,7 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
   if (P.L.empty()) {
     P.L.resize(m->nlev);
     for (int h = 0; h < m->nlev; ++h) {
-      const int64_t n = mesh->lv[h].n_layout;
+      const int64_t n = m->geo[h]->n_layout;
       MGLevelT<T>& G = P.L[h];
       G.x = alloc3<T>(m, n), G.b = alloc3<T>(m, n), G.r = alloc3<T>(m, n), G.d = alloc3<T>(m, n);
       G.t = alloc3<T>(m, n);
@@ -735,7 +772,7 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
   }
   if (g_err != cudaSuccess) return TN_ENOMEM;
   // block-Jacobi: inverse 3x3 node blocks of P A P + I - P on every level
-  for (int h = 0; h < m->nlev; ++h) ck(launch_block_inv_A<T>(mesh->lv[h], bc, mesh->div_term, P.L[h].binv, st));
+  for (int h = 0; h < m->nlev; ++h) ck(launch_block_inv_A<T>(*m->geo[h], bc, mesh->div_term, P.L[h].binv, st));
   ck(launch_diag_pmass<T>(mesh->lv[0], mesh->lv[1], P.mdiag, st));
   // power-iteration start vectors: level 0 given or SplitMix64, coarser levels restricted
   {
@@ -763,12 +800,12 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
     }
   }
   for (int h = 1; h < m->nlev; ++h)
-    ck(launch_restrict<T>(mesh->lv[h - 1], mesh->lv[h], bc, 3, 1, P.L[h - 1].x.cc(), P.L[h].x.mm(), st));
+    ck(launch_restrict<T>(*m->geo[h - 1], *m->geo[h], bc, 3, 1, P.L[h - 1].x.cc(), P.L[h].x.mm(), st));
   // power iterations on D^-1 K of every smoothing level
   std::vector<double> lam(m->nlev, 0.0);
   for (int h = 0; h + 1 < m->nlev; ++h) {
     MGLevelT<T>& G = P.L[h];
-    const Level& L = mesh->lv[h];
+    const Level& L = *m->geo[h];
     const int64_t n = L.n_layout;
     const T* const* xx[1] = {G.x.cc()};
     dots<T>(m, L, 1, 3, xx, G.x.cc(), m->S + S_TMP, st);
@@ -839,6 +876,8 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
   }
   ck(cudaStreamSynchronize(st));
   if (g_err != cudaSuccess) return TN_ECUDA;
+  capture_vcycle<T>(m, mesh);
+  if (g_err != cudaSuccess) return TN_ECUDA;
   P.ready = true;
   return TN_OK;
 }
@@ -849,7 +888,7 @@ void vcycle_t(tn_mesh* mesh, const T* const* r, T* const* z, cudaStream_t st) {
   MGLevelT<T>& G = ps<T>(m).L[0];
   const int64_t n = mesh->lv[0].n_layout;
   for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(G.b.c[c], r[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
-  vcycle_level<T>(m, mesh, 0, st);
+  run_vcycle<T>(m, mesh, st);
   for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(z[c], G.x.c[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
 }
 
@@ -928,7 +967,7 @@ void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStr
   k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, -1.0, P4<T>((const T* const*)P.tu, 3), 1.0,
                                              M4<T>(G.b.mm(), 3));
   ckl();
-  vcycle_level<T>(m, mesh, 0, st);
+  run_vcycle<T>(m, mesh, st);
   for (int c = 0; c < 3; ++c)
     ck(cudaMemcpyAsync(z.u[c], G.x.c[c], sizeof(T) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
 }
@@ -1022,9 +1061,49 @@ KVec<T> wrap(T* const* u, T* p) {
 
 }  // namespace
 
+// Multigrid level shapes (lateral level, node layers) from the mesh's level 0 down.  A cell's
+// radial / lateral size ratio q = (r_out - r_in) 2^l / (atan(2) r_mid (N_r - 1)) (atan(2): the
+// angle between neighbouring icosahedron vertices, r_mid the mid radius) decides the next
+// level: q >= 2 coarsens laterally only, q <= 1/2 radially only, otherwise both directions
+// (or the one still possible); the hierarchy ends when the preferred direction cannot coarsen.
+std::vector<std::pair<int, int>> mg_shapes(int l0, int nr0, double r_in, double r_out) {
+  std::vector<std::pair<int, int>> out{{l0, nr0}};
+  const double edge = 1.1071487177940904;
+  while (true) {
+    const int l = out.back().first, nr = out.back().second, R = nr - 1;
+    const bool can_lat = l >= 2, can_rad = R % 2 == 0 && R >= 2;
+    const double q = (r_out - r_in) * (double)(1 << l) / (edge * (0.5 * (r_in + r_out)) * (double)R);
+    int nl = l, nn = nr;
+    if (q >= 2.0) {
+      if (!can_lat) break;
+      nl = l - 1;
+    } else if (q <= 0.5) {
+      if (!can_rad) break;
+      nn = R / 2 + 1;
+    } else if (can_lat && can_rad) {
+      nl = l - 1, nn = R / 2 + 1;
+    } else if (can_lat) {
+      nl = l - 1;
+    } else if (can_rad) {
+      nn = R / 2 + 1;
+    } else {
+      break;
+    }
+    out.push_back({nl, nn});
+  }
+  return out;
+}
+
 void mg_free(MGState* m) {
   if (!m) return;
   for (void* p : m->allocs) cudaFree(p);
+  for (Level* L : m->owned_levels) {
+    destroy_level(*L);
+    delete L;
+  }
+  if (m->p64.vgraph) cudaGraphExecDestroy(m->p64.vgraph);
+  if (m->p32.vgraph) cudaGraphExecDestroy(m->p32.vgraph);
+  if (m->cap) cudaStreamDestroy(m->cap);
   if (m->S) cudaFree(m->S);
   if (m->flag) cudaFree(m->flag);
   if (m->part) cudaFree(m->part);
@@ -1074,7 +1153,8 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
     set_error("tn_mg_setup: invalid multigrid options");
     return TN_EINVAL;
   }
-  const int avail = (int)mesh->lv.size();
+  const std::vector<std::pair<int, int>> shapes = mg_shapes(mesh->lv[0].l, mesh->lv[0].n_r, mesh->r_in, mesh->r_out);
+  const int avail = (int)shapes.size();
   const int nlev = o.levels <= 0 ? avail : std::min(o.levels, avail);
   if (nlev < 2) {
     set_error("tn_mg_setup: need at least two levels");
@@ -1090,6 +1170,26 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
   if (!m) {
     m = new MGState();
     m->nlev = nlev;
+    // level geometry: the mesh's levels while the multigrid coarsens fully, own levels after
+    bool same = true;
+    for (int h = 0; h < nlev; ++h) {
+      same = same && h < (int)mesh->lv.size() && mesh->lv[h].l == shapes[h].first &&
+             mesh->lv[h].n_r == shapes[h].second;
+      if (same) {
+        m->geo.push_back(&mesh->lv[h]);
+        continue;
+      }
+      Level* L = new Level();
+      tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out);
+      m->owned_levels.push_back(L);
+      if (cs != TN_OK) {
+        mesh->mg = m;
+        mg_free(m);
+        mesh->mg = nullptr;
+        return cs;
+      }
+      m->geo.push_back(L);
+    }
     ck(cudaMalloc((void**)&m->S, sizeof(double) * S_MAX));
     ck(cudaMemset(m->S, 0, sizeof(double) * S_MAX));
     ck(cudaMalloc((void**)&m->flag, sizeof(int)));
@@ -1101,6 +1201,12 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
     }
   }
   m->opts = o;
+  // viscosity of the multigrid's own levels: mean of the children on the level above
+  for (int h = 1; h < m->nlev; ++h) {
+    if (m->geo[h] == &mesh->lv[h]) continue;
+    ck(launch_eta_coarsen(*m->geo[h - 1], *m->geo[h], m->geo[h - 1]->eta64, m->geo[h]->eta64, st));
+    ck(launch_to_f32(m->geo[h]->eta64, m->geo[h]->eta32, m->geo[h]->n_wedges, st));
+  }
   tn_status s = prec == TN_F64 ? mg_setup_t<double>(mesh, v0, st) : mg_setup_t<float>(mesh, v0, st);
   if (s != TN_OK) set_error(std::string("tn_mg_setup: ") + cudaGetErrorString(g_err));
   return s;

@@ -33,8 +33,10 @@ def from_dev(mp, ts):
     return np.stack([mp.from_layout(t.double().cpu().numpy()) for t in ts])
 
 
-@pytest.mark.parametrize("level,n_r,bc", [(3, 9, (1, 0)), (3, 9, (0, 0)), (4, 9, (0, 0))])
+@pytest.mark.parametrize("level,n_r,bc", [(3, 9, (1, 0)), (3, 9, (0, 0)), (4, 9, (0, 0)),
+                                         (2, 17, (0, 0)), (4, 5, (1, 0))])
 def test_vcycle_f64_matches_oracle(tn, level, n_r, bc):
+    """Includes semi-coarsened hierarchies: (2, 17) coarsens radially first, (4, 5) laterally."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     eta = inputs.lognormal_viscosity(om.n_wedges, 3, 0.5)
     m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, bc[0], bc[1])
