@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-solve", dest="no_solve", action="store_true",
                     help="do not run the Stokes-solve and serving measurements after the operator steps")
-    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=256)
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=64,
+                    help="requests of the seeded serving stream measured after the solves (the full stream is 256)")
     return ap.parse_args()
 
 
@@ -161,6 +162,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------------------- ranks
+def max_over_ranks(value, dist, device):
+    """Largest value over all ranks (the slowest replica's time); the value itself without a
+    process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    timed by the slowest replica."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------------------- GPU arm
 def layout_temperature(tn, m, noise_seed=None, noise_scale=0.01):
     """Prescribed temperature (degree 3, order 2, amplitude 0.01) at every layout node of level 0,
@@ -246,7 +265,8 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7):
         span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
         ok = sum(1 for r in res if r["status"] == tn.TN_OK)
         its = [r["iterations"] for r in res]
-        return {"requests": n_req, "saturated_solves_per_s": sat, "saturated_converged": ok_sat,
+        return {"requests": n_req, "stream": "first %d of the seeded 256-request stream" % n_req,
+                "saturated_solves_per_s": sat, "saturated_converged": ok_sat,
                 "poisson_rate_per_s": rate, "solves_per_s": n_req / span, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "converged": ok,
                 "max_rel_residual": max(r["rel_residual"] for r in res), "median_iterations": float(np.median(its)),
@@ -333,10 +353,8 @@ def main():
         return t0.elapsed_time(t1), per, clk, step
 
     ms, per_op, clk, step = timed_steps(u, p, yA, q, yBT, dA, args.steps, max(3, args.warmup), True)
+    ms = max_over_ranks(ms, dist, dev)
     if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = tt.item()
         dist.barrier()
     # the same step in FP32 (the inner-solve precision of the mixed path)
     u32 = [t.float() for t in u]
@@ -346,7 +364,7 @@ def main():
     del u32, p32, q32, yA32, yBT32, dA32
 
     nv, npr, ndof = dof_counts(args.level, args.n_r)
-    value = world * ndof * args.steps / (ms / 1e3) / 1e9
+    value = job_throughput(world, ndof * args.steps, ms / 1e3) / 1e9
 
     # ---- end to end through the public API: pinned host inputs -> device -> step -> host outputs
     hu = [t.cpu().pin_memory() for t in u]
@@ -375,12 +393,8 @@ def main():
         e2e_step()
     c1.record(st)
     torch.cuda.synchronize()
-    e2e_ms = c0.elapsed_time(c1)
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = tt.item()
-    e2e_value = world * ndof * e2e_steps / (e2e_ms / 1e3) / 1e9
+    e2e_ms = max_over_ranks(c0.elapsed_time(c1), dist, dev)
+    e2e_value = job_throughput(world, ndof * e2e_steps, e2e_ms / 1e3) / 1e9
 
     if rank == 0:
         cells = 10 * 4 ** args.level * (args.n_r - 1)
