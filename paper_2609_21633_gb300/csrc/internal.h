@@ -10,6 +10,8 @@
 
 namespace tn {
 
+constexpr int kLayerStride = 8;  // values per radial cell in the layer table
+
 // Per-level mesh data.  Host vectors hold the definition; device pointers are
 // owned by the level and freed by tn_mesh_destroy.
 struct Level {
@@ -24,7 +26,8 @@ struct Level {
   // q = 0..8: M^{-1}[m][x] (row-major), q = 9: |det M|, M = [s1 - s0, s2 - s0, (s0+s1+s2)/3].
   double* geo64 = nullptr;
   float* geo32 = nullptr;
-  // Per radial cell k: (1/(2 rho), 1/(6 h), rho^2 h, rho), rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
+  // Per radial cell k (kLayerStride values): w0 = 1/(2 rho), w1 = 1/(6 h), vol = rho^2 h, rho,
+  // w1 / w0, vol w0^2, vol w0, 0; rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
   double* lay64 = nullptr;
   float* lay32 = nullptr;
   // Lateral unit vectors s, SoA [3][10 (N+1) P] in lateral layout (d (N+1) + i) P + j.

@@ -80,88 +80,153 @@ struct Tab<float> {
 
 
 // ------------------------------------------------------------------------------------ element ops
+// An op processes both wedges of one hexahedral cell.  Inputs are the nodal values at the
+// cell's four lateral corners (00, 10, 01, 11) on its bottom (ub) and top (ut) node layer;
+// outputs are added to the same eight node slots (accb, acct).  Wedge-local lateral node a of
+// wedge w sits at corner kCorner[w][a]: W0 = (00, 10, 01), W1 = (11, 01, 10).  `lc` points at
+// the cell layer's table entry (w0, w1, vol, rho, r = w1 / w0, vol w0^2, vol w0).
+//
+// With a_xi = s_c1 - s_c0, a_eta = s_c2 - s_c0, a_zeta = d_c0 + d_c1 + d_c2 (s = top + bottom,
+// d = top - bottom, per component; the reference gradients scaled to {-1, 0, 1}), the strain
+// G' = a_xi M^-1[0,:] + a_eta M^-1[1,:] + r a_zeta M^-1[2,:] is grad u / w0, and
+// S'' = vol w0^2 |det M| eta (G' + G'^T - 2/3 tr G' I) is the stress of Eq. (stress) times
+// V w0.  Then H[:,0] = S'' M^-1[0,:]^T, H[:,1] = S'' M^-1[1,:]^T, H[:,2] = r S'' M^-1[2,:]^T
+// and node (a, bottom / top) receives X_a -/+ H[:,2], X = (-H[:,0] - H[:,1], H[:,0], H[:,1]).
+__device__ constexpr int kCorner[2][3] = {{0, 1, 2}, {3, 2, 1}};
+
 // Viscous block: Eq. (epsq) then Eq. (localapply) at q_c.
 template <typename T>
 struct OpA {
   static constexpr int NIN = 3, NOUT = 3;
+  static constexpr bool USES_ETA = true;
   int div_term;
-  __device__ __forceinline__ void operator()(const T (&u)[6][NIN], const T* Mi, T w0, T w1, T V, T eta,
-                                             T (&y)[6][NOUT]) const {
-    T G[3][3];
+  __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
+                                       const T (&dM)[2], const T* lc, const T (&eta)[2], T (&accb)[4][3],
+                                       T (&acct)[4][3]) const {
+    const T r = lc[4], vw2 = lc[5];
+    // accb / acct (zero on entry) first hold the per-corner sums SX of X and SH of H[:,2]
+    T(&SX)[4][3] = accb;
+    T(&SH)[4][3] = acct;
+    T s[4][3], dd[4][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T ax = (u[1][c] - u[0][c]) + (u[4][c] - u[3][c]);
-      T ay = (u[2][c] - u[0][c]) + (u[5][c] - u[3][c]);
-      T az = (u[3][c] + u[4][c] + u[5][c]) - (u[0][c] + u[1][c] + u[2][c]);
-      ax *= w0, ay *= w0, az *= w1;
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int x = 0; x < 3; ++x) G[c][x] = ax * Mi[x] + ay * Mi[3 + x] + az * Mi[6 + x];
+      for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const T* M = Mi[w];
+      T G[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = ((dd[c0][c] + dd[c1][c]) + dd[c2][c]) * r;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) G[c][x] = ax * M[x] + ay * M[3 + x] + az * M[6 + x];
+      }
+      const T ve = vw2 * dM[w] * eta[w];
+      const T t = div_term ? (T)(2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]) : (T)0;
+      T S[3][3];
+      S[0][0] = ve * ((G[0][0] + G[0][0]) - t);
+      S[1][1] = ve * ((G[1][1] + G[1][1]) - t);
+      S[2][2] = ve * ((G[2][2] + G[2][2]) - t);
+      S[0][1] = S[1][0] = ve * (G[0][1] + G[1][0]);
+      S[0][2] = S[2][0] = ve * (G[0][2] + G[2][0]);
+      S[1][2] = S[2][1] = ve * (G[1][2] + G[2][1]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T h0 = S[c][0] * M[0] + S[c][1] * M[1] + S[c][2] * M[2];
+        const T h1 = S[c][0] * M[3] + S[c][1] * M[4] + S[c][2] * M[5];
+        const T h2 = r * (S[c][0] * M[6] + S[c][1] * M[7] + S[c][2] * M[8]);
+        SX[c0][c] -= h0 + h1;
+        SX[c1][c] += h0;
+        SX[c2][c] += h1;
+        SH[c0][c] += h2;
+        SH[c1][c] += h2;
+        SH[c2][c] += h2;
+      }
     }
-    T ve = V * eta;
-    T t = div_term ? (T)(2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]) : (T)0;
-    T S[3][3];
-    S[0][0] = ve * ((G[0][0] + G[0][0]) - t);
-    S[1][1] = ve * ((G[1][1] + G[1][1]) - t);
-    S[2][2] = ve * ((G[2][2] + G[2][2]) - t);
-    S[0][1] = S[1][0] = ve * (G[0][1] + G[1][0]);
-    S[0][2] = S[2][0] = ve * (G[0][2] + G[2][0]);
-    S[1][2] = S[2][1] = ve * (G[1][2] + G[2][1]);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T h0 = w0 * (S[c][0] * Mi[0] + S[c][1] * Mi[1] + S[c][2] * Mi[2]);
-      T h1 = w0 * (S[c][0] * Mi[3] + S[c][1] * Mi[4] + S[c][2] * Mi[5]);
-      T h2 = w1 * (S[c][0] * Mi[6] + S[c][1] * Mi[7] + S[c][2] * Mi[8]);
-      T s = h0 + h1;
-      y[0][c] = -s - h2;
-      y[1][c] = h0 - h2;
-      y[2][c] = h1 - h2;
-      y[3][c] = h2 - s;
-      y[4][c] = h0 + h2;
-      y[5][c] = h1 + h2;
-    }
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T x = SX[q][c], h = SH[q][c];
+        accb[q][c] = x - h, acct[q][c] = x + h;
+      }
   }
 };
 
-// Fine-level divergence: each of the six nodes gets -V tr(grad u)(q_c) / 6
-// (pressure test function psi = N_n with N_n(q_c) = 1/6).
+// Fine-level divergence: each of the six nodes of a wedge gets -V tr(grad u)(q_c) / 6
+// (pressure test function psi = N_n with N_n(q_c) = 1/6); tr grad u = w0 tr G'.
 template <typename T>
 struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
-  __device__ __forceinline__ void operator()(const T (&u)[6][NIN], const T* Mi, T w0, T w1, T V, T,
-                                             T (&y)[6][NOUT]) const {
-    T tr = 0;
+  static constexpr bool USES_ETA = false;
+  __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
+                                       const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
+                                       T (&acct)[4][1]) const {
+    const T r = lc[4], vw = lc[6];
+    T s[4][3], dd[4][3];
+    T(&Q)[4][1] = accb;  // zero on entry
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T ax = (u[1][c] - u[0][c]) + (u[4][c] - u[3][c]);
-      T ay = (u[2][c] - u[0][c]) + (u[5][c] - u[3][c]);
-      T az = (u[3][c] + u[4][c] + u[5][c]) - (u[0][c] + u[1][c] + u[2][c]);
-      tr += (ax * w0) * Mi[c] + (ay * w0) * Mi[3 + c] + (az * w1) * Mi[6 + c];
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const T* M = Mi[w];
+      T tr = 0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = ((dd[c0][c] + dd[c1][c]) + dd[c2][c]) * r;
+        tr += ax * M[c] + ay * M[3 + c] + az * M[6 + c];
+      }
+      const T v = -(vw * dM[w]) * tr * (T)(1.0 / 6.0);
+      Q[c0][0] += v, Q[c1][0] += v, Q[c2][0] += v;
     }
-    T v = -V * tr * (T)(1.0 / 6.0);
 #pragma unroll
-    for (int j = 0; j < 6; ++j) y[j][0] = v;
+    for (int q = 0; q < 4; ++q) acct[q][0] = accb[q][0];
   }
 };
 
-// Fine-level gradient (transpose of OpDiv): y_j += -V p(q_c) grad N_j(q_c), p(q_c) = mean of 6.
+// Fine-level gradient (transpose of OpDiv): y_j += -V p(q_c) grad N_j(q_c), p(q_c) the mean of
+// the six nodal values; H[:, m] = f M^-1[m, :] (times r for m = 2), f = -vol w0 |det M| p(q_c).
 template <typename T>
 struct OpGrad {
   static constexpr int NIN = 1, NOUT = 3;
-  __device__ __forceinline__ void operator()(const T (&p)[6][NIN], const T* Mi, T w0, T w1, T V, T,
-                                             T (&y)[6][NOUT]) const {
-    T pc = ((p[0][0] + p[1][0] + p[2][0]) + (p[3][0] + p[4][0] + p[5][0])) * (T)(1.0 / 6.0);
-    T f = -V * pc;
+  static constexpr bool USES_ETA = false;
+  __device__ __forceinline__ void cell(const T (&ub)[4][1], const T (&ut)[4][1], const T (&Mi)[2][9],
+                                       const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][3],
+                                       T (&acct)[4][3]) const {
+    const T r = lc[4], vw = lc[6];
+    T(&SX)[4][3] = accb;  // zero on entry; per-corner sums of X and H[:,2]
+    T(&SH)[4][3] = acct;
+    T s[4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T h0 = f * w0 * Mi[c], h1 = f * w0 * Mi[3 + c], h2 = f * w1 * Mi[6 + c];
-      T s = h0 + h1;
-      y[0][c] = -s - h2;
-      y[1][c] = h0 - h2;
-      y[2][c] = h1 - h2;
-      y[3][c] = h2 - s;
-      y[4][c] = h0 + h2;
-      y[5][c] = h1 + h2;
+    for (int q = 0; q < 4; ++q) s[q] = ub[q][0] + ut[q][0];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const T* M = Mi[w];
+      const T f = -(vw * dM[w]) * (((s[c0] + s[c1]) + s[c2]) * (T)(1.0 / 6.0));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T h0 = f * M[c], h1 = f * M[3 + c], h2 = (f * r) * M[6 + c];
+        SX[c0][c] -= h0 + h1;
+        SX[c1][c] += h0;
+        SX[c2][c] += h1;
+        SH[c0][c] += h2;
+        SH[c1][c] += h2;
+        SH[c2][c] += h2;
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T x = SX[q][c], h = SH[q][c];
+        accb[q][c] = x - h, acct[q][c] = x + h;
+      }
   }
 };
 
@@ -218,8 +283,6 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
       dM[w] = geo[(int64_t)9 * D.n_tri + t0 + w];
     }
   }
-  // wedge-local lateral node -> cell corner: W0 = (00, 10, 01), W1 = (11, 01, 10)
-  constexpr int corner[2][3] = {{0, 1, 2}, {3, 2, 1}};
 
   auto load_level = [&](int k, T (&v)[4][NIN]) {
 #pragma unroll
@@ -313,22 +376,10 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
     if (cell_ok) {
-      const T w0 = lay[4 * k], w1 = lay[4 * k + 1], vol = lay[4 * k + 2];
       const int64_t widx = ((((int64_t)d * (n_r - 1) + k) * N + ci) * N + cj) * 2;
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        T ue[6][NIN], ye[6][NOUT];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int c = 0; c < NIN; ++c) ue[a][c] = ub[corner[w][a]][c], ue[3 + a][c] = ut[corner[w][a]][c];
-        const T e = eta ? eta[widx + w] : (T)1;
-        op(ue, Mi[w], w0, w1, vol * dM[w], e, ye);
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int c = 0; c < NOUT; ++c) accb[corner[w][a]][c] += ye[a][c], acct[corner[w][a]][c] += ye[3 + a][c];
-      }
+      T e[2] = {(T)1, (T)1};
+      if (Op::USES_ETA) e[0] = eta[widx], e[1] = eta[widx + 1];
+      op.cell(ub, ut, Mi, dM, lay + (int64_t)kLayerStride * k, e, accb, acct);
     }
     if (k >= kc0) {
 #pragma unroll
@@ -451,7 +502,7 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
     for (int side = 0; side < 2; ++side) {  // side 0: node is bottom of layer k; 1: top of layer k-1
       const int kk = side == 0 ? k : k - 1;
       if (kk < 0 || kk >= D.n_r - 1) continue;
-      const T w0 = lay[4 * kk], w1 = lay[4 * kk + 1], vol = lay[4 * kk + 2];
+      const T w0 = lay[kLayerStride * kk], w1 = lay[kLayerStride * kk + 1], vol = lay[kLayerStride * kk + 2];
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
@@ -524,7 +575,7 @@ __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict
     for (int side = 0; side < 2; ++side) {
       const int kk = side == 0 ? k : k - 1;
       if (kk < 0 || kk >= D.n_r - 1) continue;
-      const T w0 = lay[4 * kk], w1 = lay[4 * kk + 1], vol = lay[4 * kk + 2];
+      const T w0 = lay[kLayerStride * kk], w1 = lay[kLayerStride * kk + 1], vol = lay[kLayerStride * kk + 2];
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
@@ -747,7 +798,7 @@ __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T
           // weight of this coarse node: bottom node (side 0) -> 3/4 in lower child, 1/4 in upper
           const T wr = (side == 0) == (r == 0) ? (T)0.75 : (T)0.25;
           const T psi = wl * wr;
-          const T V = layF[4 * kf + 2] * dM;
+          const T V = layF[kLayerStride * kf + 2] * dM;
           const T e = etaF[((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw];
           acc += V / e * psi * psi;
         }
@@ -758,7 +809,7 @@ __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T
 }
 
 // ------------------------------------------------------------------------------------ viscosity
-// lay[4 k + 3] holds the layer mid-radius (r_k + r_k+1) / 2.
+// lay[kLayerStride k + 3] holds the layer mid-radius (r_k + r_k+1) / 2.
 __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, double jump_r, double jump_f,
                              const double* __restrict__ lay, double* eta) {
   const int N = D.N;
@@ -776,7 +827,7 @@ __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, dou
   for (int a = 0; a < 3; ++a) s += T[b + D.layer_stride + (int64_t)pi_[a] * D.P + pj_[a]];
   const double Te = s / 6.0;
   double e = exp(E * (0.5 - Te));
-  if (jump_r > 0 && lay[4 * k + 3] < jump_r) e = jump_f * e;
+  if (jump_r > 0 && lay[kLayerStride * k + 3] < jump_r) e = jump_f * e;
   eta[tid] = e;
 }
 
@@ -836,7 +887,7 @@ __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double*
       double s = 0;
       for (int a = 0; a < 3; ++a) s += T[b + (int64_t)pi_[a] * D.P + pj_[a]];
       for (int a = 0; a < 3; ++a) s += T[b + D.layer_stride + (int64_t)pi_[a] * D.P + pj_[a]];
-      const double V = lay[4 * kk + 2] * dM;
+      const double V = lay[kLayerStride * kk + 2] * dM;
       const double wgt = V * Ra * (s / 6.0) / 6.0 / nrm;
       for (int c = 0; c < 3; ++c) f[c] += wgt * sb[c];
     }

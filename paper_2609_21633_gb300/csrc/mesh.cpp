@@ -136,15 +136,20 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
           if (!(det > 0.0)) err = "degenerate or inverted lateral triangle";
         }
 
-  // ---- per radial cell: (1/(2 rho), 1/(6 h), rho^2 h, rho)
-  lay.assign((size_t)4 * (n_r - 1), 0.0);
+  // ---- per radial cell: (w0, w1, vol, rho, w1 / w0, vol w0^2, vol w0, 0) with w0 = 1/(2 rho),
+  // w1 = 1/(6 h), vol = rho^2 h
+  lay.assign((size_t)kLayerStride * (n_r - 1), 0.0);
   for (int k = 0; k + 1 < n_r; ++k) {
     double rho = 0.5 * (L.radii[k] + L.radii[k + 1]);
     double h = 0.5 * (L.radii[k + 1] - L.radii[k]);
-    lay[4 * k + 0] = 1.0 / (2.0 * rho);
-    lay[4 * k + 1] = 1.0 / (6.0 * h);
-    lay[4 * k + 2] = rho * rho * h;
-    lay[4 * k + 3] = rho;
+    double* t = &lay[(size_t)kLayerStride * k];
+    t[0] = 1.0 / (2.0 * rho);
+    t[1] = 1.0 / (6.0 * h);
+    t[2] = rho * rho * h;
+    t[3] = rho;
+    t[4] = t[1] / t[0];
+    t[5] = t[2] * t[0] * t[0];
+    t[6] = t[2] * t[0];
   }
 
   // ---- lateral unit vectors in the padded lateral layout
