@@ -98,7 +98,7 @@ __device__ constexpr int kCorner[2][3] = {{0, 1, 2}, {3, 2, 1}};
 template <typename T>
 struct OpA {
   static constexpr int NIN = 3, NOUT = 3;
-  static constexpr bool USES_ETA = true;
+  static constexpr bool USES_ETA = true, LOADS = true;
   int div_term;
   __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&eta)[2], T (&accb)[4][3],
@@ -160,7 +160,7 @@ struct OpA {
 template <typename T>
 struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
-  static constexpr bool USES_ETA = false;
+  static constexpr bool USES_ETA = false, LOADS = true;
   __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
                                        T (&acct)[4][1]) const {
@@ -194,7 +194,7 @@ struct OpDiv {
 template <typename T>
 struct OpGrad {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = false;
+  static constexpr bool USES_ETA = false, LOADS = true;
   __device__ __forceinline__ void cell(const T (&ub)[4][1], const T (&ut)[4][1], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][3],
                                        T (&acct)[4][3]) const {
@@ -227,6 +227,50 @@ struct OpGrad {
         const T x = SX[q][c], h = SH[q][c];
         accb[q][c] = x - h, acct[q][c] = x + h;
       }
+  }
+};
+
+// Diagonal of A (no input): node j of a wedge receives V eta (|g_j|^2 + c g_j[d]^2) for each
+// component d, g_j = grad N_j(q_c) = w0 (xi_a M^-1[0,:] + eta_a M^-1[1,:]) -/+ w1 M^-1[2,:]
+// (bottom / top), c = 1/3 with the -2/3 div term, 1 without (A_jj = V eta (|g|^2 I + c g g^T)).
+template <typename T>
+struct OpDiag {
+  static constexpr int NIN = 1, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = false;
+  int div_term;
+  __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&Mi)[2][9], const T (&dM)[2],
+                                       const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3]) const {
+    const T w0 = lc[0], w1 = lc[1], vol = lc[2];
+    const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const T* M = Mi[w];
+      const T ve = vol * dM[w] * eta[w];
+      T lat[3][3], u2[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const T u0 = w0 * M[x], u1 = w0 * M[3 + x];
+        u2[x] = w1 * M[6 + x];
+        lat[0][x] = -(u0 + u1), lat[1][x] = u0, lat[2][x] = u1;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = kCorner[w][a];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          T g[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) g[x] = side == 0 ? lat[a][x] - u2[x] : lat[a][x] + u2[x];
+          const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T v = ve * (g2 + third * (g[c] * g[c]));
+            if (side == 0) accb[q][c] += v;
+            else acct[q][c] += v;
+          }
+        }
+      }
+    }
   }
 };
 
@@ -285,6 +329,13 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   }
 
   auto load_level = [&](int k, T (&v)[4][NIN]) {
+    if (!Op::LOADS) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) v[q][c] = (T)0;
+      return;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -477,15 +528,18 @@ __global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, 
 // Thread per layout node; gathers the 3x3 node block of A from the (up to) 12 wedges
 // around the node: A_jj = sum_e V eta (|g|^2 I + 1/3 g g^T) (the -2/3 div term gives
 // -2/3 g g^T, the symmetric-gradient term g g^T, so 1/3 with div_term, 1 without).
+// Only the two boundary node layers are handled here (the tile kernel with OpDiag writes the
+// interior layers): blocks = 10 * 2 * (N+1)^2 threads, layer 0 and layer n_r - 1.
 template <typename T>
 __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, const T* __restrict__ eta,
                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* d0, T* d1, T* d2) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)10 * D.n_r * M * M;
+  const int64_t total = (int64_t)10 * 2 * M * M;
   if (tid >= total) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
-            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int j = (int)(tid % M), i = (int)((tid / M) % M), side_ = (int)((tid / ((int64_t)M * M)) % 2),
+            d = (int)(tid / ((int64_t)M * M * 2));
+  const int k = side_ == 0 ? 0 : D.n_r - 1;
   // (cell di, cell dj, wedge, local lateral node) of the six triangles around lattice node (i, j)
   const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
   const T gxi[3] = {-1, 1, 0}, geta[3] = {-1, 0, 1};
@@ -933,10 +987,15 @@ cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cud
 template <typename T>
 cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cudaStream_t st) {
   Dims D = dims(L);
-  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
+  // interior layers: per-cell tile kernel (boundary layers are overwritten below)
+  OpDiag<T> op{div_term};
+  const T* none[1] = {d[0]};
+  cudaError_t e = launch_tile<T, OpDiag<T>, 0>(L, bc, op, none, d, Tab<T>::eta(L), st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
   k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), Tab<T>::eta(L), Tab<T>::s(L), bc.in,
                                             bc.out, div_term, d[0], d[1], d[2]);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 2, d, nullptr, st);
 }
