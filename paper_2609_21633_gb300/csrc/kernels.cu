@@ -25,6 +25,7 @@
 // partial sum per diamond; launch_interface adds the copies in ascending
 // layout order and writes the total to every copy (the on-device stand-in
 // for the paper's additive halo exchange, Sec. 2).
+#include <cstdint>
 #include <cstdio>
 
 #include "internal.h"
@@ -295,10 +296,13 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
            T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
            const T* __restrict__ lay, const T* __restrict__ eta, const T* __restrict__ svec, int bc_in, int bc_out,
            int kc, const int* __restrict__ skip) {
+  // All offsets are 32-bit: launch_tile only accepts levels whose node and wedge arrays have
+  // fewer than 2^31 entries.
   constexpr int NIN = Op::NIN, NOUT = Op::NOUT, W = TT + 1;
   __shared__ T sm[4][NOUT][W][W];
   if (skip && *skip) return;  // device-side early exit (uniform over the grid)
   const int N = D.N, n_r = D.n_r, P = D.P;
+  const int LS = (int)D.layer_stride, NLL = (int)D.n_lat_layout;
   const int ntj = N / TT;
   const int i0 = (blockIdx.x / ntj) * TT, j0 = (blockIdx.x % ntj) * TT;
   const int d = blockIdx.z;
@@ -306,100 +310,118 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   const int ti = threadIdx.x / W, tj = threadIdx.x % W;
   const int ci = i0 - 1 + ti, cj = j0 - 1 + tj;  // this thread's cell
   const bool cell_ok = ci >= 0 && cj >= 0;       // ci, cj <= N - 1 always
-  const T* in[3] = {in0, in1, in2};
-  T* out[3] = {out0, out1, out2};
-
-  // lateral corner offsets of this cell: 00, 10, 01, 11
   const int ci0 = max(ci, 0), cj0 = max(cj, 0);
-  const int64_t base = (int64_t)d * D.diamond_stride;
-  const int64_t cofs[4] = {(int64_t)ci0 * P + cj0, (int64_t)(ci0 + 1) * P + cj0, (int64_t)ci0 * P + cj0 + 1,
-                           (int64_t)(ci0 + 1) * P + cj0 + 1};
-  const int64_t lat_base = (int64_t)d * (N + 1) * P;
-
+  // node offset of corner 00 of this cell on layer 0; corners 10, 01, 11 are +P, +1, +P+1
+  const int c00 = (int)(d * D.diamond_stride) + ci0 * P + cj0;
+  const int cdel[4] = {0, P, 1, P + 1};
+  const int lat00 = d * (N + 1) * P + ci0 * P + cj0;  // lateral-layout offset of corner 00
   // per-cell lateral geometry (both triangles), kept in registers for the whole column
   T Mi[2][9], dM[2];
   {
-    const int64_t t0 = (((int64_t)d * N + ci0) * N + cj0) * 2;
+    const int t0 = ((d * N + ci0) * N + cj0) * 2, nt = (int)D.n_tri;
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Mi[w][q] = geo[(int64_t)q * D.n_tri + t0 + w];
-      dM[w] = geo[(int64_t)9 * D.n_tri + t0 + w];
+      for (int q = 0; q < 9; ++q) Mi[w][q] = geo[q * nt + t0 + w];
+      dM[w] = geo[9 * nt + t0 + w];
     }
   }
+  const T* eta_col = eta ? eta + (((d * (n_r - 1)) * N + ci0) * N + cj0) * 2 : nullptr;  // layer k: + k N^2 2
+  const int eta_ls = N * N * 2;
+  // the node this thread owns: (ci, cj) when ti, tj >= 1; the last tile row / column also owns
+  // node N (handled in the rare path below)
+  const bool own = ti >= 1 && tj >= 1;
+  const bool own_shared = ci == 0 || ci == N || cj == 0 || cj == N;
+  const bool last_i = (i0 + TT == N) && ti == TT, last_j = (j0 + TT == N) && tj == TT;
+  // when own, ci = ci0 and cj = cj0: the owned node is corner 00 (offsets c00 and lat00)
 
   auto load_level = [&](int k, T (&v)[4][NIN]) {
-    if (!Op::LOADS) {
+    if (!Op::LOADS || !cell_ok) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int c = 0; c < NIN; ++c) v[q][c] = (T)0;
-      return;
+      if (!Op::LOADS) return;
+    } else {
+      const int o = c00 + k * LS;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v[q][0] = in0[o + cdel[q]];
+        if (NIN > 1) v[q][NIN > 1 ? 1 : 0] = in1[o + cdel[q]];
+        if (NIN > 2) v[q][NIN > 2 ? 2 : 0] = in2[o + cdel[q]];
+      }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < NIN; ++c) v[q][c] = cell_ok ? in[c][base + (int64_t)k * D.layer_stride + cofs[q]] : (T)0;
     if ((FLAGS & PROJ_IN) && cell_ok && (k == 0 || k == n_r - 1)) {
       const int bc = k == 0 ? bc_in : bc_out;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         T vv[3] = {v[q][0], v[q][NIN > 1 ? 1 : 0], v[q][NIN > 2 ? 2 : 0]};
-        project_vec(vv, svec, lat_base + cofs[q], D.n_lat_layout, bc);
+        project_vec(vv, svec, (int64_t)(lat00 + cdel[q]), (int64_t)NLL, bc);
 #pragma unroll
         for (int c = 0; c < NIN; ++c) v[q][c] = vv[c];
       }
     }
   };
 
-  // exchange the node-level sums of the four corners and write owned nodes of level k
+  // boundary epilogue and store of node value v at layout offset idx (lateral offset so)
+  auto store_node = [&](int k, int idx, int so, bool shared, T (&v)[3]) {
+    if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
+      const int bc = k == 0 ? bc_in : bc_out;
+      project_vec(v, svec, (int64_t)so, (int64_t)NLL, bc);
+      if ((FLAGS & ADD_ID) && !shared) {
+        T uu[3] = {in0[idx], in1[idx], in2[idx]};
+        T pu[3] = {uu[0], uu[1], uu[2]};
+        project_vec(pu, svec, (int64_t)so, (int64_t)NLL, bc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] += uu[c] - pu[c];
+      }
+    }
+    out0[idx] = v[0];
+    if (NOUT > 1) out1[idx] = v[NOUT > 1 ? 1 : 0];
+    if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
+  };
+
+  // exchange the node-level sums of the four corners and write the owned nodes of layer k
   auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) sm[q][c][ti][tj] = acc[q][c];
     __syncthreads();
-    // nodes owned by this thread: (ci, cj) if ti, tj >= 1; plus the extra last row / column
-    const bool last_i = (i0 + TT == N) && ti == TT, last_j = (j0 + TT == N) && tj == TT;
+    if (own) {
+      // node (ci, cj): cell (ci, cj) corner 00 + (ci-1, cj) corner 10 + (ci, cj-1) corner 01 +
+      // (ci-1, cj-1) corner 11, in that order
+      T v[3] = {0, 0, 0};
 #pragma unroll
-    for (int oi = 0; oi < 2; ++oi)
+      for (int c = 0; c < NOUT; ++c)
+        v[c] = ((sm[0][c][ti][tj] + sm[1][c][ti - 1][tj]) + sm[2][c][ti][tj - 1]) + sm[3][c][ti - 1][tj - 1];
+      store_node(k, c00 + k * LS, lat00, own_shared, v);
+    }
+    if (last_i || last_j) {  // rare: nodes in row / column N of the diamond
 #pragma unroll
-      for (int oj = 0; oj < 2; ++oj) {
-        if (oi == 1 && !last_i) continue;
-        if (oj == 1 && !last_j) continue;
-        const int xi = ti + oi, xj = tj + oj;  // node position in tile-thread coordinates
-        if (xi < 1 || xj < 1) continue;
-        const int ni = ci + oi, nj = cj + oj;
-        T v[3] = {0, 0, 0};
+      for (int oi = 0; oi < 2; ++oi)
 #pragma unroll
-        for (int c = 0; c < NOUT; ++c) {
-          T a = (xi <= TT && xj <= TT) ? sm[0][c][xi][xj] : (T)0;  // cell (ni, nj), corner 00
-          T b = (xj <= TT) ? sm[1][c][xi - 1][xj] : (T)0;          // cell (ni-1, nj), corner 10
-          T e = (xi <= TT) ? sm[2][c][xi][xj - 1] : (T)0;          // cell (ni, nj-1), corner 01
-          T f = sm[3][c][xi - 1][xj - 1];                          // cell (ni-1, nj-1), corner 11
-          v[c] = ((a + b) + e) + f;
-        }
-        const int64_t idx = base + (int64_t)k * D.layer_stride + (int64_t)ni * P + nj;
-        const bool shared = ni == 0 || ni == N || nj == 0 || nj == N;
-        if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
-          const int bc = k == 0 ? bc_in : bc_out;
-          const int64_t so = lat_base + (int64_t)ni * P + nj;
-          T raw[3] = {v[0], v[1], v[2]};
-          project_vec(raw, svec, so, D.n_lat_layout, bc);
-          if ((FLAGS & ADD_ID) && !shared) {
-            T uu[3], pu[3];
+        for (int oj = 0; oj < 2; ++oj) {
+          if (oi == 0 && oj == 0) continue;
+          if (oi == 1 && !last_i) continue;
+          if (oj == 1 && !last_j) continue;
+          const int xi = ti + oi, xj = tj + oj;
+          if (xi < 1 || xj < 1) continue;
+          const int ni = ci + oi, nj = cj + oj;
+          T v[3] = {0, 0, 0};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) uu[c] = pu[c] = in[c][idx];
-            project_vec(pu, svec, so, D.n_lat_layout, bc);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) raw[c] += uu[c] - pu[c];
+          for (int c = 0; c < NOUT; ++c) {
+            T a = (xi <= TT && xj <= TT) ? sm[0][c][xi][xj] : (T)0;
+            T b = (xj <= TT) ? sm[1][c][xi - 1][xj] : (T)0;
+            T e = (xi <= TT) ? sm[2][c][xi][xj - 1] : (T)0;
+            T f = sm[3][c][xi - 1][xj - 1];
+            v[c] = ((a + b) + e) + f;
           }
-#pragma unroll
-          for (int c = 0; c < NOUT; ++c) v[c] = raw[c];
+          const bool shared = ni == 0 || ni == N || nj == 0 || nj == N;
+          store_node(k, (int)(d * D.diamond_stride) + k * LS + ni * P + nj, d * (N + 1) * P + ni * P + nj, shared,
+                     v);
         }
-#pragma unroll
-        for (int c = 0; c < NOUT; ++c) out[c][idx] = v[c];
-      }
+    }
     __syncthreads();
   };
 
@@ -412,25 +434,17 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
 
   const int kstart = kc0 > 0 ? kc0 - 1 : 0;
   load_level(kstart, ub);
-  if (TN_PREFETCH) load_level(kstart + 1, ut);
   for (int k = kstart; k < kc1; ++k) {
-    // prefetch the next node layer while this cell layer is computed
-    T un[4][NIN];
-    if (TN_PREFETCH) {
-      if (k + 2 <= kc1) load_level(k + 2, un);
-    } else {
-      load_level(k + 1, ut);
-    }
+    load_level(k + 1, ut);
     T accb[4][NOUT], acct[4][NOUT];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
     if (cell_ok) {
-      const int64_t widx = ((((int64_t)d * (n_r - 1) + k) * N + ci) * N + cj) * 2;
       T e[2] = {(T)1, (T)1};
-      if (Op::USES_ETA) e[0] = eta[widx], e[1] = eta[widx + 1];
-      op.cell(ub, ut, Mi, dM, lay + (int64_t)kLayerStride * k, e, accb, acct);
+      if (Op::USES_ETA) e[0] = eta_col[k * eta_ls], e[1] = eta_col[k * eta_ls + 1];
+      op.cell(ub, ut, Mi, dM, lay + kLayerStride * k, e, accb, acct);
     }
     if (k >= kc0) {
 #pragma unroll
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) carry[q][c] = acct[q][c];
 #pragma unroll
-      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c], ut[q][c] = TN_PREFETCH ? un[q][c] : ut[q][c];
+      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c];
     }
   }
   if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
@@ -454,6 +468,8 @@ template <typename T, typename Op, int FLAGS>
 cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const T* eta,
                         cudaStream_t st, const int* skip = nullptr) {
   Dims D = dims(L);
+  if (L.n_layout >= (int64_t)INT32_MAX || L.n_wedges >= (int64_t)INT32_MAX || 10 * L.n_tri >= (int64_t)INT32_MAX)
+    return cudaErrorInvalidValue;  // the tile kernel uses 32-bit offsets
   const int tt = L.N >= TILE ? TILE : L.N;
   const int ntiles = (L.N / tt) * (L.N / tt);
   const int ncells = L.n_r - 1;
