@@ -202,9 +202,10 @@ def layout_temperature(tn, m, noise_seed=None, noise_scale=0.01):
     return T
 
 
-def solve_case(tn, torch, dev, level, n_r, E, Ra, mode):
-    """One Stokes solve to 1e-8 (multigrid set-up excluded from the time)."""
-    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT)
+def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0):
+    """One Stokes solve to 1e-8 (multigrid set-up excluded from the time).  Returns the stats and
+    the solution (u, p) on the unique nodes, as host FP64 arrays."""
+    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, eta_storage=eta_storage)
     try:
         info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
         Td = torch.tensor(layout_temperature(tn, m), device=dev)
@@ -220,8 +221,11 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode):
         st = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(mode=mode), check=False)
         nv = 3 * info["n_unique_nodes"]
         npr = pinfo["n_unique_nodes"]
+        cu, cp = tn.tn_mesh_canonical_index(m, 0), tn.tn_mesh_canonical_index(m, 1)
+        ku, kp = cu == np.arange(cu.size), cp == np.arange(cp.size)
+        sol = (np.stack([t.cpu().numpy()[ku] for t in u]), p.cpu().numpy()[kp])
         return {"iterations": st["iterations"], "refinements": st["refinements"], "seconds": st["seconds"],
-                "rel_residual": st["rel_residual"], "converged": bool(st["converged"]), "dofs": nv + npr}
+                "rel_residual": st["rel_residual"], "converged": bool(st["converged"]), "dofs": nv + npr}, sol
     finally:
         tn.tn_mesh_destroy(m)
 
@@ -426,11 +430,18 @@ def main():
             solves = {}
             for name, lvl, nr, E in (("l4_17_contrast1e1", 4, 17, math.log(10.0)),
                                      ("l6_65_contrast1e4", 6, 65, math.log(1e4))):
-                r64 = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64)
-                rmx = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED)
-                solves[name] = {"fp64": r64, "mixed": rmx, "mixed_speedup": r64["seconds"] / rmx["seconds"]}
+                r64, s64 = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64)
+                rmx, smx = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED)
+                rbf, sbf = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED, eta_storage=tn.TN_ETA_BF16)
+                for r, sx in ((rmx, smx), (rbf, sbf)):  # solution difference against the FP64 solve
+                    r["u_rel_diff_vs_fp64"] = float(np.linalg.norm(sx[0] - s64[0]) / np.linalg.norm(s64[0]))
+                    r["p_rel_diff_vs_fp64"] = float(np.linalg.norm(sx[1] - s64[1]) / np.linalg.norm(s64[1]))
+                solves[name] = {"fp64": r64, "mixed": rmx, "mixed_bf16_eta": rbf,
+                                "mixed_speedup": r64["seconds"] / rmx["seconds"],
+                                "mixed_bf16_eta_speedup": r64["seconds"] / rbf["seconds"]}
             line["solves"] = solves
-            line["serving"] = serving_stream(tn, args.serve_requests, args.seed)
+            if args.serve_requests > 0:
+                line["serving"] = serving_stream(tn, args.serve_requests, args.seed)
         if world == 1:
             dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
             line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

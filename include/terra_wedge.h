@@ -83,6 +83,11 @@ enum {
 
 typedef enum { TN_F64 = 0, TN_F32 = 1 } tn_prec;
 typedef enum { TN_BC_FREESLIP = 0, TN_BC_NOSLIP = 1 } tn_bc;
+/* Storage of the per-wedge viscosity that the FP32 kernels read (the FP64 kernels always read
+ * FP64).  TN_ETA_BF16 / TN_ETA_F16 keep 16-bit values eta / c plus one FP32 factor c per radial
+ * column of wedges (lateral wedge (d, i, j, w) over all radial cells), c = sqrt(min * max) of the
+ * column, so the stored values straddle 1; used on levels with N >= 16, FP32 on coarser ones. */
+typedef enum { TN_ETA_F32 = 0, TN_ETA_BF16 = 1, TN_ETA_F16 = 2 } tn_eta_storage;
 
 typedef struct tn_mesh tn_mesh;
 
@@ -91,6 +96,7 @@ typedef struct {
   int bc_outer;       /* tn_bc at r_out (default TN_BC_FREESLIP) */
   int div_term;       /* 1: keep the -2/3 div div term of Eq. elemmat (default); 0: drop it */
   int max_levels;     /* upper bound on the hierarchy depth (0 = as deep as possible) */
+  int eta_storage;    /* tn_eta_storage of the FP32 path's viscosity (default TN_ETA_F32) */
 } tn_mesh_opts;
 
 typedef struct {

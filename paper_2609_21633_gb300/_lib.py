@@ -16,6 +16,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "terra_wedge.h")
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOTCONVERGED, TN_ETIMEOUT, TN_EBUSY, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 TN_F64, TN_F32 = 0, 1
 TN_BC_FREESLIP, TN_BC_NOSLIP = 0, 1
+TN_ETA_F32, TN_ETA_BF16, TN_ETA_F16 = 0, 1, 2
 
 
 class TnError(RuntimeError):
@@ -26,7 +27,7 @@ class TnError(RuntimeError):
 
 class tn_mesh_opts(ctypes.Structure):
     _fields_ = [("bc_inner", ctypes.c_int), ("bc_outer", ctypes.c_int), ("div_term", ctypes.c_int),
-                ("max_levels", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int)]
 
 
 class tn_level_info(ctypes.Structure):
@@ -165,8 +166,8 @@ def _prec(dtype):
 
 
 def tn_mesh_create(lateral_level, radial_layers, r_in, r_out, bc_inner=TN_BC_FREESLIP, bc_outer=TN_BC_FREESLIP,
-                   div_term=True, max_levels=0):
-    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels)
+                   div_term=True, max_levels=0, eta_storage=0):
+    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage)
     out = P()
     _check(lib().tn_mesh_create(lateral_level, radial_layers, r_in, r_out, ctypes.byref(opts), ctypes.byref(out)))
     return out

@@ -42,7 +42,8 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
-                  L.grp_s32, L.owned, L.eta64, L.eta32, L.scr64, L.scr32, L.wmask, L.rad64, L.rad32};
+                  L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
+                  L.rad32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -82,7 +83,7 @@ cudaError_t apply_BT_t(tn_mesh* m, int level, const void* p, void* const* y, cud
 }  // namespace
 
 // Host tables and device arrays of one level (lateral level l, nr node layers).
-tn_status create_level(Level& L, int l, int nr, double r_in, double r_out) {
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage) {
   std::vector<double> geo, lay, s, grp_s;
   std::vector<int> gptr;
   std::vector<int64_t> goff;
@@ -108,7 +109,14 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out) {
   chk(upload(L.grp_s32, to_f32(grp_s)));
   chk(upload(L.owned, owned));
   chk(cudaMalloc((void**)&L.eta64, sizeof(double) * L.n_wedges));
-  chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
+  // 16-bit viscosity only where the tile kernel runs with full 16 x 16 tiles
+  L.eta_kind = (eta_storage != TN_ETA_F32 && L.N >= 16) ? eta_storage : TN_ETA_F32;
+  if (L.eta_kind == TN_ETA_F32) {
+    chk(cudaMalloc((void**)&L.eta32, sizeof(float) * L.n_wedges));
+  } else {
+    chk(cudaMalloc((void**)&L.eta16, sizeof(uint16_t) * L.n_wedges));
+    chk(cudaMalloc((void**)&L.eta_cs, sizeof(float) * L.n_tri));
+  }
   chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
   chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));
   {
@@ -161,8 +169,10 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   if (radial_layers < 3 || (radial_layers - 1) % 2 != 0)
     return inval("tn_mesh_create: radial_layers must be >= 3 with radial_layers - 1 even");
   if (!(r_in > 0.0) || !(r_out > r_in)) return inval("tn_mesh_create: need 0 < r_in < r_out");
-  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0};
+  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, TN_ETA_F32};
   if (opts) o = *opts;
+  if (o.eta_storage != TN_ETA_F32 && o.eta_storage != TN_ETA_BF16 && o.eta_storage != TN_ETA_F16)
+    return inval("tn_mesh_create: unknown viscosity storage");
   if ((o.bc_inner != TN_BC_FREESLIP && o.bc_inner != TN_BC_NOSLIP) ||
       (o.bc_outer != TN_BC_FREESLIP && o.bc_outer != TN_BC_NOSLIP))
     return inval("tn_mesh_create: unknown boundary condition");
@@ -174,13 +184,14 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   m->bc_in = o.bc_inner;
   m->bc_out = o.bc_outer;
   m->div_term = o.div_term ? 1 : 0;
+  m->eta_storage = o.eta_storage;
   m->r_in = r_in;
   m->r_out = r_out;
   cudaGetDevice(&m->device);
   int l = lateral_level, nr = radial_layers;
   while (true) {
     m->lv.emplace_back();
-    tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out);
+    tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage);
     if (s != TN_OK) {
       std::string msg = tn_last_error();
       tn_mesh_destroy(m);
@@ -256,7 +267,7 @@ static tn_status finish_eta(tn_mesh* m, cudaStream_t st) {
       cudaError_t e = launch_eta_coarsen(m->lv[h - 1], m->lv[h], m->lv[h - 1].eta64, m->lv[h].eta64, st);
       if (e != cudaSuccess) return cuda_fail(e, "viscosity coarsening");
     }
-    cudaError_t e = launch_to_f32(m->lv[h].eta64, m->lv[h].eta32, m->lv[h].n_wedges, st);
+    cudaError_t e = launch_eta_f32_path(m->lv[h], st);
     if (e != cudaSuccess) return cuda_fail(e, "viscosity conversion");
   }
   m->eta_set = true;

@@ -42,9 +42,14 @@ struct Level {
   uint8_t* owned = nullptr;     // [10 (N+1) P] 1 if this copy is the canonical one (or not shared)
   std::vector<int> h_grp_ptr;
   std::vector<int64_t> h_grp_off;
-  // Viscosity per wedge (wedge layout).
+  // Viscosity per wedge (wedge layout).  The FP32 kernels read eta32 (eta_kind 0) or the 16-bit
+  // eta16 (eta_kind = TN_ETA_BF16 / TN_ETA_F16) times eta_cs[t], one factor per lateral wedge
+  // t = ((d N + i) N + j) 2 + w (its radial column).
   double* eta64 = nullptr;
   float* eta32 = nullptr;
+  int eta_kind = TN_ETA_F32;
+  uint16_t* eta16 = nullptr;
+  float* eta_cs = nullptr;
   // Scratch scalar field in this level's node layout (B / B^T intermediate).
   double* scr64 = nullptr;
   float* scr32 = nullptr;
@@ -77,6 +82,7 @@ struct tn_mesh {
   tn::MGState* mg = nullptr;
   int bc_in = TN_BC_FREESLIP, bc_out = TN_BC_FREESLIP, div_term = 1;
   bool eta_set = false;
+  int eta_storage = TN_ETA_F32;
   int device = 0;
   double r_in = 0, r_out = 0;
 };
@@ -92,7 +98,7 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
 
 void set_error(const std::string& msg);
 // Tables and device arrays of one level (api.cu); destroy_level frees them.
-tn_status create_level(Level& L, int l, int nr, double r_in, double r_out);
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage);
 void destroy_level(Level& L);
 void mg_invalidate(tn_mesh* mesh);
 
@@ -103,6 +109,28 @@ struct BC {
 template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                            const int* skip = nullptr);
+
+// Vector updates fused into the epilogue of the A apply (y = K x, never stored except as a
+// partial sum at diamond-edge nodes):
+//   EPI_RESID: r = b - y
+//   EPI_CHEB1: r = b - y, d_out = c0 D^-1 r, x_out = x + d_out           (x = the apply input)
+//   EPI_CHEB2: r = r - y, d_out = c1 d + c2 D^-1 r, x_out = x_acc + d_out  (d = the apply input)
+// D^-1 = inverse 3x3 node blocks (xx, yy, zz, xy, xz, yz).  Outputs must not alias the inputs
+// the apply reads (x or d); r and x_acc / x_out may be updated in place.
+enum { EPI_NONE = 0, EPI_RESID = 1, EPI_CHEB1 = 2, EPI_CHEB2 = 3 };
+template <typename T>
+struct EpiArgs {
+  const T* b[3];
+  T* r[3];
+  const T* binv[6];
+  const T* xacc[3];  // CHEB2: x before the update
+  T* dout[3];
+  T* xout[3];
+  double c0, c1, c2;
+};
+template <typename T>
+cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
+                               T* const* t, cudaStream_t st, const int* skip = nullptr);
 template <typename T>
 cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st);
 template <typename T>
@@ -129,6 +157,8 @@ cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double 
                               cudaStream_t st);
 cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st);
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+// The FP32 path's viscosity from eta64: eta32, or eta16 and the column factors (see Level).
+cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st);
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);
 
 }  // namespace tn

@@ -28,6 +28,9 @@
 #include <cstdint>
 #include <cstdio>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace tn {
@@ -68,7 +71,6 @@ struct Tab<double> {
   static const double* lay(const Level& L) { return L.lay64; }
   static const double* s(const Level& L) { return L.s64; }
   static const double* gs(const Level& L) { return L.grp_s64; }
-  static const double* eta(const Level& L) { return L.eta64; }
 };
 template <>
 struct Tab<float> {
@@ -76,8 +78,39 @@ struct Tab<float> {
   static const float* lay(const Level& L) { return L.lay32; }
   static const float* s(const Level& L) { return L.s32; }
   static const float* gs(const Level& L) { return L.grp_s32; }
-  static const float* eta(const Level& L) { return L.eta32; }
 };
+
+// Per-wedge viscosity as a kernel reads it: v[w] (kind TN_ETA_F32, and always for FP64), or
+// the 16-bit q[w] times the column factor cs[t] of lateral wedge t (kinds TN_ETA_BF16 / F16).
+template <typename T>
+struct EtaView {
+  const T* v;
+  const uint16_t* q;
+  const float* cs;
+  int kind;
+};
+inline EtaView<double> eta_view(const Level& L, double*) { return EtaView<double>{L.eta64, nullptr, nullptr, 0}; }
+inline EtaView<float> eta_view(const Level& L, float*) {
+  return EtaView<float>{L.eta32, L.eta16, L.eta_cs, L.eta_kind};
+}
+template <typename T>
+EtaView<T> etav(const Level& L) {
+  return eta_view(L, (T*)nullptr);
+}
+
+template <int KIND>
+__device__ __forceinline__ float from16(uint16_t b) {
+  if (KIND == TN_ETA_BF16) return __bfloat162float(__ushort_as_bfloat16(b));
+  return __half2float(__ushort_as_half(b));
+}
+
+// Viscosity of wedge index w in lateral column t (kind chosen at run time).
+template <typename T>
+__device__ __forceinline__ T eta_at(const EtaView<T>& E, int64_t w, int64_t t) {
+  if (E.kind == TN_ETA_F32) return E.v[w];
+  const float f = E.kind == TN_ETA_BF16 ? from16<TN_ETA_BF16>(E.q[w]) : from16<TN_ETA_F16>(E.q[w]);
+  return (T)(f * E.cs[t]);
+}
 
 
 // ------------------------------------------------------------------------------------ element ops
@@ -290,12 +323,52 @@ __device__ __forceinline__ void project_vec(T (&v)[3], const T* s, int64_t soff,
   v[0] -= dot * sx, v[1] -= dot * sy, v[2] -= dot * sz;
 }
 
-template <typename T, typename Op, int TT, int FLAGS>
+// Fused vector update at node idx from y = (K x)(idx) (see EpiArgs); `in` is the apply input.
+template <typename T, int EPI>
+__device__ __forceinline__ void epilogue(const EpiArgs<T>& E, const T* in0, const T* in1, const T* in2, int idx,
+                                         const T (&y)[3]) {
+  if (EPI == EPI_RESID) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) E.r[c][idx] = E.b[c][idx] - y[c];
+    return;
+  }
+  T rr[3];
+  if (EPI == EPI_CHEB1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rr[c] = E.b[c][idx] - y[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rr[c] = E.r[c][idx] - y[c];
+  }
+  const T a = E.binv[0][idx], e = E.binv[1][idx], f = E.binv[2][idx], xy = E.binv[3][idx], xz = E.binv[4][idx],
+          yz = E.binv[5][idx];
+  const T z[3] = {a * rr[0] + xy * rr[1] + xz * rr[2], xy * rr[0] + e * rr[1] + yz * rr[2],
+                  xz * rr[0] + yz * rr[1] + f * rr[2]};
+  const T* in[3] = {in0, in1, in2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T dd, xn;
+    if (EPI == EPI_CHEB1) {
+      dd = (T)E.c0 * z[c];
+      xn = in[c][idx] + dd;
+    } else {
+      dd = (T)E.c1 * in[c][idx] + (T)E.c2 * z[c];
+      xn = E.xacc[c][idx] + dd;
+    }
+    E.r[c][idx] = rr[c];
+    E.dout[c][idx] = dd;
+    E.xout[c][idx] = xn;
+  }
+}
+
+// EK: viscosity storage (TN_ETA_F32: eta.v; TN_ETA_BF16 / TN_ETA_F16: eta.q times eta.cs, the
+// column factor folded into |det M| once per column).
+template <typename T, typename Op, int TT, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
 __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
     k_tile(Dims D, Op op, const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
            T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
-           const T* __restrict__ lay, const T* __restrict__ eta, const T* __restrict__ svec, int bc_in, int bc_out,
-           int kc, const int* __restrict__ skip) {
+           const T* __restrict__ lay, EtaView<T> eta, const T* __restrict__ svec, int bc_in, int bc_out,
+           int kc, const int* __restrict__ skip, EpiArgs<T> E) {
   // All offsets are 32-bit: launch_tile only accepts levels whose node and wedge arrays have
   // fewer than 2^31 entries.
   constexpr int NIN = Op::NIN, NOUT = Op::NOUT, W = TT + 1;
@@ -324,9 +397,11 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
 #pragma unroll
       for (int q = 0; q < 9; ++q) Mi[w][q] = geo[q * nt + t0 + w];
       dM[w] = geo[9 * nt + t0 + w];
+      if (EK != TN_ETA_F32 && Op::USES_ETA) dM[w] *= eta.cs[t0 + w];
     }
   }
-  const T* eta_col = eta ? eta + (((d * (n_r - 1)) * N + ci0) * N + cj0) * 2 : nullptr;  // layer k: + k N^2 2
+  // viscosity of the cell's two wedges at layer k: pair k N^2 2 + {0, 1} past the column base
+  const int eta_c0 = (((d * (n_r - 1)) * N + ci0) * N + cj0) * 2;
   const int eta_ls = N * N * 2;
   // the node this thread owns: (ci, cj) when ti, tj >= 1; the last tile row / column also owns
   // node N (handled in the rare path below)
@@ -375,6 +450,10 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c] += uu[c] - pu[c];
       }
+    }
+    if (EPI != EPI_NONE && !shared) {  // fused vector update; nothing else is stored
+      epilogue<T, EPI>(E, in0, in1, in2, idx, v);
+      return;
     }
     out0[idx] = v[0];
     if (NOUT > 1) out1[idx] = v[NOUT > 1 ? 1 : 0];
@@ -443,7 +522,21 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
       for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
     if (cell_ok) {
       T e[2] = {(T)1, (T)1};
-      if (Op::USES_ETA) e[0] = eta_col[k * eta_ls], e[1] = eta_col[k * eta_ls + 1];
+      if (Op::USES_ETA) {
+        const int o = eta_c0 + k * eta_ls;  // even: the pair is one aligned vector load
+        if (EK == TN_ETA_F32) {
+          if (sizeof(T) == 8) {
+            const double2 p = *reinterpret_cast<const double2*>(eta.v + o);
+            e[0] = (T)p.x, e[1] = (T)p.y;
+          } else {
+            const float2 p = *reinterpret_cast<const float2*>(eta.v + o);
+            e[0] = (T)p.x, e[1] = (T)p.y;
+          }
+        } else {
+          const uint32_t p = *reinterpret_cast<const uint32_t*>(eta.q + o);
+          e[0] = (T)from16<EK>((uint16_t)(p & 0xffffu)), e[1] = (T)from16<EK>((uint16_t)(p >> 16));
+        }
+      }
       op.cell(ub, ut, Mi, dM, lay + kLayerStride * k, e, accb, acct);
     }
     if (k >= kc0) {
@@ -464,9 +557,11 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
 }
 
-template <typename T, typename Op, int FLAGS>
-cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const T* eta,
-                        cudaStream_t st, const int* skip = nullptr) {
+template <typename T, typename Op, int FLAGS, int EPI = EPI_NONE>
+cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const EtaView<T>& eta,
+                        cudaStream_t st, const int* skip = nullptr, const EpiArgs<T>* epi = nullptr) {
+  EpiArgs<T> E{};
+  if (epi) E = *epi;
   Dims D = dims(L);
   if (L.n_layout >= (int64_t)INT32_MAX || L.n_wedges >= (int64_t)INT32_MAX || 10 * L.n_tri >= (int64_t)INT32_MAX)
     return cudaErrorInvalidValue;  // the tile kernel uses 32-bit offsets
@@ -484,10 +579,24 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   const T* sv = Tab<T>::s(L);
   const T* geo = Tab<T>::geo(L);
   const T* lay = Tab<T>::lay(L);
+  // 16-bit viscosity: only full tiles (levels with N >= 16 store it) and the ops that read it
+  if constexpr (Op::USES_ETA && sizeof(T) == 4) {
+    if (eta.kind != TN_ETA_F32) {
+    if (tt != TILE) return cudaErrorInvalidValue;
+    constexpr int B = (TILE + 1) * (TILE + 1);
+    if (eta.kind == TN_ETA_BF16)
+      k_tile<T, Op, TILE, FLAGS, EPI, TN_ETA_BF16><<<grid, B, 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, geo, lay,
+                                                                      eta, sv, bc.in, bc.out, kc, skip, E);
+    else
+      k_tile<T, Op, TILE, FLAGS, EPI, TN_ETA_F16><<<grid, B, 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, geo, lay,
+                                                                     eta, sv, bc.in, bc.out, kc, skip, E);
+    return cudaGetLastError();
+    }
+  }
 #define TN_TILE_CASE(TTv)                                                                                     \
   case TTv:                                                                                                   \
-    k_tile<T, Op, TTv, FLAGS><<<grid, (TTv + 1) * (TTv + 1), 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, \
-                                                                       geo, lay, eta, sv, bc.in, bc.out, kc, skip); \
+    k_tile<T, Op, TTv, FLAGS, EPI><<<grid, (TTv + 1) * (TTv + 1), 0, st>>>(                           \
+        D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E);           \
     break;
   switch (tt) {
     TN_TILE_CASE(16)
@@ -540,6 +649,40 @@ __global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, 
     for (int c = 0; c < ncomp; ++c) y[c][goff[q] + lo] = v[c];
 }
 
+// Interface sum of K x partials (mode 1: + (I - P) x at boundary layers) followed by the fused
+// vector update of the group's node, written to every copy.
+template <typename T, int EPI>
+__global__ void k_interface_epi(Dims D, int n_groups, const int* __restrict__ gptr, const int64_t* __restrict__ goff,
+                                const T* __restrict__ gs, const T* __restrict__ t0, const T* __restrict__ t1,
+                                const T* __restrict__ t2, const T* __restrict__ x0, const T* __restrict__ x1,
+                                const T* __restrict__ x2, int bc_in, int bc_out, const int* __restrict__ skip,
+                                EpiArgs<T> E) {
+  if (skip && *skip) return;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)n_groups * D.n_r) return;
+  const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
+  const T* y[3] = {t0, t1, t2};
+  const T* u[3] = {x0, x1, x2};
+  const int b = gptr[g], e = gptr[g + 1];
+  const int64_t lo = (int64_t)k * D.layer_stride;
+  T v[3] = {0, 0, 0};
+  for (int q = b; q < e; ++q)
+    for (int c = 0; c < 3; ++c) v[c] += y[c][goff[q] + lo];
+  if (k == 0 || k == D.n_r - 1) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    T w[3];
+    for (int c = 0; c < 3; ++c) w[c] = u[c][goff[b] + lo];
+    if (bc == TN_BC_NOSLIP) {
+      for (int c = 0; c < 3; ++c) v[c] += w[c];
+    } else {
+      T s[3] = {gs[g], gs[n_groups + g], gs[2 * n_groups + g]};
+      T dot = w[0] * s[0] + w[1] * s[1] + w[2] * s[2];
+      for (int c = 0; c < 3; ++c) v[c] += dot * s[c];
+    }
+  }
+  for (int q = b; q < e; ++q) epilogue<T, EPI>(E, x0, x1, x2, (int)(goff[q] + lo), v);
+}
+
 // ------------------------------------------------------------------------------------ diag(A)
 // Thread per layout node; gathers the 3x3 node block of A from the (up to) 12 wedges
 // around the node: A_jj = sum_e V eta (|g|^2 I + 1/3 g g^T) (the -2/3 div term gives
@@ -547,7 +690,7 @@ __global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, 
 // Only the two boundary node layers are handled here (the tile kernel with OpDiag writes the
 // interior layers): blocks = 10 * 2 * (N+1)^2 threads, layer 0 and layer n_r - 1.
 template <typename T>
-__global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, const T* __restrict__ eta,
+__global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* d0, T* d1, T* d2) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -576,7 +719,7 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
-      const T ve = vol * dM * eta[((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w];
+      const T ve = vol * dM * eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
       const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
       alpha += ve * g2;
       const T tv = ve * third;
@@ -621,7 +764,7 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
 // as 6 entries (xx, yy, zz, xy, xz, yz).  Same gather as k_diag_A; nodes on diamond edges get
 // P A_partial P per diamond and the identity part is added once by k_interface_block.
 template <typename T>
-__global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, const T* __restrict__ eta,
+__global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
                           const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* b0, T* b1, T* b2, T* b3,
                           T* b4, T* b5) {
   const int N = D.N, M = N + 1;
@@ -649,7 +792,7 @@ __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
-      const T ve = vol * dM * eta[((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w];
+      const T ve = vol * dM * eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
       alpha += ve * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       const T tv = ve * third;
       B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
@@ -842,7 +985,7 @@ __global__ void k_project_bdry(Dims D, T* y0, T* y1, T* y2, const T* __restrict_
 // (3/4, 1/4) for the lower child layer and (1/4, 3/4) for the upper one.
 template <typename T>
 __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T* __restrict__ layF,
-                             const T* __restrict__ etaF, T* m) {
+                             EtaView<T> etaF, T* m) {
   const int NC = C.N, MC = NC + 1, NF = F.N;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
@@ -869,7 +1012,7 @@ __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T
           const T wr = (side == 0) == (r == 0) ? (T)0.75 : (T)0.25;
           const T psi = wl * wr;
           const T V = layF[kLayerStride * kf + 2] * dM;
-          const T e = etaF[((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw];
+          const T e = eta_at(etaF, ((((int64_t)d * (F.n_r - 1) + kf) * NF + fi) * NF + fj) * 2 + fw, t);
           acc += V / e * psi * psi;
         }
       }
@@ -979,15 +1122,42 @@ template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                            const int* skip) {
   OpA<T> op{div_term};
-  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, Tab<T>::eta(L), st, skip);
+  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, etav<T>(L), st, skip);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 1, y, u, st, skip);
 }
 
 template <typename T>
+cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
+                               T* const* t, cudaStream_t st, const int* skip) {
+  OpA<T> op{div_term};
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  cudaError_t e;
+  switch (epi) {
+    case EPI_RESID: e = launch_tile<T, OpA<T>, F, EPI_RESID>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
+    case EPI_CHEB1: e = launch_tile<T, OpA<T>, F, EPI_CHEB1>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
+    case EPI_CHEB2: e = launch_tile<T, OpA<T>, F, EPI_CHEB2>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)L.n_groups * L.n_r;
+  if (n == 0) return cudaSuccess;
+  const unsigned nb = nblk(n, 128);
+  const Dims D = dims(L);
+#define TN_IEPI(EP)                                                                                             \
+  k_interface_epi<T, EP><<<nb, 128, 0, st>>>(D, L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), t[0], t[1], t[2], \
+                                             in[0], in[1], in[2], bc.in, bc.out, skip, E)
+  if (epi == EPI_RESID) TN_IEPI(EPI_RESID);
+  else if (epi == EPI_CHEB1) TN_IEPI(EPI_CHEB1);
+  else TN_IEPI(EPI_CHEB2);
+#undef TN_IEPI
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st) {
   T* out[1] = {q};
-  cudaError_t e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, nullptr, st);
+  cudaError_t e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, EtaView<T>{}, st);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 1, 0, out, nullptr, st);
 }
@@ -995,7 +1165,7 @@ cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cuda
 template <typename T>
 cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cudaStream_t st) {
   const T* in[1] = {p};
-  cudaError_t e = launch_tile<T, OpGrad<T>, PROJ_OUT>(L, bc, OpGrad<T>{}, in, y, nullptr, st);
+  cudaError_t e = launch_tile<T, OpGrad<T>, PROJ_OUT>(L, bc, OpGrad<T>{}, in, y, EtaView<T>{}, st);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 0, y, nullptr, st);
 }
@@ -1006,10 +1176,10 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
   // interior layers: per-cell tile kernel (boundary layers are overwritten below)
   OpDiag<T> op{div_term};
   const T* none[1] = {d[0]};
-  cudaError_t e = launch_tile<T, OpDiag<T>, 0>(L, bc, op, none, d, Tab<T>::eta(L), st);
+  cudaError_t e = launch_tile<T, OpDiag<T>, 0>(L, bc, op, none, d, etav<T>(L), st);
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
-  k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), Tab<T>::eta(L), Tab<T>::s(L), bc.in,
+  k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
                                             bc.out, div_term, d[0], d[1], d[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1020,7 +1190,7 @@ template <typename T>
 cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b, cudaStream_t st) {
   Dims D = dims(L);
   const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
-  k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), Tab<T>::eta(L), Tab<T>::s(L), bc.in,
+  k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
                                              bc.out, div_term, b[0], b[1], b[2], b[3], b[4], b[5]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1038,7 +1208,7 @@ cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b,
 template <typename T>
 cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st) {
   const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
-  k_diag_pmass<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), Tab<T>::eta(F), m);
+  k_diag_pmass<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), etav<T>(F), m);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   T* out[1] = {m};
@@ -1105,6 +1275,38 @@ cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef,
   return cudaGetLastError();
 }
 
+// Thread per lateral wedge column t = ((d N + i) N + j) 2 + w: c = sqrt(min * max) of the FP64
+// viscosity over the column's n_r - 1 cells (rounded to FP32), then each value stored as the
+// 16-bit rounding (to nearest even) of the FP32 rounding of eta / c.
+template <int KIND>
+__global__ void k_eta_16(Dims D, const double* __restrict__ eta, uint16_t* __restrict__ q, float* __restrict__ cs) {
+  const int64_t per_d = (int64_t)2 * D.N * D.N;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= 10 * per_d) return;
+  const int64_t base = (t / per_d) * (D.n_r - 1) * per_d + t % per_d;  // wedge index at k = 0
+  double mn = eta[base], mx = eta[base];
+  for (int k = 1; k < D.n_r - 1; ++k) {
+    const double e = eta[base + k * per_d];
+    mn = fmin(mn, e), mx = fmax(mx, e);
+  }
+  const float c = (float)sqrt(mn * mx);
+  cs[t] = c;
+  for (int k = 0; k < D.n_r - 1; ++k) {
+    const float r = (float)(eta[base + k * per_d] / (double)c);
+    q[base + k * per_d] = KIND == TN_ETA_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(r))
+                                              : __half_as_ushort(__float2half_rn(r));
+  }
+}
+
+cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st) {
+  if (L.eta_kind == TN_ETA_F32) return launch_to_f32(L.eta64, L.eta32, L.n_wedges, st);
+  if (L.eta_kind == TN_ETA_BF16)
+    k_eta_16<TN_ETA_BF16><<<nblk(L.n_tri, 256), 256, 0, st>>>(dims(L), L.eta64, L.eta16, L.eta_cs);
+  else
+    k_eta_16<TN_ETA_F16><<<nblk(L.n_tri, 256), 256, 0, st>>>(dims(L), L.eta64, L.eta16, L.eta_cs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st) {
   k_to_f32<<<nblk(n, 256), 256, 0, st>>>(a, b, n);
   return cudaGetLastError();
@@ -1122,6 +1324,8 @@ cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, d
   template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t,       \
                                          const int*);                                                            \
   template cudaError_t launch_div_fine<T>(const Level&, BC, const T* const*, T*, cudaStream_t);                 \
+  template cudaError_t launch_apply_A_epi<T>(const Level&, BC, int, int, const T* const*, const EpiArgs<T>&,     \
+                                             T* const*, cudaStream_t, const int*);                              \
   template cudaError_t launch_grad_fine<T>(const Level&, BC, const T*, T* const*, cudaStream_t);                \
   template cudaError_t launch_diag_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                        \
   template cudaError_t launch_block_inv_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                   \

@@ -389,7 +389,12 @@ struct Vec3 {
 
 template <typename T>
 struct MGLevelT {
-  Vec3<T> x, b, r, d, t, p;  // p only on the coarsest level
+  // x and d are double-buffered: the fused Chebyshev updates write the new x (or d) while the
+  // apply still reads the old one; xi / di select the current buffer.
+  Vec3<T> xb[2], b, r, db[2], t, p;  // p only on the coarsest level
+  int xi = 0, di = 0;
+  Vec3<T>& x() { return xb[xi]; }
+  Vec3<T>& d() { return db[di]; }
   T* binv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // inverse node blocks
   double lam = 0.0;
   B6<T> bi() const {
@@ -631,16 +636,16 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   // r = b, z = D^-1 r (stored in d), p = z, x = 0
   k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.b.cc(), 3), 0.0, M4<T>(C.r.mm(), 3));
   ckl();
-  k_bmul<T><<<nb(n), EB, 0, st>>>(n, C.bi(), P4<T>(C.r.cc(), 3), M4<T>(C.d.mm(), 3));
+  k_bmul<T><<<nb(n), EB, 0, st>>>(n, C.bi(), P4<T>(C.r.cc(), 3), M4<T>(C.d().mm(), 3));
   ckl();
-  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.d.cc(), 3), 0.0, M4<T>(C.p.mm(), 3));
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.d().cc(), 3), 0.0, M4<T>(C.p.mm(), 3));
   ckl();
-  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(C.d.cc(), 3), 0.0, M4<T>(C.x.mm(), 3));
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(C.d().cc(), 3), 0.0, M4<T>(C.x().mm(), 3));
   ckl();
   k_set_int<<<1, 1, 0, st>>>(m->flag, 0);
   ckl();
   const T* const* rr[1] = {C.r.cc()};
-  dots<T>(m, L, 1, 3, rr, C.d.cc(), m->S + S_RZ0, st);
+  dots<T>(m, L, 1, 3, rr, C.d().cc(), m->S + S_RZ0, st);
   k_cg_start<<<1, 1, 0, st>>>(m->S, m->flag);
   ckl();
   const double tol2 = m->opts.coarse_rtol * m->opts.coarse_rtol;
@@ -652,33 +657,54 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
     k_cg_alpha<<<1, 1, 0, st>>>(m->S, m->flag);
     ckl();
     k_cg_update<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.p.cc(), 3), P4<T>(C.t.cc(), 3), C.bi(),
-                                         M4<T>(C.x.mm(), 3), M4<T>(C.r.mm(), 3), M4<T>(C.d.mm(), 3), m->flag);
+                                         M4<T>(C.x().mm(), 3), M4<T>(C.r.mm(), 3), M4<T>(C.d().mm(), 3), m->flag);
     ckl();
-    dots<T>(m, L, 1, 3, rr, C.d.cc(), m->S + S_RZN, st, m->flag);
+    dots<T>(m, L, 1, 3, rr, C.d().cc(), m->S + S_RZN, st, m->flag);
     k_cg_beta<<<1, 1, 0, st>>>(m->S, m->flag, tol2, it == maxit - 1);
     ckl();
-    k_cg_dir<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.d.cc(), 3), M4<T>(C.p.mm(), 3), m->flag);
+    k_cg_dir<T><<<nb(n), EB, 0, st>>>(n, m->S, P4<T>(C.d().cc(), 3), M4<T>(C.p.mm(), 3), m->flag);
     ckl();
   }
-  if (proj) project_rotations<T>(m, L, C.x.mm(), st);
+  if (proj) project_rotations<T>(m, L, C.x().mm(), st);
 }
 
-// One degree-2 Chebyshev smoothing step on level h (x updated in place, rhs b).
+// One degree-2 Chebyshev smoothing step on level h (rhs b): the two operator applications carry
+// the vector updates in their epilogues (r = b - K x, d = D^-1 r / theta, x += d; then
+// r -= K d, d = c1 d + c2 D^-1 r, x += d).
+template <typename T>
+EpiArgs<T> epi_of(MGLevelT<T>& G) {
+  EpiArgs<T> E{};
+  for (int c = 0; c < 3; ++c) E.b[c] = G.b.c[c], E.r[c] = G.r.c[c];
+  for (int q = 0; q < 6; ++q) E.binv[q] = G.binv[q];
+  return E;
+}
+
 template <typename T>
 void cheb_step(MGState* m, const tn_mesh* mesh, int h, bool zero_x, cudaStream_t st) {
   MGLevelT<T>& G = ps<T>(m).L[h];
-  const int64_t n = m->geo[h]->n_layout;
+  const Level& L = *m->geo[h];
+  const BC bc{mesh->bc_in, mesh->bc_out};
+  const int64_t n = L.n_layout;
   const double a = m->opts.cheb_lo * G.lam, b = m->opts.cheb_hi * G.lam;
   const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
   const double rho0 = 1.0 / sigma, rho1 = 1.0 / (2.0 * sigma - rho0);
-  if (!zero_x) apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
-  k_cheb1<T><<<nb(n), EB, 0, st>>>(n, zero_x ? 1 : 0, 1.0 / theta, P4<T>(G.b.cc(), 3), P4<T>(G.t.cc(), 3),
-                                   G.bi(), M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
-  ckl();
-  apply_K_level<T>(mesh, h, G.d.cc(), G.t.mm(), st);
-  k_cheb2<T><<<nb(n), EB, 0, st>>>(n, rho1 * rho0, 2.0 * rho1 / delta, P4<T>(G.t.cc(), 3), G.bi(),
-                                   M4<T>(G.r.mm(), 3), M4<T>(G.d.mm(), 3), M4<T>(G.x.mm(), 3));
-  ckl();
+  if (zero_x) {
+    k_cheb1<T><<<nb(n), EB, 0, st>>>(n, 1, 1.0 / theta, P4<T>(G.b.cc(), 3), P4<T>(G.b.cc(), 3), G.bi(),
+                                     M4<T>(G.r.mm(), 3), M4<T>(G.d().mm(), 3), M4<T>(G.x().mm(), 3));
+    ckl();
+  } else {
+    EpiArgs<T> E = epi_of(G);
+    E.c0 = 1.0 / theta;
+    for (int c = 0; c < 3; ++c) E.dout[c] = G.d().c[c], E.xout[c] = G.xb[1 - G.xi].c[c];
+    ck(launch_apply_A_epi<T>(L, bc, mesh->div_term, EPI_CHEB1, G.x().cc(), E, G.t.mm(), st));
+    G.xi = 1 - G.xi;
+  }
+  EpiArgs<T> E = epi_of(G);
+  E.c1 = rho1 * rho0;
+  E.c2 = 2.0 * rho1 / delta;
+  for (int c = 0; c < 3; ++c) E.xacc[c] = G.x().c[c], E.xout[c] = G.x().c[c], E.dout[c] = G.db[1 - G.di].c[c];
+  ck(launch_apply_A_epi<T>(L, bc, mesh->div_term, EPI_CHEB2, G.d().cc(), E, G.t.mm(), st));
+  G.di = 1 - G.di;
 }
 
 // V-cycle on level h: x_h = V(b_h)
@@ -694,19 +720,21 @@ void vcycle_level(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   const Level& Lc = *m->geo[h + 1];
   const BC bc{mesh->bc_in, mesh->bc_out};
   const int64_t n = F.n_layout;
+  // The cycle starts from x = 0, so the buffer choice is reset: every cycle (captured or not)
+  // then leaves x in the same buffer and readers after it see the right one.
+  G.xi = 0, G.di = 0;
   for (int s = 0; s < m->opts.pre_smooth; ++s) cheb_step<T>(m, mesh, h, s == 0, st);
   if (m->opts.pre_smooth == 0)
-    k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(G.b.cc(), 3), 0.0, M4<T>(G.x.mm(), 3)), ckl();
-  // r = b - K x
-  apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
-  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(G.b.cc(), 3), 0.0, M4<T>(G.r.mm(), 3));
-  ckl();
-  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, -1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.r.mm(), 3));
-  ckl();
+    k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 0.0, P4<T>(G.b.cc(), 3), 0.0, M4<T>(G.x().mm(), 3)), ckl();
+  // r = b - K x (fused into the apply)
+  {
+    EpiArgs<T> E = epi_of(G);
+    ck(launch_apply_A_epi<T>(F, bc, mesh->div_term, EPI_RESID, G.x().cc(), E, G.t.mm(), st));
+  }
   ck(launch_restrict<T>(F, Lc, bc, 3, 1, G.r.cc(), C.b.mm(), st));
   vcycle_level<T>(m, mesh, h + 1, st);
-  ck(launch_prolong<T>(F, Lc, bc, 3, 1, C.x.cc(), G.t.mm(), st));
-  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.x.mm(), 3));
+  ck(launch_prolong<T>(F, Lc, bc, 3, 1, C.x().cc(), G.t.mm(), st));
+  k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.x().mm(), 3));
   ckl();
   for (int s = 0; s < m->opts.post_smooth; ++s) cheb_step<T>(m, mesh, h, false, st);
 }
@@ -759,7 +787,8 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
     for (int h = 0; h < m->nlev; ++h) {
       const int64_t n = m->geo[h]->n_layout;
       MGLevelT<T>& G = P.L[h];
-      G.x = alloc3<T>(m, n), G.b = alloc3<T>(m, n), G.r = alloc3<T>(m, n), G.d = alloc3<T>(m, n);
+      G.xb[0] = alloc3<T>(m, n), G.xb[1] = alloc3<T>(m, n), G.b = alloc3<T>(m, n), G.r = alloc3<T>(m, n);
+      G.db[0] = alloc3<T>(m, n), G.db[1] = alloc3<T>(m, n);
       G.t = alloc3<T>(m, n);
       for (int q = 0; q < 6; ++q) G.binv[q] = alloc_zero<T>(m, n);
       if (h == m->nlev - 1) G.p = alloc3<T>(m, n);
@@ -780,7 +809,7 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
     MGLevelT<T>& G = P.L[0];
     if (v0) {
       for (int c = 0; c < 3; ++c)
-        ck(cudaMemcpyAsync(G.x.c[c], v0[c], sizeof(T) * L.n_layout, cudaMemcpyDeviceToDevice, st));
+        ck(cudaMemcpyAsync(G.x().c[c], v0[c], sizeof(T) * L.n_layout, cudaMemcpyDeviceToDevice, st));
     } else {
       std::vector<int64_t> canon((size_t)L.n_layout);
       tn_mesh_canonical_index(mesh, 0, canon.data());
@@ -794,30 +823,30 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
           uint64_t z = splitmix64(m->opts.seed ^ splitmix64((uint64_t)canon[i] * 3 + c));
           hv[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
         }
-        ck(cudaMemcpyAsync(G.x.c[c], hv.data(), sizeof(T) * L.n_layout, cudaMemcpyHostToDevice, st));
+        ck(cudaMemcpyAsync(G.x().c[c], hv.data(), sizeof(T) * L.n_layout, cudaMemcpyHostToDevice, st));
         ck(cudaStreamSynchronize(st));
       }
     }
   }
   for (int h = 1; h < m->nlev; ++h)
-    ck(launch_restrict<T>(*m->geo[h - 1], *m->geo[h], bc, 3, 1, P.L[h - 1].x.cc(), P.L[h].x.mm(), st));
+    ck(launch_restrict<T>(*m->geo[h - 1], *m->geo[h], bc, 3, 1, P.L[h - 1].x().cc(), P.L[h].x().mm(), st));
   // power iterations on D^-1 K of every smoothing level
   std::vector<double> lam(m->nlev, 0.0);
   for (int h = 0; h + 1 < m->nlev; ++h) {
     MGLevelT<T>& G = P.L[h];
     const Level& L = *m->geo[h];
     const int64_t n = L.n_layout;
-    const T* const* xx[1] = {G.x.cc()};
-    dots<T>(m, L, 1, 3, xx, G.x.cc(), m->S + S_TMP, st);
-    k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.x.cc(), 3), M4<T>(G.x.mm(), 3), m->S + S_TMP);
+    const T* const* xx[1] = {G.x().cc()};
+    dots<T>(m, L, 1, 3, xx, G.x().cc(), m->S + S_TMP, st);
+    k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.x().cc(), 3), M4<T>(G.x().mm(), 3), m->S + S_TMP);
     ckl();
     for (int it = 0; it < m->opts.power_iters; ++it) {
-      apply_K_level<T>(mesh, h, G.x.cc(), G.t.mm(), st);
-      k_bmul<T><<<nb(n), EB, 0, st>>>(n, G.bi(), P4<T>(G.t.cc(), 3), M4<T>(G.d.mm(), 3));
+      apply_K_level<T>(mesh, h, G.x().cc(), G.t.mm(), st);
+      k_bmul<T><<<nb(n), EB, 0, st>>>(n, G.bi(), P4<T>(G.t.cc(), 3), M4<T>(G.d().mm(), 3));
       ckl();
-      const T* const* dd[1] = {G.d.cc()};
-      dots<T>(m, L, 1, 3, dd, G.d.cc(), m->S + S_TMP + h % 4, st);
-      k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.d.cc(), 3), M4<T>(G.x.mm(), 3), m->S + S_TMP + h % 4);
+      const T* const* dd[1] = {G.d().cc()};
+      dots<T>(m, L, 1, 3, dd, G.d().cc(), m->S + S_TMP + h % 4, st);
+      k_normalize<T><<<nb(n), EB, 0, st>>>(n, 3, P4<T>(G.d().cc(), 3), M4<T>(G.x().mm(), 3), m->S + S_TMP + h % 4);
       ckl();
     }
     double l2 = 0.0;
@@ -853,7 +882,7 @@ tn_status mg_setup_t(tn_mesh* mesh, const void* const* v0, cudaStream_t st) {
       k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, -1.0, P4<T>(G.t.cc(), 3), 1.0, M4<T>(G.b.mm(), 3));
       ckl();
       vcycle_level<T>(m, mesh, 0, st);
-      k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, 1.0, P4<T>(G.x.cc(), 3), 1.0, M4<T>(wv.mm(), 3));
+      k_axpby<T><<<nb(n0), EB, 0, st>>>(n0, 3, 1.0, P4<T>(G.x().cc(), 3), 1.0, M4<T>(wv.mm(), 3));
       ckl();
     }
     ck(launch_div_fine<T>(L0, bc, wv.cc(), scr, st));
@@ -889,7 +918,7 @@ void vcycle_t(tn_mesh* mesh, const T* const* r, T* const* z, cudaStream_t st) {
   const int64_t n = mesh->lv[0].n_layout;
   for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(G.b.c[c], r[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
   run_vcycle<T>(m, mesh, st);
-  for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(z[c], G.x.c[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+  for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(z[c], G.x().c[c], sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
 }
 
 // ============================================================================ FGMRES
@@ -969,7 +998,7 @@ void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStr
   ckl();
   run_vcycle<T>(m, mesh, st);
   for (int c = 0; c < 3; ++c)
-    ck(cudaMemcpyAsync(z.u[c], G.x.c[c], sizeof(T) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
+    ck(cudaMemcpyAsync(z.u[c], G.x().c[c], sizeof(T) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
 }
 
 
@@ -1180,7 +1209,7 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
         continue;
       }
       Level* L = new Level();
-      tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out);
+      tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out, mesh->eta_storage);
       m->owned_levels.push_back(L);
       if (cs != TN_OK) {
         mesh->mg = m;
@@ -1205,7 +1234,7 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
   for (int h = 1; h < m->nlev; ++h) {
     if (m->geo[h] == &mesh->lv[h]) continue;
     ck(launch_eta_coarsen(*m->geo[h - 1], *m->geo[h], m->geo[h - 1]->eta64, m->geo[h]->eta64, st));
-    ck(launch_to_f32(m->geo[h]->eta64, m->geo[h]->eta32, m->geo[h]->n_wedges, st));
+    ck(launch_eta_f32_path(*m->geo[h], st));
   }
   tn_status s = prec == TN_F64 ? mg_setup_t<double>(mesh, v0, st) : mg_setup_t<float>(mesh, v0, st);
   if (s != TN_OK) set_error(std::string("tn_mg_setup: ") + cudaGetErrorString(g_err));

@@ -34,9 +34,9 @@ def tn():
 class Case:
     """One mesh on both sides with random fields (seeded)."""
 
-    def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0):
+    def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0, eta_storage=0):
         self.tn = tn
-        self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term)
+        self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term, eta_storage=eta_storage)
         self.info = tn.tn_mesh_info(self.m, 0)
         self.om = ShellMesh(level, n_r, r_in, r_out)
         self.map = LayoutMap(self.info, self.om)
@@ -113,6 +113,44 @@ def test_apply_A_f32(tn):
     tn.tn_apply_A(c.m, 0, [c.dev(u[i], torch.float32) for i in range(3)], y)
     got = np.stack([c.host(t) for t in y])
     assert max_rel(got, want) <= TOL32
+    c.close()
+
+
+def _bf16_round(x32):
+    """float32 -> bfloat16 (round to nearest even), returned as float32."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint32)
+    return (b << 16).view(np.float32)
+
+
+def stored_viscosity(eta_layout, N, n_r, kind):
+    """The viscosity the FP32 kernels see under 16-bit storage, from the format the header
+    states: per radial column of wedges c = fp32(sqrt(min max)), value = 16-bit(fp32(eta / c)) * c."""
+    e = eta_layout.reshape(10, n_r - 1, 2 * N * N)
+    c = np.sqrt(e.min(axis=1) * e.max(axis=1)).astype(np.float32)
+    r = (e / c[:, None, :].astype(np.float64)).astype(np.float32)
+    q = _bf16_round(r) if kind == 1 else r.astype(np.float16).astype(np.float32)
+    return (q.astype(np.float64) * c[:, None, :].astype(np.float64)).reshape(-1)
+
+
+@pytest.mark.parametrize("kind,unit", [(1, 2.0 ** -8), (2, 2.0 ** -11)])
+def test_apply_A_and_diag_f32_with_16bit_viscosity(tn, kind, unit):
+    c = Case(tn, 4, 17, eta_storage=kind)
+    eta_q = c.map.wedges_from_layout(stored_viscosity(c.map.wedges_to_layout(c.eta), 16, 17, kind))
+    # rounding to nearest: relative change at most the unit roundoff (plus the FP32 steps)
+    assert np.abs(eta_q / c.eta - 1).max() <= unit * (1 + 1e-3) + 2e-7
+    u = c.vec(12)
+    y = c.zeros(dtype=torch.float32)
+    tn.tn_apply_A(c.m, 0, [c.dev(u[i], torch.float32) for i in range(3)], y)
+    got = np.stack([c.host(t) for t in y])
+    err_q = max_rel(got, O.apply_A_constrained(c.om, eta_q, u, c.P))
+    err_full = max_rel(got, O.apply_A_constrained(c.om, c.eta, u, c.P))
+    print(f"kind {kind}: vs stored eta {err_q:.2e}, vs FP64 eta {err_full:.2e}")
+    assert err_q <= TOL32
+    assert err_full > 10 * err_q  # the kernel really read the 16-bit values
+    d = c.zeros(dtype=torch.float32)
+    tn.tn_diag_A(c.m, 0, d)
+    assert max_rel(np.stack([c.host(t) for t in d]), O.diag_A_constrained(c.om, eta_q, c.P)) <= TOL32
     c.close()
 
 
