@@ -36,6 +36,10 @@ A_FLOPS_PER_CELL = 400.0
 # DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 164.5 MB for
 # 2,621,440 cells), scaled to the bench size by cells; None once the kernel changes.
 A_TRAFFIC_BYTES_PER_CELL = None
+# Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
+# restriction, interface), B^T 3 (prolongation, tile, interface), diag 3 (tile, boundary-layer
+# gather, interface).
+LAUNCHES_PER_STEP = 12
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -202,10 +206,10 @@ def layout_temperature(tn, m, noise_seed=None, noise_scale=0.01):
     return T
 
 
-def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0):
+def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=0.0):
     """One Stokes solve to 1e-8 (multigrid set-up excluded from the time).  Returns the stats and
     the solution (u, p) on the unique nodes, as host FP64 arrays."""
-    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, eta_storage=eta_storage)
+    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, eta_storage=eta_storage, hg_kappa=hg_kappa)
     try:
         info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
         Td = torch.tensor(layout_temperature(tn, m), device=dev)
@@ -423,7 +427,7 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
-            "gpu_launches": 11 * args.steps,
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         }
         if world == 1 and not args.no_solve:
             # Stokes solves to 1e-8: FP64 against FP32 inner solves with FP64 refinement

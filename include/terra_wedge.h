@@ -97,6 +97,10 @@ typedef struct {
   int div_term;       /* 1: keep the -2/3 div div term of Eq. elemmat (default); 0: drop it */
   int max_levels;     /* upper bound on the hierarchy depth (0 = as deep as possible) */
   int eta_storage;    /* tn_eta_storage of the FP32 path's viscosity (default TN_ETA_F32) */
+  double hg_kappa;    /* hourglass control of the A block, Eq. hgstab (default 0 = off): every level's
+                       * element matrices get eps_e sum_m,d (g_m x e_d)(g_m x e_d)^T with
+                       * eps_e = hg_kappa tr(A_e) / 18 and g_m the hourglass vectors of Eq. hourglass
+                       * minus their physical linear part (rigid motions keep zero energy) */
 } tn_mesh_opts;
 
 typedef struct {

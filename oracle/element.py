@@ -13,6 +13,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * Viscous element matrix, Eq. (elemmat) under the one-point rule:
   (A_e)_{ab} = V_e eta_e [2 eps(phi_a) : eps(phi_b) - 2/3 div(phi_a) div(phi_b)]
   for vector basis functions phi_a = N_j e_d, a = 3 j + d.
+* Hourglass control, Eq. (hgstab): A_e + eps_e sum_m sum_d (g_m x e_d)(g_m x e_d)^T.
+  Readings (the paper leaves both open): g_m are the nodal hourglass vectors w_m of
+  Eq. (hourglass) with their physical linear part removed, g_m = w_m - sum_c (w_m . X_c) dN/dx_c,
+  the hourglass base vectors of Flanagan & Belytschko (1981) -- so that rigid motions and every
+  linear field keep zero stabilisation energy; eps_e = kappa tr(A_e) / 18, kappa times the mean
+  diagonal entry of the element matrix ("scaled with the local stiffness").
 """
 import numpy as np
 
@@ -87,3 +93,23 @@ def hourglass_vectors():
     w1 = np.array([(xi - 1.0 / 3.0) * z for xi, _, z in nodes])
     w2 = np.array([(et - 1.0 / 3.0) * z for _, et, z in nodes])
     return np.stack([w1, w2])
+
+
+def hourglass_base_vectors(x, grad):
+    """g_m = w_m - sum_c (w_m . X_c) grad N(q_c)[:, c] per wedge, shape (n, 2, 6), from node
+    coordinates ``x`` (n, 6, 3) and gradients ``grad`` (n, 6, 3) (Flanagan & Belytschko 1981)."""
+    w = hourglass_vectors()
+    wX = np.einsum("mj,njc->nmc", w, x)
+    return w[None] - np.einsum("nmc,njc->nmj", wX, grad)
+
+
+def hourglass_stabilised(A, g, kappa):
+    """Eq. (hgstab) on element matrices A (n, 18, 18) with base vectors g (n, 2, 6) and
+    eps_e = kappa tr(A_e) / 18; DoF a = 3 j + d."""
+    eps = kappa * np.einsum("naa->n", A) / 18.0
+    S = np.zeros_like(A)
+    for m in range(2):
+        G = np.einsum("ni,nj->nij", g[:, m], g[:, m])
+        for d in range(3):
+            S[:, d::3, d::3] += G
+    return A + eps[:, None, None] * S

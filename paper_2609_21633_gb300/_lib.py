@@ -27,7 +27,7 @@ class TnError(RuntimeError):
 
 class tn_mesh_opts(ctypes.Structure):
     _fields_ = [("bc_inner", ctypes.c_int), ("bc_outer", ctypes.c_int), ("div_term", ctypes.c_int),
-                ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int)]
+                ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int), ("hg_kappa", ctypes.c_double)]
 
 
 class tn_level_info(ctypes.Structure):
@@ -166,8 +166,8 @@ def _prec(dtype):
 
 
 def tn_mesh_create(lateral_level, radial_layers, r_in, r_out, bc_inner=TN_BC_FREESLIP, bc_outer=TN_BC_FREESLIP,
-                   div_term=True, max_levels=0, eta_storage=0):
-    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage)
+                   div_term=True, max_levels=0, eta_storage=0, hg_kappa=0.0):
+    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage, float(hg_kappa))
     out = P()
     _check(lib().tn_mesh_create(lateral_level, radial_layers, r_in, r_out, ctypes.byref(opts), ctypes.byref(out)))
     return out

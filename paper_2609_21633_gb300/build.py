@@ -12,7 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libterra_wedge.so"
-SOURCES = ["kernels.cu", "solver.cu", "server.cu", "api.cu", "noalloc.cu", "mesh.cpp"]
+# (source, extra flags): kernels.cu is compiled in three parts (the FP64 and the FP32 A-apply
+# launchers apart)
+SOURCES = [("kernels.cu", ["-DTN_PART=1"]), ("kernels.cu", ["-DTN_PART=2"]), ("kernels.cu", ["-DTN_PART=3"]),
+           ("solver.cu", []), ("server.cu", []), ("api.cu", []), ("noalloc.cu", []), ("mesh.cpp", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -30,10 +33,10 @@ def build(verbose=False, extra_flags=()):
     os.makedirs(os.path.join(LIBDIR, "obj"), exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", *ARCH, *extra_flags]
     procs, objs = [], []
-    for src in SOURCES:
-        obj = os.path.join(LIBDIR, "obj", src + ".o")
+    for i, (src, flags) in enumerate(SOURCES):
+        obj = os.path.join(LIBDIR, "obj", "%d_%s.o" % (i, src))
         lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
-        cmd = [nvcc(), *common, *lang, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *common, *flags, *lang, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"] if verbose else []
         procs.append((src, cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))

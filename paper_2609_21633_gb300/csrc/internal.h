@@ -10,7 +10,7 @@
 
 namespace tn {
 
-constexpr int kLayerStride = 8;  // values per radial cell in the layer table
+constexpr int kLayerStride = 12;  // values per radial cell in the layer table
 
 // Per-level mesh data.  Host vectors hold the definition; device pointers are
 // owned by the level and freed by tn_mesh_destroy.
@@ -27,7 +27,8 @@ struct Level {
   double* geo64 = nullptr;
   float* geo32 = nullptr;
   // Per radial cell k (kLayerStride values): w0 = 1/(2 rho), w1 = 1/(6 h), vol = rho^2 h, rho,
-  // w1 / w0, vol w0^2, vol w0, 0; rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
+  // w1 / w0, vol w0^2, vol w0, -vol w0 / 6, w0 / (9 w1), vol w1^2, 0, 0;
+  // rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
   double* lay64 = nullptr;
   float* lay32 = nullptr;
   // Lateral unit vectors s, SoA [3][10 (N+1) P] in lateral layout (d (N+1) + i) P + j.
@@ -48,6 +49,8 @@ struct Level {
   double* eta64 = nullptr;
   float* eta32 = nullptr;
   int eta_kind = TN_ETA_F32;
+  // Hourglass control of the A block (0: off): eps_e = hg_kappa tr(A_e) / 18.
+  double hg_kappa = 0;
   uint16_t* eta16 = nullptr;
   float* eta_cs = nullptr;
   // Scratch scalar field in this level's node layout (B / B^T intermediate).
@@ -83,6 +86,7 @@ struct tn_mesh {
   int bc_in = TN_BC_FREESLIP, bc_out = TN_BC_FREESLIP, div_term = 1;
   bool eta_set = false;
   int eta_storage = TN_ETA_F32;
+  double hg_kappa = 0;
   int device = 0;
   double r_in = 0, r_out = 0;
 };

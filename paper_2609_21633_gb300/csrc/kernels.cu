@@ -27,11 +27,19 @@
 // for the paper's additive halo exchange, Sec. 2).
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
+
+// The file is compiled three times: TN_PART 1 holds everything but the A-apply launchers, TN_PART 2
+// the FP64 and TN_PART 3 the FP32 A-apply launchers (their many tile-kernel instantiations then
+// compile in parallel); 0 = all.
+#ifndef TN_PART
+#define TN_PART 0
+#endif
 
 namespace tn {
 
@@ -116,76 +124,167 @@ __device__ __forceinline__ T eta_at(const EtaView<T>& E, int64_t w, int64_t t) {
 // ------------------------------------------------------------------------------------ element ops
 // An op processes both wedges of one hexahedral cell.  Inputs are the nodal values at the
 // cell's four lateral corners (00, 10, 01, 11) on its bottom (ub) and top (ut) node layer;
-// outputs are added to the same eight node slots (accb, acct).  Wedge-local lateral node a of
-// wedge w sits at corner kCorner[w][a]: W0 = (00, 10, 01), W1 = (11, 01, 10).  `lc` points at
-// the cell layer's table entry (w0, w1, vol, rho, r = w1 / w0, vol w0^2, vol w0).
+// the op assigns the cell's contributions to the same eight node slots (accb, acct), every
+// entry.  Wedge-local lateral node a of wedge w sits at corner kCorner[w][a]: W0 = (00, 10, 01),
+// W1 = (11, 01, 10), so corner 00 belongs to W0 only, 11 to W1 only and 10, 01 to both.  `lc`
+// points at the cell layer's table entry (w0, w1, vol, rho, r = w1 / w0, vol w0^2, vol w0,
+// -vol w0 / 6).
 //
 // With a_xi = s_c1 - s_c0, a_eta = s_c2 - s_c0, a_zeta = d_c0 + d_c1 + d_c2 (s = top + bottom,
 // d = top - bottom, per component; the reference gradients scaled to {-1, 0, 1}), the strain
-// G' = a_xi M^-1[0,:] + a_eta M^-1[1,:] + r a_zeta M^-1[2,:] is grad u / w0, and
+// G' = a_xi M^-1[0,:] + a_eta M^-1[1,:] + a_zeta r M^-1[2,:] is grad u / w0, and
 // S'' = vol w0^2 |det M| eta (G' + G'^T - 2/3 tr G' I) is the stress of Eq. (stress) times
-// V w0.  Then H[:,0] = S'' M^-1[0,:]^T, H[:,1] = S'' M^-1[1,:]^T, H[:,2] = r S'' M^-1[2,:]^T
+// V w0.  Then H[:,0] = S'' M^-1[0,:]^T, H[:,1] = S'' M^-1[1,:]^T, H[:,2] = S'' r M^-1[2,:]^T
 // and node (a, bottom / top) receives X_a -/+ H[:,2], X = (-H[:,0] - H[:,1], H[:,0], H[:,1]).
+// Contributions are assigned where a corner is first touched and added otherwise (adding to a
+// zero start would cost an instruction per entry: x + 0 cannot be folded in IEEE arithmetic).
 __device__ constexpr int kCorner[2][3] = {{0, 1, 2}, {3, 2, 1}};
 
-// Viscous block: Eq. (epsq) then Eq. (localapply) at q_c.
+// Corner combination shared by the vector-valued ops: X[q] are the per-corner sums of X, h[w]
+// the H[:,2] column of wedge w; corner 00 gets h[0], 11 gets h[1], 10 and 01 get both.
+template <typename T, int NC>
+__device__ __forceinline__ void combine_corners(const T (&X)[4][NC], const T (&h)[2][NC], T (&accb)[4][NC],
+                                                T (&acct)[4][NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const T h01 = h[0][c] + h[1][c];
+    accb[0][c] = X[0][c] - h[0][c], acct[0][c] = X[0][c] + h[0][c];
+    accb[3][c] = X[3][c] - h[1][c], acct[3][c] = X[3][c] + h[1][c];
+    accb[1][c] = X[1][c] - h01, acct[1][c] = X[1][c] + h01;
+    accb[2][c] = X[2][c] - h01, acct[2][c] = X[2][c] + h01;
+  }
+}
+
+// Per-column state of the ops without any: nothing.
+struct NoCol {};
+
+// Hourglass control, Eq. (hgstab), in the scaled quantities above.  With the hourglass vectors
+// made orthogonal to the physical linear fields (g_m = w_m - sum_c (w_m . X_c) dN/dx_c), and
+// w_1 . X = 2h (s_1 - sbar), w_2 . X = 2h (s_2 - sbar), (s_a - sbar) . M^-1[m,:] known from
+// M^-1 M = I, everything reduces to k9 = w0 / (9 w1) = 1 / (9 r):
+//   alpha_1 = g_1 . u = (d_c1 - a_zeta / 3) - k9 (2 a_xi - a_eta),
+//   alpha_2 = g_2 . u = (d_c2 - a_zeta / 3) - k9 (2 a_eta - a_xi),
+// and eps sum_m alpha_m g_m adds -eps k9 b_1 to H[:,0], -eps k9 b_2 to H[:,1] and
+// +/- eps / 3 (-(b_1 + b_2), b_1, b_2) at lateral nodes (a = 0, 1, 2) on the top / bottom layer,
+// b_1 = 2 alpha_1 - alpha_2, b_2 = 2 alpha_2 - alpha_1.  eps = hgk eta (vol w0^2 eL + vol w1^2 eR),
+// hgk = kappa (3 + c) / 18, eL = 2 |det M| (|m0 + m1|^2 + |m0|^2 + |m1|^2), eR = 6 |det M| |m2|^2
+// (m = rows of M^-1): kappa tr(A_e) / 18, since tr(A_e) = V eta (3 + c) sum_j |grad N_j|^2.
 template <typename T>
+struct HgCol {
+  T eL[2], eR[2];
+};
+template <typename T>
+__device__ __forceinline__ HgCol<T> hg_column(const T (&Mi)[2][9], const T (&dM)[2]) {
+  HgCol<T> col;
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const T* M = Mi[w];
+    T l = 0, q = 0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const T s01 = M[x] + M[3 + x];
+      l += s01 * s01 + M[x] * M[x] + M[3 + x] * M[3 + x];
+      q += M[6 + x] * M[6 + x];
+    }
+    col.eL[w] = (T)2 * dM[w] * l;
+    col.eR[w] = (T)6 * dM[w] * q;
+  }
+  return col;
+}
+
+// Viscous block: Eq. (epsq) then Eq. (localapply) at q_c; HG adds the hourglass control.
+template <typename T, bool HG = false>
 struct OpA {
   static constexpr int NIN = 3, NOUT = 3;
   static constexpr bool USES_ETA = true, LOADS = true;
+  using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
+  T hgk;  // kappa (3 + c) / 18 (HG only)
+  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2]) const {
+    if constexpr (HG) return hg_column(Mi, dM);
+    else return Col{};
+  }
   __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&eta)[2], T (&accb)[4][3],
-                                       T (&acct)[4][3]) const {
+                                       T (&acct)[4][3], const Col& col) const {
     const T r = lc[4], vw2 = lc[5];
-    // accb / acct (zero on entry) first hold the per-corner sums SX of X and SH of H[:,2]
-    T(&SX)[4][3] = accb;
-    T(&SH)[4][3] = acct;
     T s[4][3], dd[4][3];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
+    // X: per-corner sums of X; without HG h[w] is the H[:,2] column of wedge w, with HG Y holds
+    // the per-corner sums of the top-minus-bottom part
+    T X[4][3], h[2][3], Y[4][3];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
       const T* M = Mi[w];
-      T G[3][3];
+      const T mr[3] = {r * M[6], r * M[7], r * M[8]};  // r M^-1[2,:]
+      T G[3][3], al1[3], al2[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = ((dd[c0][c] + dd[c1][c]) + dd[c2][c]) * r;
+        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = (dd[c0][c] + dd[c1][c]) + dd[c2][c];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) G[c][x] = ax * M[x] + ay * M[3 + x] + az * M[6 + x];
+        for (int x = 0; x < 3; ++x) G[c][x] = ax * M[x] + ay * M[3 + x] + az * mr[x];
+        if constexpr (HG) {
+          const T k9 = lc[8], a3 = az * (T)(1.0 / 3.0);
+          al1[c] = (dd[c1][c] - a3) - k9 * (ax + ax - ay);
+          al2[c] = (dd[c2][c] - a3) - k9 * (ay + ay - ax);
+        }
       }
       const T ve = vw2 * dM[w] * eta[w];
-      const T t = div_term ? (T)(2.0 / 3.0) * (G[0][0] + G[1][1] + G[2][2]) : (T)0;
+      const T ve2 = ve + ve;
       T S[3][3];
-      S[0][0] = ve * ((G[0][0] + G[0][0]) - t);
-      S[1][1] = ve * ((G[1][1] + G[1][1]) - t);
-      S[2][2] = ve * ((G[2][2] + G[2][2]) - t);
+      if (div_term) {
+        const T vt = (ve * (T)(-2.0 / 3.0)) * ((G[0][0] + G[1][1]) + G[2][2]);
+        S[0][0] = ve2 * G[0][0] + vt, S[1][1] = ve2 * G[1][1] + vt, S[2][2] = ve2 * G[2][2] + vt;
+      } else {
+        S[0][0] = ve2 * G[0][0], S[1][1] = ve2 * G[1][1], S[2][2] = ve2 * G[2][2];
+      }
       S[0][1] = S[1][0] = ve * (G[0][1] + G[1][0]);
       S[0][2] = S[2][0] = ve * (G[0][2] + G[2][0]);
       S[1][2] = S[2][1] = ve * (G[1][2] + G[2][1]);
+      T ek = 0, e3 = 0;
+      if constexpr (HG) {
+        const T eps = (hgk * eta[w]) * (vw2 * col.eL[w] + lc[9] * col.eR[w]);
+        ek = eps * lc[8], e3 = eps * (T)(1.0 / 3.0);
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T h0 = S[c][0] * M[0] + S[c][1] * M[1] + S[c][2] * M[2];
-        const T h1 = S[c][0] * M[3] + S[c][1] * M[4] + S[c][2] * M[5];
-        const T h2 = r * (S[c][0] * M[6] + S[c][1] * M[7] + S[c][2] * M[8]);
-        SX[c0][c] -= h0 + h1;
-        SX[c1][c] += h0;
-        SX[c2][c] += h1;
-        SH[c0][c] += h2;
-        SH[c1][c] += h2;
-        SH[c2][c] += h2;
+        T h0 = S[c][0] * M[0] + S[c][1] * M[1] + S[c][2] * M[2];
+        T h1 = S[c][0] * M[3] + S[c][1] * M[4] + S[c][2] * M[5];
+        const T h2 = S[c][0] * mr[0] + S[c][1] * mr[1] + S[c][2] * mr[2];
+        if constexpr (HG) {
+          const T b1 = (al1[c] + al1[c]) - al2[c], b2 = (al2[c] + al2[c]) - al1[c];
+          h0 -= ek * b1, h1 -= ek * b2;
+          const T v1 = e3 * b1, v2 = e3 * b2;
+          const T y0 = h2 - (v1 + v2), y1 = h2 + v1, y2 = h2 + v2;
+          Y[c0][c] = y0;
+          if (w == 0) {
+            Y[c1][c] = y1, Y[c2][c] = y2;
+          } else {
+            Y[c1][c] += y1, Y[c2][c] += y2;
+          }
+        } else {
+          h[w][c] = h2;
+        }
+        X[c0][c] = -(h0 + h1);
+        if (w == 0) {
+          X[c1][c] = h0, X[c2][c] = h1;
+        } else {
+          X[c1][c] += h0, X[c2][c] += h1;
+        }
       }
     }
+    if constexpr (HG) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T x = SX[q][c], h = SH[q][c];
-        accb[q][c] = x - h, acct[q][c] = x + h;
-      }
+        for (int c = 0; c < 3; ++c) accb[q][c] = X[q][c] - Y[q][c], acct[q][c] = X[q][c] + Y[q][c];
+    } else {
+      combine_corners<T, 3>(X, h, accb, acct);
+    }
   }
 };
 
@@ -195,31 +294,36 @@ template <typename T>
 struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
   static constexpr bool USES_ETA = false, LOADS = true;
+  using Col = NoCol;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2]) const { return Col{}; }
   __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
-                                       T (&acct)[4][1]) const {
-    const T r = lc[4], vw = lc[6];
+                                       T (&acct)[4][1], const Col&) const {
+    const T r = lc[4], vw6 = lc[7];
     T s[4][3], dd[4][3];
-    T(&Q)[4][1] = accb;  // zero on entry
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
+    T v[2];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
       const T* M = Mi[w];
-      T tr = 0;
+      T lat = 0, rad = 0;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = ((dd[c0][c] + dd[c1][c]) + dd[c2][c]) * r;
-        tr += ax * M[c] + ay * M[3 + c] + az * M[6 + c];
+        const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = (dd[c0][c] + dd[c1][c]) + dd[c2][c];
+        lat = c == 0 ? ax * M[0] + ay * M[3] : lat + ax * M[c] + ay * M[3 + c];
+        rad = c == 0 ? az * M[6] : rad + az * M[6 + c];
       }
-      const T v = -(vw * dM[w]) * tr * (T)(1.0 / 6.0);
-      Q[c0][0] += v, Q[c1][0] += v, Q[c2][0] += v;
+      v[w] = (vw6 * dM[w]) * (lat + r * rad);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acct[q][0] = accb[q][0];
+    const T v01 = v[0] + v[1];
+    accb[0][0] = acct[0][0] = v[0];
+    accb[3][0] = acct[3][0] = v[1];
+    accb[1][0] = acct[1][0] = v01;
+    accb[2][0] = acct[2][0] = v01;
   }
 };
 
@@ -229,57 +333,74 @@ template <typename T>
 struct OpGrad {
   static constexpr int NIN = 1, NOUT = 3;
   static constexpr bool USES_ETA = false, LOADS = true;
+  using Col = NoCol;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2]) const { return Col{}; }
   __device__ __forceinline__ void cell(const T (&ub)[4][1], const T (&ut)[4][1], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][3],
-                                       T (&acct)[4][3]) const {
-    const T r = lc[4], vw = lc[6];
-    T(&SX)[4][3] = accb;  // zero on entry; per-corner sums of X and H[:,2]
-    T(&SH)[4][3] = acct;
+                                       T (&acct)[4][3], const Col&) const {
+    const T r = lc[4], vw6 = lc[7];
     T s[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) s[q] = ub[q][0] + ut[q][0];
+    T X[4][3], h[2][3];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
       const T* M = Mi[w];
-      const T f = -(vw * dM[w]) * (((s[c0] + s[c1]) + s[c2]) * (T)(1.0 / 6.0));
+      const T f = (vw6 * dM[w]) * ((s[c0] + s[c1]) + s[c2]);
+      const T fr = f * r;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const T h0 = f * M[c], h1 = f * M[3 + c], h2 = (f * r) * M[6 + c];
-        SX[c0][c] -= h0 + h1;
-        SX[c1][c] += h0;
-        SX[c2][c] += h1;
-        SH[c0][c] += h2;
-        SH[c1][c] += h2;
-        SH[c2][c] += h2;
+        const T h0 = f * M[c], h1 = f * M[3 + c];
+        h[w][c] = fr * M[6 + c];
+        X[c0][c] = -(h0 + h1);
+        if (w == 0) {
+          X[c1][c] = h0, X[c2][c] = h1;
+        } else {
+          X[c1][c] += h0, X[c2][c] += h1;
+        }
       }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T x = SX[q][c], h = SH[q][c];
-        accb[q][c] = x - h, acct[q][c] = x + h;
-      }
+    combine_corners<T, 3>(X, h, accb, acct);
   }
 };
 
 // Diagonal of A (no input): node j of a wedge receives V eta (|g_j|^2 + c g_j[d]^2) for each
 // component d, g_j = grad N_j(q_c) = w0 (xi_a M^-1[0,:] + eta_a M^-1[1,:]) -/+ w1 M^-1[2,:]
 // (bottom / top), c = 1/3 with the -2/3 div term, 1 without (A_jj = V eta (|g|^2 I + c g g^T)).
-template <typename T>
+template <typename T, bool HG = false>
 struct OpDiag {
   static constexpr int NIN = 1, NOUT = 3;
   static constexpr bool USES_ETA = true, LOADS = false;
+  using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
+  T hgk;
+  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2]) const {
+    if constexpr (HG) return hg_column(Mi, dM);
+    else return Col{};
+  }
+  // With HG, node (a, side) of a wedge also gets eps (g_1,j^2 + g_2,j^2) in every component:
+  // g_m,j = zeta_j (xi_a or eta_a - 1/3) - k9 (...), which is eps n_a (k9 - zeta / 3)^2 with
+  // n_a = 2, 5, 5 for a = 0, 1, 2 (zeta = -1 bottom, +1 top).
   __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&Mi)[2][9], const T (&dM)[2],
-                                       const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3]) const {
+                                       const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3],
+                                       const Col& col) const {
     const T w0 = lc[0], w1 = lc[1], vol = lc[2];
     const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) accb[q][c] = acct[q][c] = 0;
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       const T* M = Mi[w];
       const T ve = vol * dM[w] * eta[w];
+      T hb = 0, ht = 0;  // eps (k9 + 1/3)^2 and eps (k9 - 1/3)^2
+      if constexpr (HG) {
+        const T eps = (hgk * eta[w]) * (lc[5] * col.eL[w] + lc[9] * col.eR[w]);
+        const T kb = lc[8] + (T)(1.0 / 3.0), kt = lc[8] - (T)(1.0 / 3.0);
+        hb = eps * (kb * kb), ht = eps * (kt * kt);
+      }
       T lat[3][3], u2[3];
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
@@ -296,9 +417,12 @@ struct OpDiag {
 #pragma unroll
           for (int x = 0; x < 3; ++x) g[x] = side == 0 ? lat[a][x] - u2[x] : lat[a][x] + u2[x];
           const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          T hs = 0;
+          if constexpr (HG) hs = (a == 0 ? (T)2 : (T)5) * (side == 0 ? hb : ht);
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const T v = ve * (g2 + third * (g[c] * g[c]));
+            T v = ve * (g2 + third * (g[c] * g[c]));
+            if constexpr (HG) v += hs;
             if (side == 0) accb[q][c] += v;
             else acct[q][c] += v;
           }
@@ -400,6 +524,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
       if (EK != TN_ETA_F32 && Op::USES_ETA) dM[w] *= eta.cs[t0 + w];
     }
   }
+  const typename Op::Col col = op.column(Mi, dM);
   // viscosity of the cell's two wedges at layer k: pair k N^2 2 + {0, 1} past the column base
   const int eta_c0 = (((d * (n_r - 1)) * N + ci0) * N + cj0) * 2;
   const int eta_ls = N * N * 2;
@@ -515,12 +640,13 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   load_level(kstart, ub);
   for (int k = kstart; k < kc1; ++k) {
     load_level(k + 1, ut);
-    T accb[4][NOUT], acct[4][NOUT];
+    T accb[4][NOUT], acct[4][NOUT];  // assigned by the op (zero for a halo cell outside the diamond)
+    if (!cell_ok) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
-    if (cell_ok) {
+        for (int c = 0; c < NOUT; ++c) accb[q][c] = acct[q][c] = 0;
+    } else {
       T e[2] = {(T)1, (T)1};
       if (Op::USES_ETA) {
         const int o = eta_c0 + k * eta_ls;  // even: the pair is one aligned vector load
@@ -537,7 +663,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
           e[0] = (T)from16<EK>((uint16_t)(p & 0xffffu)), e[1] = (T)from16<EK>((uint16_t)(p >> 16));
         }
       }
-      op.cell(ub, ut, Mi, dM, lay + kLayerStride * k, e, accb, acct);
+      op.cell(ub, ut, Mi, dM, lay + kLayerStride * k, e, accb, acct, col);
     }
     if (k >= kc0) {
 #pragma unroll
@@ -689,9 +815,25 @@ __global__ void k_interface_epi(Dims D, int n_groups, const int* __restrict__ gp
 // -2/3 g g^T, the symmetric-gradient term g g^T, so 1/3 with div_term, 1 without).
 // Only the two boundary node layers are handled here (the tile kernel with OpDiag writes the
 // interior layers): blocks = 10 * 2 * (N+1)^2 threads, layer 0 and layer n_r - 1.
+// Hourglass-control part of the node block of wedge-local lateral node a (side 0: the node is on
+// the wedge's bottom layer): eps n_a (k9 - zeta / 3)^2 times the identity (see OpDiag).
+template <typename T>
+__device__ __forceinline__ T hg_node_diag(const T (&Mi)[9], T dM, T et, const T* lc, T hgk, int a, int side) {
+  T l = 0, q = 0;
+  for (int x = 0; x < 3; ++x) {
+    const T s01 = Mi[x] + Mi[3 + x];
+    l += s01 * s01 + Mi[x] * Mi[x] + Mi[3 + x] * Mi[3 + x];
+    q += Mi[6 + x] * Mi[6 + x];
+  }
+  const T eps = (hgk * et) * (lc[5] * ((T)2 * dM * l) + lc[9] * ((T)6 * dM * q));
+  const T kz = side == 0 ? lc[8] + (T)(1.0 / 3.0) : lc[8] - (T)(1.0 / 3.0);
+  return eps * (a == 0 ? (T)2 : (T)5) * (kz * kz);
+}
+
 template <typename T>
 __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
-                         const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* d0, T* d1, T* d2) {
+                         const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, T* d0, T* d1,
+                         T* d2) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)10 * 2 * M * M;
@@ -719,7 +861,9 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
-      const T ve = vol * dM * eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
+      const T et = eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
+      const T ve = vol * dM * et;
+      if (hgk > (T)0) alpha += hg_node_diag(Mi, dM, et, lay + kLayerStride * kk, hgk, a, side);
       const T g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
       alpha += ve * g2;
       const T tv = ve * third;
@@ -765,8 +909,8 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
 // P A_partial P per diamond and the identity part is added once by k_interface_block.
 template <typename T>
 __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
-                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T* b0, T* b1, T* b2, T* b3,
-                          T* b4, T* b5) {
+                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, T* b0, T* b1,
+                          T* b2, T* b3, T* b4, T* b5) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)10 * D.n_r * M * M;
@@ -792,7 +936,9 @@ __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict
       const T gz = side == 0 ? (T)-1 : (T)1;
       T g[3];
       for (int x = 0; x < 3; ++x) g[x] = Mi[x] * (w0 * gxi[a]) + Mi[3 + x] * (w0 * geta[a]) + Mi[6 + x] * (w1 * gz);
-      const T ve = vol * dM * eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
+      const T et = eta_at(eta, ((((int64_t)d * (D.n_r - 1) + kk) * N + ci) * N + cj) * 2 + w, t);
+      const T ve = vol * dM * et;
+      if (hgk > (T)0) alpha += hg_node_diag(Mi, dM, et, lay + kLayerStride * kk, hgk, a, side);
       alpha += ve * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
       const T tv = ve * third;
       B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
@@ -1023,6 +1169,7 @@ __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T
 
 // ------------------------------------------------------------------------------------ viscosity
 // lay[kLayerStride k + 3] holds the layer mid-radius (r_k + r_k+1) / 2.
+#if TN_PART == 0 || TN_PART == 1
 __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, double jump_r, double jump_f,
                              const double* __restrict__ lay, double* eta) {
   const int N = D.N;
@@ -1113,32 +1260,53 @@ __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double*
   f0[idx] = f[0], f1[idx] = f[1], f2[idx] = f[2];
 }
 
+#endif  // TN_PART == 0 || TN_PART == 1
+
 inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------------------- launchers
+// kappa (3 + c) / 18 of the hourglass control (c = 1/3 with the div term, 1 without).
+inline double hg_coef(const Level& L, int div_term) {
+  return L.hg_kappa * (3.0 + (div_term ? 1.0 / 3.0 : 1.0)) / 18.0;
+}
+
+template <typename T, bool HG>
+cudaError_t apply_A_hg(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
+                       const int* skip) {
+  OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
+  return launch_tile<T, OpA<T, HG>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, etav<T>(L), st, skip);
+}
+
 template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                            const int* skip) {
-  OpA<T> op{div_term};
-  cudaError_t e = launch_tile<T, OpA<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, etav<T>(L), st, skip);
+  cudaError_t e = L.hg_kappa > 0 ? apply_A_hg<T, true>(L, bc, div_term, u, y, st, skip)
+                                 : apply_A_hg<T, false>(L, bc, div_term, u, y, st, skip);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 1, y, u, st, skip);
+}
+
+template <typename T, bool HG>
+cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
+                           T* const* t, cudaStream_t st, const int* skip) {
+  OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
+  using Op = OpA<T, HG>;
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  switch (epi) {
+    case EPI_RESID: return launch_tile<T, Op, F, EPI_RESID>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    case EPI_CHEB1: return launch_tile<T, Op, F, EPI_CHEB1>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    case EPI_CHEB2: return launch_tile<T, Op, F, EPI_CHEB2>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
 cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
                                T* const* t, cudaStream_t st, const int* skip) {
-  OpA<T> op{div_term};
-  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
-  cudaError_t e;
-  switch (epi) {
-    case EPI_RESID: e = launch_tile<T, OpA<T>, F, EPI_RESID>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
-    case EPI_CHEB1: e = launch_tile<T, OpA<T>, F, EPI_CHEB1>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
-    case EPI_CHEB2: e = launch_tile<T, OpA<T>, F, EPI_CHEB2>(L, bc, op, in, t, etav<T>(L), st, skip, &E); break;
-    default: return cudaErrorInvalidValue;
-  }
+  cudaError_t e = L.hg_kappa > 0 ? apply_A_epi_hg<T, true>(L, bc, div_term, epi, in, E, t, st, skip)
+                                 : apply_A_epi_hg<T, false>(L, bc, div_term, epi, in, E, t, st, skip);
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)L.n_groups * L.n_r;
   if (n == 0) return cudaSuccess;
@@ -1154,6 +1322,7 @@ cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, con
   return cudaGetLastError();
 }
 
+#if TN_PART == 0 || TN_PART == 1
 template <typename T>
 cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st) {
   T* out[1] = {q};
@@ -1174,13 +1343,16 @@ template <typename T>
 cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cudaStream_t st) {
   Dims D = dims(L);
   // interior layers: per-cell tile kernel (boundary layers are overwritten below)
-  OpDiag<T> op{div_term};
   const T* none[1] = {d[0]};
-  cudaError_t e = launch_tile<T, OpDiag<T>, 0>(L, bc, op, none, d, etav<T>(L), st);
+  const T hgk = (T)hg_coef(L, div_term);
+  cudaError_t e = L.hg_kappa > 0
+                      ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk}, none, d, etav<T>(L), st)
+                      : launch_tile<T, OpDiag<T, false>, 0>(L, bc, OpDiag<T, false>{div_term, hgk}, none, d, etav<T>(L),
+                                                            st);
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
   k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
-                                            bc.out, div_term, d[0], d[1], d[2]);
+                                            bc.out, div_term, hgk, d[0], d[1], d[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 2, d, nullptr, st);
@@ -1191,7 +1363,8 @@ cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b,
   Dims D = dims(L);
   const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
   k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
-                                             bc.out, div_term, b[0], b[1], b[2], b[3], b[4], b[5]);
+                                             bc.out, div_term, (T)hg_coef(L, div_term), b[0], b[1], b[2], b[3], b[4],
+                                             b[5]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t ng = (int64_t)L.n_groups * L.n_r;
@@ -1321,11 +1494,7 @@ cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, d
 }
 
 #define TN_INST(T)                                                                                               \
-  template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t,       \
-                                         const int*);                                                            \
   template cudaError_t launch_div_fine<T>(const Level&, BC, const T* const*, T*, cudaStream_t);                 \
-  template cudaError_t launch_apply_A_epi<T>(const Level&, BC, int, int, const T* const*, const EpiArgs<T>&,     \
-                                             T* const*, cudaStream_t, const int*);                              \
   template cudaError_t launch_grad_fine<T>(const Level&, BC, const T*, T* const*, cudaStream_t);                \
   template cudaError_t launch_diag_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                        \
   template cudaError_t launch_block_inv_A<T>(const Level&, BC, int, T* const*, cudaStream_t);                   \
@@ -1339,5 +1508,19 @@ cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, d
 TN_INST(double)
 TN_INST(float)
 #undef TN_INST
+#endif  // TN_PART == 0 || TN_PART == 1
+
+#define TN_INST_A(T)                                                                                             \
+  template cudaError_t launch_apply_A<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t,       \
+                                         const int*);                                                            \
+  template cudaError_t launch_apply_A_epi<T>(const Level&, BC, int, int, const T* const*, const EpiArgs<T>&,     \
+                                             T* const*, cudaStream_t, const int*);
+#if TN_PART == 0 || TN_PART == 2
+TN_INST_A(double)
+#endif
+#if TN_PART == 0 || TN_PART == 3
+TN_INST_A(float)
+#endif
+#undef TN_INST_A
 
 }  // namespace tn

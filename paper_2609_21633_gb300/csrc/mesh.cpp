@@ -136,8 +136,8 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
           if (!(det > 0.0)) err = "degenerate or inverted lateral triangle";
         }
 
-  // ---- per radial cell: (w0, w1, vol, rho, w1 / w0, vol w0^2, vol w0, 0) with w0 = 1/(2 rho),
-  // w1 = 1/(6 h), vol = rho^2 h
+  // ---- per radial cell: (w0, w1, vol, rho, w1 / w0, vol w0^2, vol w0, -vol w0 / 6,
+  // w0 / (9 w1), vol w1^2, 0, 0) with w0 = 1/(2 rho), w1 = 1/(6 h), vol = rho^2 h
   lay.assign((size_t)kLayerStride * (n_r - 1), 0.0);
   for (int k = 0; k + 1 < n_r; ++k) {
     double rho = 0.5 * (L.radii[k] + L.radii[k + 1]);
@@ -150,6 +150,9 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
     t[4] = t[1] / t[0];
     t[5] = t[2] * t[0] * t[0];
     t[6] = t[2] * t[0];
+    t[7] = -t[6] / 6.0;
+    t[8] = t[0] / (9.0 * t[1]);
+    t[9] = t[2] * t[1] * t[1];
   }
 
   // ---- lateral unit vectors in the padded lateral layout

@@ -34,9 +34,11 @@ def tn():
 class Case:
     """One mesh on both sides with random fields (seeded)."""
 
-    def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0, eta_storage=0):
+    def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0, eta_storage=0,
+                 hg_kappa=0.0):
         self.tn = tn
-        self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term, eta_storage=eta_storage)
+        self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term, eta_storage=eta_storage,
+                                   hg_kappa=hg_kappa)
         self.info = tn.tn_mesh_info(self.m, 0)
         self.om = ShellMesh(level, n_r, r_in, r_out)
         self.map = LayoutMap(self.info, self.om)
@@ -113,6 +115,28 @@ def test_apply_A_f32(tn):
     tn.tn_apply_A(c.m, 0, [c.dev(u[i], torch.float32) for i in range(3)], y)
     got = np.stack([c.host(t) for t in y])
     assert max_rel(got, want) <= TOL32
+    c.close()
+
+
+@pytest.mark.parametrize("level,n_r,bc,div_term", [(3, 9, "noslip/free", True), (4, 17, "free/free", True),
+                                                  (4, 9, "free/free", False)])
+def test_hourglass_control_apply_and_diag(tn, level, n_r, bc, div_term):
+    """Eq. (hgstab) with kappa = 0.3: FP64 apply and diagonal at the FP64 bar, FP32 apply at the
+    FP32 bar, against the oracle's explicit element matrices with Flanagan-Belytschko vectors."""
+    kappa = 0.3
+    c = Case(tn, level, n_r, BCS[bc], div_term=div_term, hg_kappa=kappa)
+    u = c.vec(21)
+    want = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=div_term, kappa=kappa)
+    plain = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=div_term)
+    assert max_rel(plain, want) > 1e-3  # the control changes the result
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        y = c.zeros(dtype=dtype)
+        tn.tn_apply_A(c.m, 0, [c.dev(u[i], dtype) for i in range(3)], y)
+        assert max_rel(np.stack([c.host(t) for t in y]), want) <= tol, dtype
+    d = c.zeros()
+    tn.tn_diag_A(c.m, 0, d)
+    want_d = O.diag_A_constrained(c.om, c.eta, c.P, div_term=div_term, kappa=kappa)
+    assert max_rel(np.stack([c.host(t) for t in d]), want_d) <= TOL64
     c.close()
 
 

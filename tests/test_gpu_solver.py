@@ -33,13 +33,15 @@ def from_dev(mp, ts):
     return np.stack([mp.from_layout(t.double().cpu().numpy()) for t in ts])
 
 
-@pytest.mark.parametrize("level,n_r,bc", [(3, 9, (1, 0)), (3, 9, (0, 0)), (4, 9, (0, 0)),
-                                         (2, 17, (0, 0)), (4, 5, (1, 0))])
-def test_vcycle_f64_matches_oracle(tn, level, n_r, bc):
-    """Includes semi-coarsened hierarchies: (2, 17) coarsens radially first, (4, 5) laterally."""
+@pytest.mark.parametrize("level,n_r,bc,kappa", [(3, 9, (1, 0), 0.0), (3, 9, (0, 0), 0.0), (4, 9, (0, 0), 0.0),
+                                               (2, 17, (0, 0), 0.0), (4, 5, (1, 0), 0.0), (3, 9, (1, 0), 0.3),
+                                               (4, 5, (0, 0), 0.3)])
+def test_vcycle_f64_matches_oracle(tn, level, n_r, bc, kappa):
+    """Includes semi-coarsened hierarchies: (2, 17) coarsens radially first, (4, 5) laterally;
+    kappa > 0: hourglass control (Eq. hgstab) on every level."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     eta = inputs.lognormal_viscosity(om.n_wedges, 3, 0.5)
-    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, bc[0], bc[1])
+    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, bc[0], bc[1], hg_kappa=kappa)
     mp = LayoutMap(tn.tn_mesh_info(m, 0), om)
     tn.tn_set_viscosity(m, torch.tensor(mp.wedges_to_layout(eta), device="cuda"))
     # a fixed coarse-CG iteration count keeps the comparison away from a stopping-test tie
@@ -47,7 +49,7 @@ def test_vcycle_f64_matches_oracle(tn, level, n_r, bc):
     v0 = inputs.normal((3, om.n_nodes), 4)
     tn.tn_mg_setup(m, torch.float64, opts, to_dev(mp, v0))
     H = Hierarchy(level, n_r, 0.55, 1.0, eta, bc=(ORACLE_BC[bc[0]], ORACLE_BC[bc[1]]), coarse_rtol=0.0,
-                  coarse_max_iters=20)
+                  coarse_max_iters=20, kappa=kappa)
     H.setup(v0.ravel())
     for h in range(H.nlev - 1):
         assert abs(tn.tn_mg_lambda(m, torch.float64, h) / H.lam[h] - 1) < 1e-12
@@ -76,11 +78,11 @@ def test_vcycle_f32_close_to_f64(tn):
     tn.tn_mesh_destroy(m)
 
 
-def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0):
+def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0):
     """Spherical benchmark-like solve: T of the A-series shape, eta = exp(ln 10 (1/2 - T)), Ra = 7e3."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     T = inputs.temperature(om.node_xyz(), 0.55, 1.0)
-    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, eta_storage=eta_storage)
+    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, eta_storage=eta_storage, hg_kappa=kappa)
     info = tn.tn_mesh_info(m, 0)
     mp = LayoutMap(info, om)
     Td = torch.tensor(mp.to_layout(T), device="cuda")
@@ -91,7 +93,7 @@ def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0):
     u = [torch.zeros_like(f[0]) for _ in range(3)]
     p = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
     stats = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(rtol=rtol, mode=mode))
-    S = StokesSystem(om, viscosity(om, T, np.log(10.0)))
+    S = StokesSystem(om, viscosity(om, T, np.log(10.0)), kappa=kappa)
     b = S.rhs(T, 7e3)
     pm = LayoutMap(pinfo, S.pmesh)
     ug = from_dev(mp, u)
@@ -100,11 +102,12 @@ def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0):
     return stats, S, b, ug, pg, om
 
 
-@pytest.mark.parametrize("mode,eta_storage", [(0, 0), (1, 0), (1, 1), (1, 2)])
-def test_stokes_solve_reaches_1e8_by_the_oracle(tn, mode, eta_storage):
+@pytest.mark.parametrize("mode,eta_storage,kappa", [(0, 0, 0.0), (1, 0, 0.0), (1, 1, 0.0), (1, 2, 0.0), (0, 0, 0.3),
+                                                    (1, 1, 0.3)])
+def test_stokes_solve_reaches_1e8_by_the_oracle(tn, mode, eta_storage, kappa):
     # mixed mode with 16-bit viscosity in the FP32 inner solve: the FP64 refinement still meets
-    # 1e-8 on the FP64 system
-    stats, S, b, ug, pg, om = config0(tn, mode=mode, eta_storage=eta_storage)
+    # 1e-8 on the FP64 system; kappa > 0: the hourglass-controlled system (Eq. hgstab)
+    stats, S, b, ug, pg, om = config0(tn, mode=mode, eta_storage=eta_storage, kappa=kappa)
     res = S.residual(b, ug, pg)
     print(f"mode {mode}: {stats}, oracle residual {res:.3e}")
     assert stats["converged"] == 1

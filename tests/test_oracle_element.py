@@ -2,8 +2,8 @@
 import numpy as np
 import pytest
 
-from oracle.element import (GHAT, QC, basis, basis_ref_gradients, geometry, hourglass_vectors,
-                            viscous_element_matrix)
+from oracle.element import (GHAT, QC, basis, basis_ref_gradients, geometry, hourglass_base_vectors,
+                            hourglass_stabilised, hourglass_vectors, viscous_element_matrix)
 from oracle.mesh import ShellMesh
 
 REF_NODES = [(0.0, 0.0, -1.0), (1.0, 0.0, -1.0), (0.0, 1.0, -1.0),
@@ -129,3 +129,60 @@ def test_diagonal_closed_form():
                 g = grad[e, j]
                 want = V[e] * eta[e] * (g @ g + g[d] ** 2 / 3.0)
                 assert abs(A[e, 3 * j + d, 3 * j + d] - want) <= 1e-13 * abs(want)
+
+
+def _linear_fields(xe):
+    """Nodal values (6, 3) of the 12 physical linear fields u_d = x_c (and the 3 constants)."""
+    out = []
+    for d in range(3):
+        t = np.zeros((6, 3)); t[:, d] = 1.0
+        out.append(t)
+        for c in range(3):
+            v = np.zeros((6, 3)); v[:, d] = xe[:, c]
+            out.append(v)
+    return out
+
+
+def test_hourglass_base_vectors():
+    """Eq. (hgstab) with Flanagan-Belytschko base vectors: g_m is orthogonal to every physical
+    linear field and to the constants, and keeps the hourglass part: g_m . w_m' = w_m . w_m' on
+    the reference-linear part's complement (g - w is a combination of gradient columns)."""
+    x, _ = random_wedges()
+    _, _, grad, _ = geometry(x)
+    g = hourglass_base_vectors(x, grad)
+    w = hourglass_vectors()
+    for e in range(x.shape[0]):
+        for m in range(2):
+            assert abs(g[e, m].sum()) <= 1e-14
+            for c in range(3):
+                assert abs(g[e, m] @ x[e, :, c]) <= 1e-14
+            # g_m - w_m lies in the span of the gradient columns dN/dx_c
+            coef, *_ = np.linalg.lstsq(grad[e], g[e, m] - w[m], rcond=None)
+            np.testing.assert_allclose(grad[e] @ coef, g[e, m] - w[m], atol=1e-13)
+
+
+def test_stabilised_element_matrix():
+    """A_e + eps sum (g_m x e_d)(g_m x e_d)^T: symmetric, rank 11 (5 + 6: every hourglass mode
+    now has energy), equal to A_e on all linear fields, eps = kappa tr(A_e) / 18, and the added
+    energy of the unit reference hourglass mode w_m x e_d is eps sum_m' (g_m' . w_m)^2."""
+    x, eta = random_wedges()
+    _, _, grad, V = geometry(x)
+    A = viscous_element_matrix(grad, V, eta)
+    g = hourglass_base_vectors(x, grad)
+    kappa = 0.25
+    As = hourglass_stabilised(A, g, kappa)
+    w = hourglass_vectors()
+    for e in range(x.shape[0]):
+        scale = np.abs(As[e]).max()
+        np.testing.assert_array_equal(As[e], As[e].T)
+        assert np.linalg.matrix_rank(As[e], tol=1e-10 * scale) == 11
+        assert np.linalg.eigvalsh(As[e]).min() >= -1e-12 * scale
+        for u in _linear_fields(x[e]):
+            np.testing.assert_allclose(As[e] @ u.ravel(), A[e] @ u.ravel(), atol=1e-13 * scale)
+        eps = kappa * np.trace(A[e]) / 18.0
+        for m in range(2):
+            for d in range(3):
+                v = np.zeros((6, 3)); v[:, d] = w[m]
+                got = v.ravel() @ (As[e] - A[e]) @ v.ravel()
+                want = eps * sum((g[e, mm] @ w[m]) ** 2 for mm in range(2))
+                assert abs(got - want) <= 1e-12 * abs(want)
