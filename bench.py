@@ -36,6 +36,8 @@ A_FLOPS_PER_CELL = 400.0
 # DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 164.5 MB for
 # 2,621,440 cells), scaled to the bench size by cells; None once the kernel changes.
 A_TRAFFIC_BYTES_PER_CELL = None
+# Hourglass-control coefficient of the solves and the serving stream that use it.
+HG_KAPPA = 0.3
 # Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
 # restriction, interface), B^T 3 (prolongation, tile, interface), diag 3 (tile, boundary-layer
 # gather, interface).
@@ -234,10 +236,11 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=
         tn.tn_mesh_destroy(m)
 
 
-def serving_stream(tn, n_req=256, seed=0, load=0.7):
+def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1):
     """Serving workload: seeded Stokes requests (lateral level U{3..6}, radial layers U{9,17,33,65},
     viscosity contrast log-uniform in [1, 1e4], temperature perturbation degree U{2..8}, order
-    U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), FP32 inner solves with FP64 refinement to 1e-8.
+    U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), FP32 inner solves with FP64 refinement to 1e-8,
+    hourglass control kappa = hg_kappa, FP32-path viscosity storage eta_storage (1 = BF16).
     Phase 1 submits all requests at once (saturated throughput); phase 2 submits them with
     Poisson arrivals at `load` x the saturated rate and reports latency percentiles."""
     rng = np.random.default_rng(seed)
@@ -251,7 +254,7 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7):
         amp = float(rng.uniform(0.01, 0.05))
         reqs.append(dict(lateral_level=l, radial_layers=nr, E=math.log(contrast), Ra=7e3, t_degree=deg,
                          t_order=order, t_amplitude=amp))
-    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4))
+    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4, hg_kappa=hg_kappa, eta_storage=eta_storage))
     try:
         tickets = [tn.tn_server_submit(srv, **q) for q in reqs]
         res = [tn.tn_server_wait(srv, t) for t in tickets]
@@ -278,7 +281,8 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7):
                 "poisson_rate_per_s": rate, "solves_per_s": n_req / span, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "converged": ok,
                 "max_rel_residual": max(r["rel_residual"] for r in res), "median_iterations": float(np.median(its)),
-                "max_active": 4, "mode": "FP32 inner + FP64 refinement, rtol 1e-8"}
+                "max_active": 4, "mode": "FP32 inner + FP64 refinement, rtol 1e-8",
+                "hg_kappa": hg_kappa, "eta_storage": ["f32", "bf16", "f16"][eta_storage]}
     finally:
         tn.tn_server_destroy(srv)
 
@@ -440,12 +444,22 @@ def main():
                 for r, sx in ((rmx, smx), (rbf, sbf)):  # solution difference against the FP64 solve
                     r["u_rel_diff_vs_fp64"] = float(np.linalg.norm(sx[0] - s64[0]) / np.linalg.norm(s64[0]))
                     r["p_rel_diff_vs_fp64"] = float(np.linalg.norm(sx[1] - s64[1]) / np.linalg.norm(s64[1]))
+                # the hourglass-controlled system (Eq. hgstab, kappa = 0.3): FP64 and mixed
+                h64, t64 = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64, hg_kappa=HG_KAPPA)
+                hbf, tbf = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED, eta_storage=tn.TN_ETA_BF16,
+                                      hg_kappa=HG_KAPPA)
+                hbf["u_rel_diff_vs_fp64"] = float(np.linalg.norm(tbf[0] - t64[0]) / np.linalg.norm(t64[0]))
+                hbf["p_rel_diff_vs_fp64"] = float(np.linalg.norm(tbf[1] - t64[1]) / np.linalg.norm(t64[1]))
+                # discretisation change of the control: its FP64 solution against the plain one
+                h64["u_rel_diff_vs_plain"] = float(np.linalg.norm(t64[0] - s64[0]) / np.linalg.norm(s64[0]))
                 solves[name] = {"fp64": r64, "mixed": rmx, "mixed_bf16_eta": rbf,
                                 "mixed_speedup": r64["seconds"] / rmx["seconds"],
-                                "mixed_bf16_eta_speedup": r64["seconds"] / rbf["seconds"]}
+                                "mixed_bf16_eta_speedup": r64["seconds"] / rbf["seconds"],
+                                "hg%.1f_fp64" % HG_KAPPA: h64, "hg%.1f_mixed_bf16_eta" % HG_KAPPA: hbf,
+                                "hg_mixed_bf16_eta_speedup_vs_plain_fp64": r64["seconds"] / hbf["seconds"]}
             line["solves"] = solves
             if args.serve_requests > 0:
-                line["serving"] = serving_stream(tn, args.serve_requests, args.seed)
+                line["serving"] = serving_stream(tn, args.serve_requests, args.seed, hg_kappa=HG_KAPPA)
         if world == 1:
             dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
             line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

@@ -316,6 +316,8 @@ typedef struct {
   int mode;                /* tn_solve_mode of every solve (TN_SOLVE_MIXED) */
   double rtol;             /* 1e-8 */
   int keep_solutions;      /* 1: keep a host copy of every solution for tn_server_solution (0) */
+  int eta_storage;         /* tn_mesh_opts.eta_storage of every request's mesh (TN_ETA_F32) */
+  double hg_kappa;         /* tn_mesh_opts.hg_kappa of every request's mesh (0: the plain one-point A) */
 } tn_server_opts;
 typedef struct {
   int lateral_level, radial_layers;

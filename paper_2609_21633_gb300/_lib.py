@@ -64,7 +64,8 @@ TN_SOLVE_F64, TN_SOLVE_MIXED = 0, 1
 
 class tn_server_opts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("mode", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("keep_solutions", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("keep_solutions", ctypes.c_int), ("eta_storage", ctypes.c_int),
+                ("hg_kappa", ctypes.c_double)]
 
 
 class tn_request(ctypes.Structure):

@@ -43,7 +43,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32};
+                  L.rad32, L.dcoef64, L.dcoef32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -195,6 +195,10 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
     m->lv.emplace_back();
     tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage);
     m->lv.back().hg_kappa = o.hg_kappa;
+    if (s == TN_OK) {
+      cudaError_t ce = launch_diag_coef(m->lv.back(), m->div_term);
+      if (ce != cudaSuccess) s = cuda_fail(ce, "tn_mesh_create: diagonal factors");
+    }
     if (s != TN_OK) {
       std::string msg = tn_last_error();
       tn_mesh_destroy(m);

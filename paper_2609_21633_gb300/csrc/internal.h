@@ -51,6 +51,10 @@ struct Level {
   int eta_kind = TN_ETA_F32;
   // Hourglass control of the A block (0: off): eps_e = hg_kappa tr(A_e) / 18.
   double hg_kappa = 0;
+  // Per-triangle factors of the diagonal of A ([24][n_tri], see OpDiag), for div term dcoef_div.
+  double* dcoef64 = nullptr;
+  float* dcoef32 = nullptr;
+  int dcoef_div = -1;
   uint16_t* eta16 = nullptr;
   float* eta_cs = nullptr;
   // Scratch scalar field in this level's node layout (B / B^T intermediate).
@@ -161,6 +165,9 @@ cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double 
                               cudaStream_t st);
 cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st);
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
+// Per-triangle factors of diag(A) for the level's geometry and div term (allocates on first
+// use; synchronous).
+cudaError_t launch_diag_coef(Level& L, int div_term);
 // The FP32 path's viscosity from eta64: eta32, or eta16 and the column factors (see Level).
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st);
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);

@@ -79,6 +79,7 @@ struct Tab<double> {
   static const double* lay(const Level& L) { return L.lay64; }
   static const double* s(const Level& L) { return L.s64; }
   static const double* gs(const Level& L) { return L.grp_s64; }
+  static const double* dcoef(const Level& L) { return L.dcoef64; }
 };
 template <>
 struct Tab<float> {
@@ -86,6 +87,7 @@ struct Tab<float> {
   static const float* lay(const Level& L) { return L.lay32; }
   static const float* s(const Level& L) { return L.s32; }
   static const float* gs(const Level& L) { return L.grp_s32; }
+  static const float* dcoef(const Level& L) { return L.dcoef32; }
 };
 
 // Per-wedge viscosity as a kernel reads it: v[w] (kind TN_ETA_F32, and always for FP64), or
@@ -200,7 +202,7 @@ struct OpA {
   using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
   T hgk;  // kappa (3 + c) / 18 (HG only)
-  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2]) const {
+  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2], int) const {
     if constexpr (HG) return hg_column(Mi, dM);
     else return Col{};
   }
@@ -295,7 +297,7 @@ struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
   static constexpr bool USES_ETA = false, LOADS = true;
   using Col = NoCol;
-  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2]) const { return Col{}; }
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
   __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
                                        T (&acct)[4][1], const Col&) const {
@@ -334,7 +336,7 @@ struct OpGrad {
   static constexpr int NIN = 1, NOUT = 3;
   static constexpr bool USES_ETA = false, LOADS = true;
   using Col = NoCol;
-  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2]) const { return Col{}; }
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
   __device__ __forceinline__ void cell(const T (&ub)[4][1], const T (&ut)[4][1], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][3],
                                        T (&acct)[4][3], const Col&) const {
@@ -366,22 +368,87 @@ struct OpGrad {
 };
 
 // Diagonal of A (no input): node j of a wedge receives V eta (|g_j|^2 + c g_j[d]^2) for each
-// component d, g_j = grad N_j(q_c) = w0 (xi_a M^-1[0,:] + eta_a M^-1[1,:]) -/+ w1 M^-1[2,:]
-// (bottom / top), c = 1/3 with the -2/3 div term, 1 without (A_jj = V eta (|g|^2 I + c g g^T)).
+// component d, g_j = grad N_j(q_c) = w0 (l_a -/+ r m2) (bottom / top), with m_k the rows of M^-1,
+// l_0 = -(m0 + m1), l_1 = m0, l_2 = m1, r = w1 / w0, and c = 1/3 with the -2/3 div term, 1 without
+// (A_jj = V eta (|g|^2 I + c g g^T)).  Expanded:
+//   V eta w0^2 (P_ad + r^2 Q_d -/+ 2 r R_ad),
+//   P_ad = |l_a|^2 + c l_ad^2, Q_d = |m2|^2 + c m2_d^2, R_ad = l_a . m2 + c l_ad m2_d,
+// whose 21 factors depend on the lateral triangle only: they come from a per-level table (see
+// k_diag_coef), so a cell costs three FMAs per node and component.  V eta w0^2 = vol w0^2 |det M|
+// eta.  With HG, node (a, side) also gets eps (g_1,j^2 + g_2,j^2) in every component, which is
+// eps n_a (k9 - zeta / 3)^2 with n_a = 2, 5, 5 for a = 0, 1, 2 (zeta = -1 bottom, +1 top).
+constexpr int kDiagCoef = 24;  // table values per lateral triangle: P (9), R (9), Q (3), 2L, 6R, 0
+
 template <typename T, bool HG = false>
 struct OpDiag {
+  static constexpr int NIN = 1, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = false;
+  struct Col {
+    int t0;
+  };
+  int div_term;
+  T hgk;
+  const T* coef;  // [kDiagCoef][n_tri]
+  int n_tri;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int t0) const { return Col{t0}; }
+  __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&)[2][9], const T (&dM)[2],
+                                       const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3],
+                                       const Col& col) const {
+    const T r = lc[4], vw2 = lc[5];
+    const T r2 = r * r, rr = r + r;
+    T kbb = 0, ktt = 0;
+    if constexpr (HG) {
+      const T kb = lc[8] + (T)(1.0 / 3.0), kt = lc[8] - (T)(1.0 / 3.0);
+      kbb = kb * kb, ktt = kt * kt;
+    }
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const T* cf = coef + col.t0 + w;
+      const T A = vw2 * dM[w] * eta[w];
+      const T Ar2 = A * r2, A2r = A * rr;
+      T hb = 0, ht = 0;
+      if constexpr (HG) {
+        const T eps = (hgk * eta[w]) * dM[w] * (vw2 * cf[21 * n_tri] + lc[9] * cf[22 * n_tri]);
+        hb = eps * kbb, ht = eps * ktt;
+      }
+      T AQ[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) AQ[d] = Ar2 * cf[(18 + d) * n_tri];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = kCorner[w][a];
+        const bool first = w == 0 || q == 3;  // corner 11 belongs to W1 only
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const T inner = A * cf[(3 * a + d) * n_tri] + AQ[d];
+          const T cr = A2r * cf[(9 + 3 * a + d) * n_tri];
+          T vb = inner - cr, vt = inner + cr;
+          if constexpr (HG) {
+            const T na = a == 0 ? (T)2 : (T)5;
+            vb += na * hb, vt += na * ht;
+          }
+          accb[q][d] = first ? vb : accb[q][d] + vb;
+          acct[q][d] = first ? vt : acct[q][d] + vt;
+        }
+      }
+    }
+  }
+};
+
+// Diagonal in gradient form (the FP32 path, where the table loads cost more than the arithmetic
+// they save): node (a, side) of a wedge gets ve (|g|^2 + c g_d^2) with g = l_a w0 -/+ w1 m2
+// formed per cell, plus the hourglass term of OpDiag.
+template <typename T, bool HG = false>
+struct OpDiagG {
   static constexpr int NIN = 1, NOUT = 3;
   static constexpr bool USES_ETA = true, LOADS = false;
   using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
   T hgk;
-  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2]) const {
+  __device__ __forceinline__ Col column(const T (&Mi)[2][9], const T (&dM)[2], int) const {
     if constexpr (HG) return hg_column(Mi, dM);
     else return Col{};
   }
-  // With HG, node (a, side) of a wedge also gets eps (g_1,j^2 + g_2,j^2) in every component:
-  // g_m,j = zeta_j (xi_a or eta_a - 1/3) - k9 (...), which is eps n_a (k9 - zeta / 3)^2 with
-  // n_a = 2, 5, 5 for a = 0, 1, 2 (zeta = -1 bottom, +1 top).
   __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&Mi)[2][9], const T (&dM)[2],
                                        const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3],
                                        const Col& col) const {
@@ -524,7 +591,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
       if (EK != TN_ETA_F32 && Op::USES_ETA) dM[w] *= eta.cs[t0 + w];
     }
   }
-  const typename Op::Col col = op.column(Mi, dM);
+  const typename Op::Col col = op.column(Mi, dM, ((d * N + ci0) * N + cj0) * 2);
   // viscosity of the cell's two wedges at layer k: pair k N^2 2 + {0, 1} past the column base
   const int eta_c0 = (((d * (n_r - 1)) * N + ci0) * N + cj0) * 2;
   const int eta_ls = N * N * 2;
@@ -815,6 +882,39 @@ __global__ void k_interface_epi(Dims D, int n_groups, const int* __restrict__ gp
 // -2/3 g g^T, the symmetric-gradient term g g^T, so 1/3 with div_term, 1 without).
 // Only the two boundary node layers are handled here (the tile kernel with OpDiag writes the
 // interior layers): blocks = 10 * 2 * (N+1)^2 threads, layer 0 and layer n_r - 1.
+// Thread per lateral triangle: the OpDiag factors P_ad (q = 3a + d), R_ad (q = 9 + 3a + d), Q_d
+// (q = 18 + d), then 2 (|m0 + m1|^2 + |m0|^2 + |m1|^2) (q = 21) and 6 |m2|^2 (q = 22) of the
+// hourglass eps, from the FP64 geometry; written to the FP64 and the FP32 table.
+__global__ void k_diag_coef(int64_t n_tri, const double* __restrict__ geo, int div_term, double* c64, float* c32) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_tri) return;
+  double m[3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int x = 0; x < 3; ++x) m[k][x] = geo[(3 * k + x) * n_tri + t];
+  const double c = div_term ? 1.0 / 3.0 : 1.0;
+  double l[3][3];
+  for (int x = 0; x < 3; ++x) l[0][x] = -(m[0][x] + m[1][x]), l[1][x] = m[0][x], l[2][x] = m[1][x];
+  double v[kDiagCoef] = {};
+  const double m22 = m[2][0] * m[2][0] + m[2][1] * m[2][1] + m[2][2] * m[2][2];
+  for (int a = 0; a < 3; ++a) {
+    const double ll = l[a][0] * l[a][0] + l[a][1] * l[a][1] + l[a][2] * l[a][2];
+    const double lm = l[a][0] * m[2][0] + l[a][1] * m[2][1] + l[a][2] * m[2][2];
+    for (int d = 0; d < 3; ++d) {
+      v[3 * a + d] = ll + c * l[a][d] * l[a][d];
+      v[9 + 3 * a + d] = lm + c * l[a][d] * m[2][d];
+    }
+  }
+  for (int d = 0; d < 3; ++d) v[18 + d] = m22 + c * m[2][d] * m[2][d];
+  double L = 0;
+  for (int x = 0; x < 3; ++x) {
+    const double s01 = m[0][x] + m[1][x];
+    L += s01 * s01 + m[0][x] * m[0][x] + m[1][x] * m[1][x];
+  }
+  v[21] = 2.0 * L;
+  v[22] = 6.0 * m22;
+  for (int q = 0; q < kDiagCoef; ++q) c64[q * n_tri + t] = v[q], c32[q * n_tri + t] = (float)v[q];
+}
+
 // Hourglass-control part of the node block of wedge-local lateral node a (side 0: the node is on
 // the wedge's bottom layer): eps n_a (k9 - zeta / 3)^2 times the identity (see OpDiag).
 template <typename T>
@@ -1345,10 +1445,20 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
   // interior layers: per-cell tile kernel (boundary layers are overwritten below)
   const T* none[1] = {d[0]};
   const T hgk = (T)hg_coef(L, div_term);
-  cudaError_t e = L.hg_kappa > 0
-                      ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk}, none, d, etav<T>(L), st)
-                      : launch_tile<T, OpDiag<T, false>, 0>(L, bc, OpDiag<T, false>{div_term, hgk}, none, d, etav<T>(L),
-                                                            st);
+  const bool hg = L.hg_kappa > 0;
+  cudaError_t e;
+  if constexpr (sizeof(T) == 8) {  // FP64: per-triangle factor table
+    if (!L.dcoef64 || L.dcoef_div != div_term) return cudaErrorInvalidValue;  // built with the level
+    const T* coef = Tab<T>::dcoef(L);
+    const int nt = (int)L.n_tri;
+    e = hg ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk, coef, nt}, none, d, etav<T>(L),
+                                               st)
+           : launch_tile<T, OpDiag<T, false>, 0>(L, bc, OpDiag<T, false>{div_term, hgk, coef, nt}, none, d,
+                                                etav<T>(L), st);
+  } else {  // FP32: gradient form
+    e = hg ? launch_tile<T, OpDiagG<T, true>, 0>(L, bc, OpDiagG<T, true>{div_term, hgk}, none, d, etav<T>(L), st)
+           : launch_tile<T, OpDiagG<T, false>, 0>(L, bc, OpDiagG<T, false>{div_term, hgk}, none, d, etav<T>(L), st);
+  }
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
   k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
@@ -1469,6 +1579,20 @@ __global__ void k_eta_16(Dims D, const double* __restrict__ eta, uint16_t* __res
     q[base + k * per_d] = KIND == TN_ETA_BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(r))
                                               : __half_as_ushort(__float2half_rn(r));
   }
+}
+
+cudaError_t launch_diag_coef(Level& L, int div_term) {
+  if (!L.dcoef64) {
+    cudaError_t e = cudaMalloc((void**)&L.dcoef64, sizeof(double) * kDiagCoef * L.n_tri);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc((void**)&L.dcoef32, sizeof(float) * kDiagCoef * L.n_tri);
+    if (e != cudaSuccess) return e;
+  }
+  k_diag_coef<<<nblk(L.n_tri, 256), 256>>>(L.n_tri, L.geo64, div_term, L.dcoef64, L.dcoef32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  L.dcoef_div = div_term;
+  return cudaDeviceSynchronize();
 }
 
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st) {

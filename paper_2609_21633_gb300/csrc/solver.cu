@@ -1211,6 +1211,7 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
       Level* L = new Level();
       tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out, mesh->eta_storage);
       L->hg_kappa = mesh->hg_kappa;
+      if (cs == TN_OK && launch_diag_coef(*L, mesh->div_term) != cudaSuccess) cs = TN_ECUDA;
       m->owned_levels.push_back(L);
       if (cs != TN_OK) {
         mesh->mg = m;
