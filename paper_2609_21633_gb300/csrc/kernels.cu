@@ -59,6 +59,18 @@ constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
 #ifndef TN_CTA_TARGET
 #define TN_CTA_TARGET (32 * 152)
 #endif
+// CTA target for wide (16 x 32) tiles, which run one CTA per SM; 0 disables wide tiles.
+#ifndef TN_CTA_TARGET_WIDE
+#define TN_CTA_TARGET_WIDE (16 * 152)
+#endif
+#ifndef TN_WIDE_TILES
+#define TN_WIDE_TILES 1
+#endif
+// Register cap of the wide tiles: 561 threads are 18 warps, allocated as 20 (a multiple of the 4
+// sub-partitions), so 65536 / (20 x 32) rounds down to 96 registers per thread.
+#ifndef TN_WIDE_MAXREG
+#define TN_WIDE_MAXREG 96
+#endif
 #ifndef TN_KC_MIN
 #define TN_KC_MIN 8
 #endif
@@ -554,24 +566,28 @@ __device__ __forceinline__ void epilogue(const EpiArgs<T>& E, const T* in0, cons
 
 // EK: viscosity storage (TN_ETA_F32: eta.v; TN_ETA_BF16 / TN_ETA_F16: eta.q times eta.cs, the
 // column factor folded into |det M| once per column).
-template <typename T, typename Op, int TT, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
-__global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
-    k_tile(Dims D, Op op, const T* __restrict__ in0, const T* __restrict__ in1, const T* __restrict__ in2,
-           T* __restrict__ out0, T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ geo,
-           const T* __restrict__ lay, EtaView<T> eta, const T* __restrict__ svec, int bc_in, int bc_out,
-           int kc, const int* __restrict__ skip, EpiArgs<T> E) {
+// A CTA owns TI x TJ lateral node columns and computes the (TI + 1) x (TJ + 1) cells touching them.
+#define TN_TILE_PARAMS                                                                                          \
+  Dims D, Op op, const T *__restrict__ in0, const T *__restrict__ in1, const T *__restrict__ in2,             \
+      T *__restrict__ out0, T *__restrict__ out1, T *__restrict__ out2, const T *__restrict__ geo,             \
+      const T *__restrict__ lay, EtaView<T> eta, const T *__restrict__ svec, int bc_in, int bc_out, int kc,    \
+      const int *__restrict__ skip, EpiArgs<T> E
+#define TN_TILE_ARGS D, op, in0, in1, in2, out0, out1, out2, geo, lay, eta, svec, bc_in, bc_out, kc, skip, E
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI, int EK>
+__device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
   // All offsets are 32-bit: launch_tile only accepts levels whose node and wedge arrays have
   // fewer than 2^31 entries.
-  constexpr int NIN = Op::NIN, NOUT = Op::NOUT, W = TT + 1;
-  __shared__ T sm[4][NOUT][W][W];
+  constexpr int NIN = Op::NIN, NOUT = Op::NOUT, WI = TI + 1, WJ = TJ + 1;
+  // corners 10, 01, 11 of every cell (corner 00 is the thread's own node: it stays in registers)
+  __shared__ T sm[3][NOUT][WI][WJ];
   if (skip && *skip) return;  // device-side early exit (uniform over the grid)
   const int N = D.N, n_r = D.n_r, P = D.P;
   const int LS = (int)D.layer_stride, NLL = (int)D.n_lat_layout;
-  const int ntj = N / TT;
-  const int i0 = (blockIdx.x / ntj) * TT, j0 = (blockIdx.x % ntj) * TT;
+  const int ntj = N / TJ;
+  const int i0 = (blockIdx.x / ntj) * TI, j0 = (blockIdx.x % ntj) * TJ;
   const int d = blockIdx.z;
   const int kc0 = blockIdx.y * kc, kc1 = min(n_r - 1, kc0 + kc);
-  const int ti = threadIdx.x / W, tj = threadIdx.x % W;
+  const int ti = threadIdx.x / WJ, tj = threadIdx.x % WJ;
   const int ci = i0 - 1 + ti, cj = j0 - 1 + tj;  // this thread's cell
   const bool cell_ok = ci >= 0 && cj >= 0;       // ci, cj <= N - 1 always
   const int ci0 = max(ci, 0), cj0 = max(cj, 0);
@@ -599,7 +615,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   // node N (handled in the rare path below)
   const bool own = ti >= 1 && tj >= 1;
   const bool own_shared = ci == 0 || ci == N || cj == 0 || cj == N;
-  const bool last_i = (i0 + TT == N) && ti == TT, last_j = (j0 + TT == N) && tj == TT;
+  const bool last_i = (i0 + TI == N) && ti == TI, last_j = (j0 + TJ == N) && tj == TJ;
   // when own, ci = ci0 and cj = cj0: the owned node is corner 00 (offsets c00 and lat00)
 
   auto load_level = [&](int k, T (&v)[4][NIN]) {
@@ -655,9 +671,9 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   // exchange the node-level sums of the four corners and write the owned nodes of layer k
   auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 1; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) sm[q][c][ti][tj] = acc[q][c];
+      for (int c = 0; c < NOUT; ++c) sm[q - 1][c][ti][tj] = acc[q][c];
     __syncthreads();
     if (own) {
       // node (ci, cj): cell (ci, cj) corner 00 + (ci-1, cj) corner 10 + (ci, cj-1) corner 01 +
@@ -665,7 +681,7 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
       T v[3] = {0, 0, 0};
 #pragma unroll
       for (int c = 0; c < NOUT; ++c)
-        v[c] = ((sm[0][c][ti][tj] + sm[1][c][ti - 1][tj]) + sm[2][c][ti][tj - 1]) + sm[3][c][ti - 1][tj - 1];
+        v[c] = ((acc[0][c] + sm[0][c][ti - 1][tj]) + sm[1][c][ti][tj - 1]) + sm[2][c][ti - 1][tj - 1];
       store_node(k, c00 + k * LS, lat00, own_shared, v);
     }
     if (last_i || last_j) {  // rare: nodes in row / column N of the diamond
@@ -679,14 +695,14 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
           const int xi = ti + oi, xj = tj + oj;
           if (xi < 1 || xj < 1) continue;
           const int ni = ci + oi, nj = cj + oj;
+          // node (ni, nj) is in row or column N: no cell has it as corner 00
           T v[3] = {0, 0, 0};
 #pragma unroll
           for (int c = 0; c < NOUT; ++c) {
-            T a = (xi <= TT && xj <= TT) ? sm[0][c][xi][xj] : (T)0;
-            T b = (xj <= TT) ? sm[1][c][xi - 1][xj] : (T)0;
-            T e = (xi <= TT) ? sm[2][c][xi][xj - 1] : (T)0;
-            T f = sm[3][c][xi - 1][xj - 1];
-            v[c] = ((a + b) + e) + f;
+            T b = (xj <= TJ) ? sm[0][c][xi - 1][xj] : (T)0;
+            T e = (xi <= TI) ? sm[1][c][xi][xj - 1] : (T)0;
+            T f = sm[2][c][xi - 1][xj - 1];
+            v[c] = (b + e) + f;
           }
           const bool shared = ni == 0 || ni == N || nj == 0 || nj == N;
           store_node(k, (int)(d * D.diamond_stride) + k * LS + ni * P + nj, d * (N + 1) * P + ni * P + nj, shared,
@@ -750,6 +766,19 @@ __global__ void __launch_bounds__((TT + 1) * (TT + 1), MinBlocks<T>::value)
   if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
 }
 
+// Square tiles: MinBlocks CTAs per SM through the register cap of the launch bounds.
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
+__global__ void __launch_bounds__((TI + 1) * (TJ + 1), MinBlocks<T>::value) k_tile(TN_TILE_PARAMS) {
+  tile_body<T, Op, TI, TJ, FLAGS, EPI, EK>(TN_TILE_ARGS);
+}
+
+// Wide tiles (16 x 32 nodes, 561 threads, one CTA per SM): registers capped at TN_WIDE_MAXREG so
+// that the CTA fits the register file.
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
+__global__ void __maxnreg__(TN_WIDE_MAXREG) k_tile_wide(TN_TILE_PARAMS) {
+  tile_body<T, Op, TI, TJ, FLAGS, EPI, EK>(TN_TILE_ARGS);
+}
+
 template <typename T, typename Op, int FLAGS, int EPI = EPI_NONE>
 cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const EtaView<T>& eta,
                         cudaStream_t st, const int* skip = nullptr, const EpiArgs<T>* epi = nullptr) {
@@ -758,12 +787,18 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   Dims D = dims(L);
   if (L.n_layout >= (int64_t)INT32_MAX || L.n_wedges >= (int64_t)INT32_MAX || 10 * L.n_tri >= (int64_t)INT32_MAX)
     return cudaErrorInvalidValue;  // the tile kernel uses 32-bit offsets
-  const int tt = L.N >= TILE ? TILE : L.N;
-  const int ntiles = (L.N / tt) * (L.N / tt);
+  // tile shape: FP64 16 x 32 nodes where N >= 32 (fewer halo cells and idle lanes per owned node,
+  // one CTA per SM; measured slower for the issue-bound FP32 kernels), else square N' x N' with
+  // N' = min(N, 16)
+  constexpr bool kWideT = sizeof(T) == 8 && TN_WIDE_TILES;
+  const bool wide = kWideT && L.N >= 2 * TILE;
+  const int ti_ = L.N >= TILE ? TILE : L.N, tj_ = wide ? 2 * TILE : ti_;
+  const int ntiles = (L.N / ti_) * (L.N / tj_);
   const int ncells = L.n_r - 1;
-  // radial chunks: enough CTAs to fill the GPU a few times over
+  // radial chunks: enough CTAs to fill the GPU a few times over (wide tiles: one CTA per SM)
+  const int64_t target = wide ? TN_CTA_TARGET_WIDE : TN_CTA_TARGET;
   int kc = ncells;
-  while (kc > TN_KC_MIN && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < TN_CTA_TARGET) kc = (kc + 1) / 2;
+  while (kc > TN_KC_MIN && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < target) kc = (kc + 1) / 2;
   dim3 grid(ntiles, (ncells + kc - 1) / kc, 10);
   const T* i1 = Op::NIN > 1 ? in[1] : in[0];
   const T* i2 = Op::NIN > 2 ? in[2] : in[0];
@@ -772,35 +807,34 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   const T* sv = Tab<T>::s(L);
   const T* geo = Tab<T>::geo(L);
   const T* lay = Tab<T>::lay(L);
-  // 16-bit viscosity: only full tiles (levels with N >= 16 store it) and the ops that read it
+#define TN_TILE_LAUNCH(KERNEL, TIv, TJv, EKv)                                                                   \
+  KERNEL<T, Op, TIv, TJv, FLAGS, EPI, EKv><<<grid, (TIv + 1) * (TJv + 1), 0, st>>>(                             \
+      D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E)
+  // 16-bit viscosity (FP32 path only): only full tiles (levels with N >= 16 store it)
   if constexpr (Op::USES_ETA && sizeof(T) == 4) {
     if (eta.kind != TN_ETA_F32) {
-    if (tt != TILE) return cudaErrorInvalidValue;
-    constexpr int B = (TILE + 1) * (TILE + 1);
-    if (eta.kind == TN_ETA_BF16)
-      k_tile<T, Op, TILE, FLAGS, EPI, TN_ETA_BF16><<<grid, B, 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, geo, lay,
-                                                                      eta, sv, bc.in, bc.out, kc, skip, E);
-    else
-      k_tile<T, Op, TILE, FLAGS, EPI, TN_ETA_F16><<<grid, B, 0, st>>>(D, op, in[0], i1, i2, out[0], o1, o2, geo, lay,
-                                                                     eta, sv, bc.in, bc.out, kc, skip, E);
-    return cudaGetLastError();
+      if (ti_ != TILE) return cudaErrorInvalidValue;
+      if (eta.kind == TN_ETA_BF16) TN_TILE_LAUNCH(k_tile, TILE, TILE, TN_ETA_BF16);
+      else TN_TILE_LAUNCH(k_tile, TILE, TILE, TN_ETA_F16);
+      return cudaGetLastError();
     }
   }
-#define TN_TILE_CASE(TTv)                                                                                     \
-  case TTv:                                                                                                   \
-    k_tile<T, Op, TTv, FLAGS, EPI><<<grid, (TTv + 1) * (TTv + 1), 0, st>>>(                           \
-        D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E);           \
-    break;
-  switch (tt) {
-    TN_TILE_CASE(16)
-    TN_TILE_CASE(8)
-    TN_TILE_CASE(4)
-    TN_TILE_CASE(2)
-    TN_TILE_CASE(1)
+  if constexpr (kWideT) {
+    if (wide) {
+      TN_TILE_LAUNCH(k_tile_wide, TILE, 2 * TILE, TN_ETA_F32);
+      return cudaGetLastError();
+    }
+  }
+  switch (ti_) {
+    case 16: TN_TILE_LAUNCH(k_tile, 16, 16, TN_ETA_F32); break;
+    case 8: TN_TILE_LAUNCH(k_tile, 8, 8, TN_ETA_F32); break;
+    case 4: TN_TILE_LAUNCH(k_tile, 4, 4, TN_ETA_F32); break;
+    case 2: TN_TILE_LAUNCH(k_tile, 2, 2, TN_ETA_F32); break;
+    case 1: TN_TILE_LAUNCH(k_tile, 1, 1, TN_ETA_F32); break;
     default:
       return cudaErrorInvalidValue;
   }
-#undef TN_TILE_CASE
+#undef TN_TILE_LAUNCH
   return cudaGetLastError();
 }
 
