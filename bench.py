@@ -220,9 +220,7 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=
         tn.tn_buoyancy(m, Td, Ra, f)
         u = [torch.zeros_like(f[0]) for _ in range(3)]
         p = torch.zeros(pinfo["n_layout"], device=dev, dtype=torch.float64)
-        tn.tn_mg_setup(m, torch.float64)
-        if mode == tn.TN_SOLVE_MIXED:
-            tn.tn_mg_setup(m, torch.float32)
+        tn.tn_mg_setup(m, torch.float32 if mode == tn.TN_SOLVE_MIXED else torch.float64)
         torch.cuda.synchronize()
         st = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(mode=mode), check=False)
         nv = 3 * info["n_unique_nodes"]

@@ -1,5 +1,6 @@
 // C ABI of the wedge Stokes library: argument checks, mesh hierarchy lifetime, dispatch.
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -83,7 +84,38 @@ cudaError_t apply_BT_t(tn_mesh* m, int level, const void* p, void* const* y, cud
 }  // namespace
 
 // Host tables and device arrays of one level (lateral level l, nr node layers).
-tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage) {
+// The diag(A) factor table of the level (see Level::dcoef64) from the FP64 geometry table.
+std::vector<double> diag_factors(const std::vector<double>& geo, int64_t n_tri, int div_term) {
+  std::vector<double> v((size_t)kDiagCoef * n_tri, 0.0);
+  const double c = div_term ? 1.0 / 3.0 : 1.0;
+  for (int64_t t = 0; t < n_tri; ++t) {
+    double m[3][3], l[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int x = 0; x < 3; ++x) m[k][x] = geo[(size_t)(3 * k + x) * n_tri + t];
+    for (int x = 0; x < 3; ++x) l[0][x] = -(m[0][x] + m[1][x]), l[1][x] = m[0][x], l[2][x] = m[1][x];
+    auto put = [&](int q, double val) { v[(size_t)q * n_tri + t] = val; };
+    const double m22 = m[2][0] * m[2][0] + m[2][1] * m[2][1] + m[2][2] * m[2][2];
+    for (int a = 0; a < 3; ++a) {
+      const double ll = l[a][0] * l[a][0] + l[a][1] * l[a][1] + l[a][2] * l[a][2];
+      const double lm = l[a][0] * m[2][0] + l[a][1] * m[2][1] + l[a][2] * m[2][2];
+      for (int d = 0; d < 3; ++d) {
+        put(3 * a + d, ll + c * l[a][d] * l[a][d]);
+        put(9 + 3 * a + d, lm + c * l[a][d] * m[2][d]);
+      }
+    }
+    for (int d = 0; d < 3; ++d) put(18 + d, m22 + c * m[2][d] * m[2][d]);
+    double L = 0;
+    for (int x = 0; x < 3; ++x) {
+      const double s01 = m[0][x] + m[1][x];
+      L += s01 * s01 + m[0][x] * m[0][x] + m[1][x] * m[1][x];
+    }
+    put(21, 2.0 * L);
+    put(22, 6.0 * m22);
+  }
+  return v;
+}
+
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage, int div_term) {
   std::vector<double> geo, lay, s, grp_s;
   std::vector<int> gptr;
   std::vector<int64_t> goff;
@@ -99,6 +131,12 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
   };
   chk(upload(L.geo64, geo));
   chk(upload(L.geo32, to_f32(geo)));
+  {
+    const std::vector<double> dc = diag_factors(geo, L.n_tri, div_term);
+    chk(upload(L.dcoef64, dc));
+    chk(upload(L.dcoef32, to_f32(dc)));
+    L.dcoef_div = div_term;
+  }
   chk(upload(L.lay64, lay));
   chk(upload(L.lay32, to_f32(lay)));
   chk(upload(L.s64, s));
@@ -177,6 +215,13 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   if ((o.bc_inner != TN_BC_FREESLIP && o.bc_inner != TN_BC_NOSLIP) ||
       (o.bc_outer != TN_BC_FREESLIP && o.bc_outer != TN_BC_NOSLIP))
     return inval("tn_mesh_create: unknown boundary condition");
+  {
+    // kernel attributes once per process, before any stream work or graph capture needs them
+    static std::once_flag once;
+    static cudaError_t prep = cudaSuccess;
+    std::call_once(once, [] { prep = prepare_tile_kernels(); });
+    if (prep != cudaSuccess) return cuda_fail(prep, "tn_mesh_create: kernel attributes");
+  }
   tn_mesh* m = new (std::nothrow) tn_mesh();
   if (!m) {
     set_error("tn_mesh_create: host allocation failed");
@@ -193,12 +238,8 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   int l = lateral_level, nr = radial_layers;
   while (true) {
     m->lv.emplace_back();
-    tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage);
+    tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage, m->div_term);
     m->lv.back().hg_kappa = o.hg_kappa;
-    if (s == TN_OK) {
-      cudaError_t ce = launch_diag_coef(m->lv.back(), m->div_term);
-      if (ce != cudaSuccess) s = cuda_fail(ce, "tn_mesh_create: diagonal factors");
-    }
     if (s != TN_OK) {
       std::string msg = tn_last_error();
       tn_mesh_destroy(m);

@@ -11,6 +11,7 @@
 namespace tn {
 
 constexpr int kLayerStride = 12;  // values per radial cell in the layer table
+constexpr int kDiagCoef = 24;     // values per lateral triangle in the diag(A) factor table
 
 // Per-level mesh data.  Host vectors hold the definition; device pointers are
 // owned by the level and freed by tn_mesh_destroy.
@@ -106,7 +107,7 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
 
 void set_error(const std::string& msg);
 // Tables and device arrays of one level (api.cu); destroy_level frees them.
-tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage);
+tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage, int div_term);
 void destroy_level(Level& L);
 void mg_invalidate(tn_mesh* mesh);
 
@@ -165,9 +166,9 @@ cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double 
                               cudaStream_t st);
 cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st);
 cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st);
-// Per-triangle factors of diag(A) for the level's geometry and div term (allocates on first
-// use; synchronous).
-cudaError_t launch_diag_coef(Level& L, int div_term);
+// Kernel attributes that must be set before the first launch (shared-memory opt-ins); called
+// once per process by tn_mesh_create.
+cudaError_t prepare_tile_kernels();
 // The FP32 path's viscosity from eta64: eta32, or eta16 and the column factors (see Level).
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st);
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);

@@ -136,8 +136,9 @@ __device__ __forceinline__ T eta_at(const EtaView<T>& E, int64_t w, int64_t t) {
 
 
 // ------------------------------------------------------------------------------------ element ops
-// An op processes both wedges of one hexahedral cell.  Inputs are the nodal values at the
-// cell's four lateral corners (00, 10, 01, 11) on its bottom (ub) and top (ut) node layer;
+// An op processes both wedges of one hexahedral cell.  Inputs are, at the cell's four lateral
+// corners (00, 10, 01, 11), the sums s = top + bottom and differences d = top - bottom of the
+// nodal values on its bottom and top node layer (computed once per node by the tile kernel);
 // the op assigns the cell's contributions to the same eight node slots (accb, acct), every
 // entry.  Wedge-local lateral node a of wedge w sits at corner kCorner[w][a]: W0 = (00, 10, 01),
 // W1 = (11, 01, 10), so corner 00 belongs to W0 only, 11 to W1 only and 10, 01 to both.  `lc`
@@ -210,7 +211,7 @@ __device__ __forceinline__ HgCol<T> hg_column(const T (&Mi)[2][9], const T (&dM)
 template <typename T, bool HG = false>
 struct OpA {
   static constexpr int NIN = 3, NOUT = 3;
-  static constexpr bool USES_ETA = true, LOADS = true;
+  static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
   using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
   T hgk;  // kappa (3 + c) / 18 (HG only)
@@ -218,15 +219,10 @@ struct OpA {
     if constexpr (HG) return hg_column(Mi, dM);
     else return Col{};
   }
-  __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
+  __device__ __forceinline__ void cell(const T (&s)[4][3], const T (&dd)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&eta)[2], T (&accb)[4][3],
                                        T (&acct)[4][3], const Col& col) const {
     const T r = lc[4], vw2 = lc[5];
-    T s[4][3], dd[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
     // X: per-corner sums of X; without HG h[w] is the H[:,2] column of wedge w, with HG Y holds
     // the per-corner sums of the top-minus-bottom part
     T X[4][3], h[2][3], Y[4][3];
@@ -307,18 +303,13 @@ struct OpA {
 template <typename T>
 struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
-  static constexpr bool USES_ETA = false, LOADS = true;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
   using Col = NoCol;
   __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
-  __device__ __forceinline__ void cell(const T (&ub)[4][3], const T (&ut)[4][3], const T (&Mi)[2][9],
+  __device__ __forceinline__ void cell(const T (&s)[4][3], const T (&dd)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
                                        T (&acct)[4][1], const Col&) const {
     const T r = lc[4], vw6 = lc[7];
-    T s[4][3], dd[4][3];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s[q][c] = ub[q][c] + ut[q][c], dd[q][c] = ut[q][c] - ub[q][c];
     T v[2];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
@@ -346,16 +337,14 @@ struct OpDiv {
 template <typename T>
 struct OpGrad {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = false, LOADS = true;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = false;
   using Col = NoCol;
   __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
-  __device__ __forceinline__ void cell(const T (&ub)[4][1], const T (&ut)[4][1], const T (&Mi)[2][9],
+  __device__ __forceinline__ void cell(const T (&sn)[4][1], const T (&)[4][1], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][3],
                                        T (&acct)[4][3], const Col&) const {
     const T r = lc[4], vw6 = lc[7];
-    T s[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) s[q] = ub[q][0] + ut[q][0];
+    const T s[4] = {sn[0][0], sn[1][0], sn[2][0], sn[3][0]};
     T X[4][3], h[2][3];
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
@@ -385,16 +374,15 @@ struct OpGrad {
 // (A_jj = V eta (|g|^2 I + c g g^T)).  Expanded:
 //   V eta w0^2 (P_ad + r^2 Q_d -/+ 2 r R_ad),
 //   P_ad = |l_a|^2 + c l_ad^2, Q_d = |m2|^2 + c m2_d^2, R_ad = l_a . m2 + c l_ad m2_d,
-// whose 21 factors depend on the lateral triangle only: they come from a per-level table (see
-// k_diag_coef), so a cell costs three FMAs per node and component.  V eta w0^2 = vol w0^2 |det M|
+// whose 21 factors depend on the lateral triangle only: they come from a per-level table
+// (Level::dcoef64 / dcoef32), so a cell costs three FMAs per node and component.  V eta w0^2 = vol w0^2 |det M|
 // eta.  With HG, node (a, side) also gets eps (g_1,j^2 + g_2,j^2) in every component, which is
 // eps n_a (k9 - zeta / 3)^2 with n_a = 2, 5, 5 for a = 0, 1, 2 (zeta = -1 bottom, +1 top).
-constexpr int kDiagCoef = 24;  // table values per lateral triangle: P (9), R (9), Q (3), 2L, 6R, 0
 
 template <typename T, bool HG = false>
 struct OpDiag {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = true, LOADS = false;
+  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false;
   struct Col {
     int t0;
   };
@@ -453,7 +441,7 @@ struct OpDiag {
 template <typename T, bool HG = false>
 struct OpDiagG {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = true, LOADS = false;
+  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false;
   using Col = typename std::conditional<HG, HgCol<T>, NoCol>::type;
   int div_term;
   T hgk;
@@ -573,13 +561,32 @@ __device__ __forceinline__ void epilogue(const EpiArgs<T>& E, const T* in0, cons
       const T *__restrict__ lay, EtaView<T> eta, const T *__restrict__ svec, int bc_in, int bc_out, int kc,    \
       const int *__restrict__ skip, EpiArgs<T> E
 #define TN_TILE_ARGS D, op, in0, in1, in2, out0, out1, out2, geo, lay, eta, svec, bc_in, bc_out, kc, skip, E
+// Shared memory of a tile: NS per-node values (corner sums s and, for ops that need them,
+// differences d of the input, per component) on the (TI + 2) x (TJ + 2) nodes the cells touch,
+// then corners 10, 01, 11 of every cell's output contributions.
+template <typename T, typename Op, int TI, int TJ>
+struct TileSmem {
+  // FP64 shares the per-node sums through shared memory (the FP64 pipe is the bottleneck); the
+  // issue-bound FP32 kernels form them per cell from four corner loads instead (measured faster)
+  static constexpr bool SHARE = sizeof(T) == 8;
+  static constexpr int NS = (Op::LOADS && SHARE) ? (Op::NEEDS_D ? 2 * Op::NIN : Op::NIN) : 0;
+  static constexpr int SD = NS * (TI + 2) * (TJ + 2);
+  static constexpr int SM = 3 * Op::NOUT * (TI + 1) * (TJ + 1);
+  static constexpr size_t bytes = sizeof(T) * (size_t)(SD + SM);
+};
+
 template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI, int EK>
 __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
   // All offsets are 32-bit: launch_tile only accepts levels whose node and wedge arrays have
   // fewer than 2^31 entries.
   constexpr int NIN = Op::NIN, NOUT = Op::NOUT, WI = TI + 1, WJ = TJ + 1;
-  // corners 10, 01, 11 of every cell (corner 00 is the thread's own node: it stays in registers)
-  __shared__ T sm[3][NOUT][WI][WJ];
+  using Sh = TileSmem<T, Op, TI, TJ>;
+  constexpr int NS = Sh::NS;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  T* const sd = reinterpret_cast<T*>(tile_smem);  // [NS][WI + 1][WJ + 1]
+  T* const sm = sd + Sh::SD;                        // [3][NOUT][WI][WJ]
+  auto SD = [&](int v, int i, int j) -> T& { return sd[(v * (WI + 1) + i) * (WJ + 1) + j]; };
+  auto SM = [&](int q, int c, int i, int j) -> T& { return sm[((q * NOUT + c) * WI + i) * WJ + j]; };
   if (skip && *skip) return;  // device-side early exit (uniform over the grid)
   const int N = D.N, n_r = D.n_r, P = D.P;
   const int LS = (int)D.layer_stride, NLL = (int)D.n_lat_layout;
@@ -591,9 +598,8 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
   const int ci = i0 - 1 + ti, cj = j0 - 1 + tj;  // this thread's cell
   const bool cell_ok = ci >= 0 && cj >= 0;       // ci, cj <= N - 1 always
   const int ci0 = max(ci, 0), cj0 = max(cj, 0);
-  // node offset of corner 00 of this cell on layer 0; corners 10, 01, 11 are +P, +1, +P+1
+  // node offset of corner 00 of this cell on layer 0 (the thread's own node when cell_ok)
   const int c00 = (int)(d * D.diamond_stride) + ci0 * P + cj0;
-  const int cdel[4] = {0, P, 1, P + 1};
   const int lat00 = d * (N + 1) * P + ci0 * P + cj0;  // lateral-layout offset of corner 00
   // per-cell lateral geometry (both triangles), kept in registers for the whole column
   T Mi[2][9], dM[2];
@@ -618,30 +624,39 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
   const bool last_i = (i0 + TI == N) && ti == TI, last_j = (j0 + TJ == N) && tj == TJ;
   // when own, ci = ci0 and cj = cj0: the owned node is corner 00 (offsets c00 and lat00)
 
-  auto load_level = [&](int k, T (&v)[4][NIN]) {
-    if (!Op::LOADS || !cell_ok) {
+  // Input nodes: every thread reads its own node (ci, cj) (slot (ti, tj) of sd) and carries it
+  // from layer to layer; the WI + WJ + 1 nodes of the extra row i0 + TI and column j0 + TJ
+  // (slots WI and WJ) are read, both layers, by threads 0, 1, ... (extra_node).
+  constexpr int NX = WI + WJ + 1;
+  auto extra_node = [&](int e, int& si, int& sj) {
+    si = e < WJ ? WI : (e < WJ + WI ? e - WJ : WI);
+    sj = e < WJ ? e : WJ;
+  };
+  // load one node's input at layer k (projected at the boundary layers), zero if absent
+  auto load_node = [&](bool ok, int off, int lat, int k, T (&v)[NIN]) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+    for (int c = 0; c < NIN; ++c) v[c] = (T)0;
+    if (!ok) return;
+    const int o = off + k * LS;
+    v[0] = in0[o];
+    if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
+    if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
+    if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
+      T vv[3] = {v[0], v[NIN > 1 ? 1 : 0], v[NIN > 2 ? 2 : 0]};
+      project_vec(vv, svec, (int64_t)lat, (int64_t)NLL, k == 0 ? bc_in : bc_out);
 #pragma unroll
-        for (int c = 0; c < NIN; ++c) v[q][c] = (T)0;
-      if (!Op::LOADS) return;
-    } else {
-      const int o = c00 + k * LS;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        v[q][0] = in0[o + cdel[q]];
-        if (NIN > 1) v[q][NIN > 1 ? 1 : 0] = in1[o + cdel[q]];
-        if (NIN > 2) v[q][NIN > 2 ? 2 : 0] = in2[o + cdel[q]];
-      }
+      for (int c = 0; c < NIN; ++c) v[c] = vv[c];
     }
-    if ((FLAGS & PROJ_IN) && cell_ok && (k == 0 || k == n_r - 1)) {
-      const int bc = k == 0 ? bc_in : bc_out;
+  };
+  // corner sums / differences of one node between layers k and k+1 into sd slot (i, j)
+  auto put_node = [&](int i, int j, const T (&b)[NIN], const T (&t)[NIN], T (&sv)[NIN], T (&dv)[NIN]) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        T vv[3] = {v[q][0], v[q][NIN > 1 ? 1 : 0], v[q][NIN > 2 ? 2 : 0]};
-        project_vec(vv, svec, (int64_t)(lat00 + cdel[q]), (int64_t)NLL, bc);
-#pragma unroll
-        for (int c = 0; c < NIN; ++c) v[q][c] = vv[c];
+    for (int c = 0; c < NIN; ++c) {
+      sv[c] = b[c] + t[c];
+      SD(c, i, j) = sv[c];
+      if (Op::NEEDS_D) {
+        dv[c] = t[c] - b[c];
+        SD(NIN + c, i, j) = dv[c];
       }
     }
   };
@@ -668,12 +683,13 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
     if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
   };
 
-  // exchange the node-level sums of the four corners and write the owned nodes of layer k
+  // exchange the node-level sums of the four corners and write the owned nodes of layer k.  The
+  // caller has synchronised since sm was last read; sd is not touched.
   auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
 #pragma unroll
     for (int q = 1; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < NOUT; ++c) sm[q - 1][c][ti][tj] = acc[q][c];
+      for (int c = 0; c < NOUT; ++c) SM(q - 1, c, ti, tj) = acc[q][c];
     __syncthreads();
     if (own) {
       // node (ci, cj): cell (ci, cj) corner 00 + (ci-1, cj) corner 10 + (ci, cj-1) corner 01 +
@@ -681,7 +697,7 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
       T v[3] = {0, 0, 0};
 #pragma unroll
       for (int c = 0; c < NOUT; ++c)
-        v[c] = ((acc[0][c] + sm[0][c][ti - 1][tj]) + sm[1][c][ti][tj - 1]) + sm[2][c][ti - 1][tj - 1];
+        v[c] = ((acc[0][c] + SM(0, c, ti - 1, tj)) + SM(1, c, ti, tj - 1)) + SM(2, c, ti - 1, tj - 1);
       store_node(k, c00 + k * LS, lat00, own_shared, v);
     }
     if (last_i || last_j) {  // rare: nodes in row / column N of the diamond
@@ -699,9 +715,9 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
           T v[3] = {0, 0, 0};
 #pragma unroll
           for (int c = 0; c < NOUT; ++c) {
-            T b = (xj <= TJ) ? sm[0][c][xi - 1][xj] : (T)0;
-            T e = (xi <= TI) ? sm[1][c][xi][xj - 1] : (T)0;
-            T f = sm[2][c][xi - 1][xj - 1];
+            T b = (xj <= TJ) ? SM(0, c, xi - 1, xj) : (T)0;
+            T e = (xi <= TI) ? SM(1, c, xi, xj - 1) : (T)0;
+            T f = SM(2, c, xi - 1, xj - 1);
             v[c] = (b + e) + f;
           }
           const bool shared = ni == 0 || ni == N || nj == 0 || nj == N;
@@ -709,10 +725,38 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
                      v);
         }
     }
-    __syncthreads();
   };
 
-  T ub[4][NIN], ut[4][NIN];
+  // per-cell path (FP32): the four corners of the cell, carried from layer to layer
+  constexpr bool PERCELL = Op::LOADS && !Sh::SHARE;
+  const int cdel[4] = {0, P, 1, P + 1};
+  auto load_corners = [&](int k, T (&v)[4][NIN]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) v[q][c] = (T)0;
+    if (!cell_ok) return;
+    const int o = c00 + k * LS;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q][0] = in0[o + cdel[q]];
+      if (NIN > 1) v[q][NIN > 1 ? 1 : 0] = in1[o + cdel[q]];
+      if (NIN > 2) v[q][NIN > 2 ? 2 : 0] = in2[o + cdel[q]];
+    }
+    if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
+      const int bc = k == 0 ? bc_in : bc_out;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T vv[3] = {v[q][0], v[q][NIN > 1 ? 1 : 0], v[q][NIN > 2 ? 2 : 0]};
+        project_vec(vv, svec, (int64_t)(lat00 + cdel[q]), (int64_t)NLL, bc);
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) v[q][c] = vv[c];
+      }
+    }
+  };
+  T ubc[PERCELL ? 4 : 1][NIN];
+
+  T ub[NIN];  // own node at the bottom layer of the current cell layer
   T carry[4][NOUT];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -720,9 +764,52 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
     for (int c = 0; c < NOUT; ++c) carry[q][c] = 0;
 
   const int kstart = kc0 > 0 ? kc0 - 1 : 0;
-  load_level(kstart, ub);
+  if (NS > 0) load_node(cell_ok, c00, lat00, kstart, ub);
+  if constexpr (PERCELL) load_corners(kstart, ubc);
   for (int k = kstart; k < kc1; ++k) {
-    load_level(k + 1, ut);
+    // corner sums and differences of layer pair (k, k+1): own node, then the extra nodes
+    T s[4][NIN], dd[4][NIN];
+    if constexpr (PERCELL) {
+      T utc[4][NIN];
+      load_corners(k + 1, utc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) {
+          s[q][c] = ubc[q][c] + utc[q][c];
+          if (Op::NEEDS_D) dd[q][c] = utc[q][c] - ubc[q][c];
+          ubc[q][c] = utc[q][c];
+        }
+    }
+    if (NS > 0) {
+      T ut[NIN];
+      load_node(cell_ok, c00, lat00, k + 1, ut);
+      put_node(ti, tj, ub, ut, s[0], dd[0]);
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) ub[c] = ut[c];
+      for (int e = (int)threadIdx.x; e < NX; e += (int)blockDim.x) {
+        int si, sj;
+        extra_node(e, si, sj);
+        const int ni = i0 - 1 + si, nj = j0 - 1 + sj;
+        const bool ok = ni >= 0 && nj >= 0;  // ni, nj <= N always
+        const int off = (int)(d * D.diamond_stride) + max(ni, 0) * P + max(nj, 0);
+        const int lat = d * (N + 1) * P + max(ni, 0) * P + max(nj, 0);
+        T xb[NIN], xt[NIN], xs[NIN], xd[NIN];
+        load_node(ok, off, lat, k, xb);
+        load_node(ok, off, lat, k + 1, xt);
+        put_node(si, sj, xb, xt, xs, xd);
+      }
+      __syncthreads();
+      // corners 10, 01, 11 of this cell: nodes (ci+1, cj), (ci, cj+1), (ci+1, cj+1)
+      const int qi[3] = {ti + 1, ti, ti + 1}, qj[3] = {tj, tj + 1, tj + 1};
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) {
+          s[q][c] = SD(c, qi[q - 1], qj[q - 1]);
+          if (Op::NEEDS_D) dd[q][c] = SD(NIN + c, qi[q - 1], qj[q - 1]);
+        }
+    }
     T accb[4][NOUT], acct[4][NOUT];  // assigned by the op (zero for a halo cell outside the diamond)
     if (!cell_ok) {
 #pragma unroll
@@ -746,7 +833,7 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
           e[0] = (T)from16<EK>((uint16_t)(p & 0xffffu)), e[1] = (T)from16<EK>((uint16_t)(p >> 16));
         }
       }
-      op.cell(ub, ut, Mi, dM, lay + kLayerStride * k, e, accb, acct, col);
+      op.cell(s, dd, Mi, dM, lay + kLayerStride * k, e, accb, acct, col);
     }
     if (k >= kc0) {
 #pragma unroll
@@ -755,15 +842,18 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
         for (int c = 0; c < NOUT; ++c) accb[q][c] += carry[q][c];
       exchange_write(k, accb);
     }
+    // sd and sm are rewritten only after every thread has passed the next barrier, which comes
+    // after its reads of this layer; without shared inputs (NS = 0) a barrier closes the layer
+    if (NS == 0 || k < kc0) __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) carry[q][c] = acct[q][c];
-#pragma unroll
-      for (int c = 0; c < NIN; ++c) ub[q][c] = ut[q][c];
-    }
   }
-  if (kc1 == n_r - 1) exchange_write(n_r - 1, carry);
+  if (kc1 == n_r - 1) {
+    __syncthreads();  // sm of the last layer has been read by every thread
+    exchange_write(n_r - 1, carry);
+  }
 }
 
 // Square tiles: MinBlocks CTAs per SM through the register cap of the launch bounds.
@@ -807,8 +897,10 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   const T* sv = Tab<T>::s(L);
   const T* geo = Tab<T>::geo(L);
   const T* lay = Tab<T>::lay(L);
+  // kernels with more than 48 KB of shared memory (FP64 A on wide tiles) got their attribute
+  // from prepare_tile_kernels() when the first mesh was created
 #define TN_TILE_LAUNCH(KERNEL, TIv, TJv, EKv)                                                                   \
-  KERNEL<T, Op, TIv, TJv, FLAGS, EPI, EKv><<<grid, (TIv + 1) * (TJv + 1), 0, st>>>(                             \
+  KERNEL<T, Op, TIv, TJv, FLAGS, EPI, EKv><<<grid, (TIv + 1) * (TJv + 1), TileSmem<T, Op, TIv, TJv>::bytes, st>>>( \
       D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E)
   // 16-bit viscosity (FP32 path only): only full tiles (levels with N >= 16 store it)
   if constexpr (Op::USES_ETA && sizeof(T) == 4) {
@@ -916,39 +1008,6 @@ __global__ void k_interface_epi(Dims D, int n_groups, const int* __restrict__ gp
 // -2/3 g g^T, the symmetric-gradient term g g^T, so 1/3 with div_term, 1 without).
 // Only the two boundary node layers are handled here (the tile kernel with OpDiag writes the
 // interior layers): blocks = 10 * 2 * (N+1)^2 threads, layer 0 and layer n_r - 1.
-// Thread per lateral triangle: the OpDiag factors P_ad (q = 3a + d), R_ad (q = 9 + 3a + d), Q_d
-// (q = 18 + d), then 2 (|m0 + m1|^2 + |m0|^2 + |m1|^2) (q = 21) and 6 |m2|^2 (q = 22) of the
-// hourglass eps, from the FP64 geometry; written to the FP64 and the FP32 table.
-__global__ void k_diag_coef(int64_t n_tri, const double* __restrict__ geo, int div_term, double* c64, float* c32) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_tri) return;
-  double m[3][3];
-  for (int k = 0; k < 3; ++k)
-    for (int x = 0; x < 3; ++x) m[k][x] = geo[(3 * k + x) * n_tri + t];
-  const double c = div_term ? 1.0 / 3.0 : 1.0;
-  double l[3][3];
-  for (int x = 0; x < 3; ++x) l[0][x] = -(m[0][x] + m[1][x]), l[1][x] = m[0][x], l[2][x] = m[1][x];
-  double v[kDiagCoef] = {};
-  const double m22 = m[2][0] * m[2][0] + m[2][1] * m[2][1] + m[2][2] * m[2][2];
-  for (int a = 0; a < 3; ++a) {
-    const double ll = l[a][0] * l[a][0] + l[a][1] * l[a][1] + l[a][2] * l[a][2];
-    const double lm = l[a][0] * m[2][0] + l[a][1] * m[2][1] + l[a][2] * m[2][2];
-    for (int d = 0; d < 3; ++d) {
-      v[3 * a + d] = ll + c * l[a][d] * l[a][d];
-      v[9 + 3 * a + d] = lm + c * l[a][d] * m[2][d];
-    }
-  }
-  for (int d = 0; d < 3; ++d) v[18 + d] = m22 + c * m[2][d] * m[2][d];
-  double L = 0;
-  for (int x = 0; x < 3; ++x) {
-    const double s01 = m[0][x] + m[1][x];
-    L += s01 * s01 + m[0][x] * m[0][x] + m[1][x] * m[1][x];
-  }
-  v[21] = 2.0 * L;
-  v[22] = 6.0 * m22;
-  for (int q = 0; q < kDiagCoef; ++q) c64[q * n_tri + t] = v[q], c32[q * n_tri + t] = (float)v[q];
-}
-
 // Hourglass-control part of the node block of wedge-local lateral node a (side 0: the node is on
 // the wedge's bottom layer): eps n_a (k9 - zeta / 3)^2 times the identity (see OpDiag).
 template <typename T>
@@ -1615,20 +1674,6 @@ __global__ void k_eta_16(Dims D, const double* __restrict__ eta, uint16_t* __res
   }
 }
 
-cudaError_t launch_diag_coef(Level& L, int div_term) {
-  if (!L.dcoef64) {
-    cudaError_t e = cudaMalloc((void**)&L.dcoef64, sizeof(double) * kDiagCoef * L.n_tri);
-    if (e != cudaSuccess) return e;
-    e = cudaMalloc((void**)&L.dcoef32, sizeof(float) * kDiagCoef * L.n_tri);
-    if (e != cudaSuccess) return e;
-  }
-  k_diag_coef<<<nblk(L.n_tri, 256), 256>>>(L.n_tri, L.geo64, div_term, L.dcoef64, L.dcoef32);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  L.dcoef_div = div_term;
-  return cudaDeviceSynchronize();
-}
-
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st) {
   if (L.eta_kind == TN_ETA_F32) return launch_to_f32(L.eta64, L.eta32, L.n_wedges, st);
   if (L.eta_kind == TN_ETA_BF16)
@@ -1675,6 +1720,27 @@ TN_INST(float)
                                              T* const*, cudaStream_t, const int*);
 #if TN_PART == 0 || TN_PART == 2
 TN_INST_A(double)
+
+// Opt the tile kernels that need more than 48 KB of shared memory (FP64 A on 16 x 32 tiles,
+// every epilogue, with and without hourglass control) into their dynamic size.
+template <bool HG, int EPI>
+cudaError_t set_wide_a_attr() {
+  using Op = OpA<double, HG>;
+  constexpr size_t sh = TileSmem<double, Op, TILE, 2 * TILE>::bytes;
+  if (sh <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k_tile_wide<double, Op, TILE, 2 * TILE, PROJ_IN | PROJ_OUT | ADD_ID, EPI, TN_ETA_F32>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+}
+
+cudaError_t prepare_tile_kernels() {
+  const cudaError_t e[8] = {set_wide_a_attr<false, EPI_NONE>(), set_wide_a_attr<false, EPI_RESID>(),
+                            set_wide_a_attr<false, EPI_CHEB1>(), set_wide_a_attr<false, EPI_CHEB2>(),
+                            set_wide_a_attr<true, EPI_NONE>(),  set_wide_a_attr<true, EPI_RESID>(),
+                            set_wide_a_attr<true, EPI_CHEB1>(),  set_wide_a_attr<true, EPI_CHEB2>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
 #endif
 #if TN_PART == 0 || TN_PART == 3
 TN_INST_A(float)

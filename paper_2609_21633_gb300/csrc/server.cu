@@ -91,14 +91,16 @@ struct Shape {
 };
 
 // Device bytes a resident hierarchy may hold (tables, viscosity, multigrid and FGMRES(30)
-// workspaces in FP64 and FP32), estimated from the finest node layout.
-size_t footprint(const Shape& s) {
+// workspaces), estimated from the finest node layout.  Per layout entry and component: FP64
+// solves hold 63 Krylov and about 30 multigrid / work vectors in FP64; mixed solves hold them in
+// FP32 plus 4 FP64 work vectors.  The coarser levels add about 1/7; geometry, viscosity and
+// masks about 40 bytes.
+size_t footprint(const Shape& s, int mode) {
   const int N = 1 << s.l;
   const size_t P = (size_t)(N + 4) / 4 * 4;
   const size_t n0 = (size_t)10 * s.nr * (N + 1) * P;
-  // per layout entry: 3 components x (63 Krylov + 30 multigrid / work vectors) x (8 + 4) bytes,
-  // plus geometry, viscosity and masks; the coarser levels add about 1/7.
-  return (size_t)((double)n0 * 3.0 * 93.0 * 12.0 * 8.0 / 7.0) + ((size_t)64 << 20);
+  const double per = mode == TN_SOLVE_MIXED ? 3.0 * (93.0 * 4.0 + 4.0 * 8.0) : 3.0 * 93.0 * 8.0;
+  return (size_t)((double)n0 * (per * 8.0 / 7.0 + 40.0)) + ((size_t)64 << 20);
 }
 
 struct Job {
@@ -149,12 +151,12 @@ int acquire_locked(tn_server* S, const Shape& s, tn_mesh** out, std::vector<tn_m
       return 1;
     }
   }
-  const size_t need = footprint(s);
+  const size_t need = footprint(s, S->opts.mode);
   while (S->reserved + need > S->budget && !S->idle.empty()) {
     size_t lru = 0;
     for (size_t q = 1; q < S->idle.size(); ++q)
       if (S->idle[q].last_use < S->idle[lru].last_use) lru = q;
-    S->reserved -= footprint(S->idle[lru].shape);
+    S->reserved -= footprint(S->idle[lru].shape, S->opts.mode);
     to_free.push_back(S->idle[lru].mesh);
     S->idle.erase(S->idle.begin() + lru);
   }
@@ -226,7 +228,7 @@ void run_job(tn_server* S, Job* J, tn_mesh* mesh, cudaStream_t st) {
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (mesh) S->idle.push_back(Pooled{mesh, Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, ++S->use_clock});
-    else S->reserved -= footprint(Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out});
+    else S->reserved -= footprint(Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, S->opts.mode);
     J->res.t_end = S->now();
     J->res.state = 2;
     J->done = true;
@@ -338,7 +340,7 @@ tn_status tn_server_submit(tn_server* S, const tn_request* req, uint64_t* ticket
     J->res.state = 0;
     S->jobs[J->ticket] = J;
     const Shape s{req->lateral_level, req->radial_layers, req->r_in, req->r_out};
-    if (footprint(s) > S->budget) {  // can never be admitted
+    if (footprint(s, S->opts.mode) > S->budget) {  // can never be admitted
       J->res.status = TN_ENOMEM;
       J->res.state = 2;
       J->res.t_start = J->res.t_end = J->res.t_submit;

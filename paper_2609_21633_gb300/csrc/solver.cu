@@ -930,10 +930,11 @@ void alloc_kvec(MGState* m, const tn_mesh* mesh, KVec<T>& v) {
 
 template <typename T>
 void ensure_krylov(MGState* m, const tn_mesh* mesh, int restart) {
+  // restart 0: only V[0] and the work vectors (the FP64 side of the mixed mode)
   PrecState<T>& P = ps<T>(m);
   if ((int)P.Z.size() >= restart && !P.V.empty()) return;
-  P.V.resize(restart + 1);
-  P.Z.resize(restart);
+  if ((int)P.V.size() < restart + 1) P.V.resize(restart + 1);
+  if ((int)P.Z.size() < restart) P.Z.resize(restart);
   for (auto& v : P.V)
     if (!v.p) alloc_kvec<T>(m, mesh, v);
   for (auto& v : P.Z)
@@ -1209,9 +1210,9 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
         continue;
       }
       Level* L = new Level();
-      tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out, mesh->eta_storage);
+      tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out, mesh->eta_storage,
+                                  mesh->div_term);
       L->hg_kappa = mesh->hg_kappa;
-      if (cs == TN_OK && launch_diag_coef(*L, mesh->div_term) != cudaSuccess) cs = TN_ECUDA;
       m->owned_levels.push_back(L);
       if (cs != TN_OK) {
         mesh->mg = m;
@@ -1312,19 +1313,17 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   auto t0 = std::chrono::steady_clock::now();
   const bool mixed = o.mode == TN_SOLVE_MIXED;
   tn_status s;
-  if (!mesh->mg || !mesh->mg->p64.ready) {
-    s = tn_mg_setup(mesh, TN_F64, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
-    if (s != TN_OK) return s;
-  }
-  if (mixed && !mesh->mg->p32.ready) {
-    s = tn_mg_setup(mesh, TN_F32, &mesh->mg->opts, nullptr, stream);
+  // the mixed mode needs only the FP32 multigrid and, in FP64, the residual work vectors
+  const tn_prec mg_prec = mixed ? TN_F32 : TN_F64;
+  if (!mesh->mg || !(mixed ? mesh->mg->p32.ready : mesh->mg->p64.ready)) {
+    s = tn_mg_setup(mesh, mg_prec, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
     if (s != TN_OK) return s;
   }
   g_err = cudaSuccess;
   MGState* m = mesh->mg;
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
-  ensure_krylov<double>(m, mesh, o.restart);
+  ensure_krylov<double>(m, mesh, mixed ? 0 : o.restart);
   if (mixed) ensure_krylov<float>(m, mesh, o.restart);
   if (g_err != cudaSuccess) {
     set_error("tn_stokes_solve: workspace allocation failed");
