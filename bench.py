@@ -33,9 +33,10 @@ LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, 
 # per wedge 33 (differences) + 9 (scaling) + 45 (grad u) + 20 (stress) + 54 (stress x M^-T)
 # + 21 (test-gradient combination) + 18 (accumulation) = 200.
 A_FLOPS_PER_CELL = 400.0
-# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 164.5 MB for
-# 2,621,440 cells), scaled to the bench size by cells; None once the kernel changes.
-A_TRAFFIC_BYTES_PER_CELL = None
+# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 206.4 MB for
+# 2,621,440 cells, 16 x 32 tiles with shared corner sums), scaled to the bench size by cells; None
+# once the kernel changes.
+A_TRAFFIC_BYTES_PER_CELL = 206.4e6 / 2621440
 # Hourglass-control coefficient of the solves and the serving stream that use it.
 HG_KAPPA = 0.3
 # Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
@@ -59,6 +60,9 @@ def parse():
                     help="do not run the Stokes-solve and serving measurements after the operator steps")
     ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=64,
                     help="requests of the seeded serving stream measured after the solves (the full stream is 256)")
+    ap.add_argument("--largest-shell", dest="largest_shell", action="store_true",
+                    help="instead of the operator step: one Stokes solve on the largest single-GPU shell "
+                         "(level 8, 257 layers) and its resident device memory")
     return ap.parse_args()
 
 
@@ -285,10 +289,42 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1)
         tn.tn_server_destroy(srv)
 
 
+def largest_shell(tn, torch, repeats=2):
+    """Largest single-GPU coupled-run shell: lateral level 8 (257 x 257 nodes per diamond), 257
+    radial layers (505 M velocity DoFs), Ra = 1e5, temperature viscosity contrast 1e2, free-slip;
+    one mixed-precision Stokes solve to 1e-8 (FP32 inner FGMRES(30) / V-cycle, FP64 refinement,
+    hourglass control kappa = 0.3, BF16 viscosity), through the serving API, which builds the
+    temperature field on the device.  Reports each request's time (mesh creation, set-up and
+    solve; the second request reuses the resident hierarchy) and the device memory it holds."""
+    free0, total = torch.cuda.mem_get_info()
+    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=1, memory_fraction=0.95, hg_kappa=HG_KAPPA,
+                                                        eta_storage=tn.TN_ETA_BF16))
+    out = {"workload": "icosahedral shell l=8 (N=256), 257 radial layers, Ra=1e5, viscosity contrast 1e2",
+           "velocity_dofs": dof_counts(8, 257)[0], "pressure_dofs": dof_counts(8, 257)[1],
+           "device_memory_gb": total / 1e9, "runs": []}
+    try:
+        for _ in range(repeats):
+            t = tn.tn_server_submit(srv, 8, 257, math.log(100.0), 1e5, 3, 2, 0.01)
+            r = tn.tn_server_wait(srv, t)
+            free1, _ = torch.cuda.mem_get_info()
+            out["runs"].append({"status": r["status"], "iterations": r["iterations"], "refinements": r["refinements"],
+                                "rel_residual": r["rel_residual"], "seconds": r["t_end"] - r["t_start"],
+                                "resident_gb": (free0 - free1) / 1e9})
+    finally:
+        tn.tn_server_destroy(srv)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.largest_shell:
+        import torch
+        import paper_2609_21633_gb300 as tn
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(largest_shell(tn, torch)))
+        return 0
     import torch
     import paper_2609_21633_gb300 as tn
     from paper_2609_21633_gb300 import inputs

@@ -298,6 +298,160 @@ struct OpA {
   }
 };
 
+// Packed FP32 pairs (sm_100+ f32x2 instructions): one instruction per pair halves the issue
+// slots of the FP32 element arithmetic, which bounds the FP32 tile kernels.
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// FP32 viscous block without hourglass control: the same arithmetic as OpA with the two wedges
+// of the cell as the two lanes of packed f32x2 values (x = W0, y = W1).  W0's corners (c0, c1,
+// c2) are (00, 10, 01) and W1's are (11, 01, 10), so the lane pairs are (00, 11), (10, 01), (01, 10).
+template <>
+struct OpA<float, false> {
+  static constexpr int NIN = 3, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
+  struct Col {
+    float2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
+  };
+  int div_term;
+  float hgk;
+  __device__ __forceinline__ Col column(const float (&Mi)[2][9], const float (&dM)[2], int) const {
+    Col c;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) c.M[q] = p2(Mi[0][q], Mi[1][q]);
+    c.dM = p2(dM[0], dM[1]);
+    return c;
+  }
+  __device__ __forceinline__ void cell(const float (&s)[4][3], const float (&dd)[4][3], const float (&)[2][9],
+                                       const float (&)[2], const float* lc, const float (&eta)[2],
+                                       float (&accb)[4][3], float (&acct)[4][3], const Col& col) const {
+    const float2 r = p2(lc[4], lc[4]);
+    const float2* M = col.M;
+    const float2 mr[3] = {mul2(r, M[6]), mul2(r, M[7]), mul2(r, M[8])};
+    float2 G[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 s0 = p2(s[0][c], s[3][c]), s1 = p2(s[1][c], s[2][c]), s2 = p2(s[2][c], s[1][c]);
+      const float2 ax = sub2(s1, s0), ay = sub2(s2, s0);
+      const float2 az = add2(add2(p2(dd[0][c], dd[3][c]), p2(dd[1][c], dd[2][c])), p2(dd[2][c], dd[1][c]));
+#pragma unroll
+      for (int x = 0; x < 3; ++x) G[c][x] = fma2(ax, M[x], fma2(ay, M[3 + x], mul2(az, mr[x])));
+    }
+    const float2 ve = mul2(mul2(p2(lc[5], lc[5]), col.dM), p2(eta[0], eta[1]));
+    const float2 ve2 = add2(ve, ve);
+    float2 S[3][3];
+    if (div_term) {
+      const float2 vt = mul2(mul2(ve, p2(-2.f / 3.f, -2.f / 3.f)), add2(add2(G[0][0], G[1][1]), G[2][2]));
+      S[0][0] = fma2(ve2, G[0][0], vt), S[1][1] = fma2(ve2, G[1][1], vt), S[2][2] = fma2(ve2, G[2][2], vt);
+    } else {
+      S[0][0] = mul2(ve2, G[0][0]), S[1][1] = mul2(ve2, G[1][1]), S[2][2] = mul2(ve2, G[2][2]);
+    }
+    S[0][1] = S[1][0] = mul2(ve, add2(G[0][1], G[1][0]));
+    S[0][2] = S[2][0] = mul2(ve, add2(G[0][2], G[2][0]));
+    S[1][2] = S[2][1] = mul2(ve, add2(G[1][2], G[2][1]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 h0 = fma2(S[c][0], M[0], fma2(S[c][1], M[1], mul2(S[c][2], M[2])));
+      const float2 h1 = fma2(S[c][0], M[3], fma2(S[c][1], M[4], mul2(S[c][2], M[5])));
+      const float2 h2 = fma2(S[c][0], mr[0], fma2(S[c][1], mr[1], mul2(S[c][2], mr[2])));
+      // X at corners (00, 11) = -(h0 + h1) per lane; at (10, 01) = (h0.x + h1.y, h1.x + h0.y)
+      const float2 x03 = add2(h0, h1);
+      const float2 x12 = add2(p2(h0.x, h1.x), p2(h1.y, h0.y));
+      // top-minus-bottom part: h2 at (00, 11), h2.x + h2.y at (10, 01)
+      const float hs = h2.x + h2.y;
+      const float2 h12 = p2(hs, hs);
+      const float2 b03 = add2(x03, h2), t03 = sub2(h2, x03);  // -(X) -/+ h2 negated: b = -(X - h2)
+      const float2 b12 = sub2(x12, h12), t12 = add2(x12, h12);
+      accb[0][c] = -b03.x, acct[0][c] = t03.x;
+      accb[3][c] = -b03.y, acct[3][c] = t03.y;
+      accb[1][c] = b12.x, acct[1][c] = t12.x;
+      accb[2][c] = b12.y, acct[2][c] = t12.y;
+    }
+  }
+};
+
+// FP32 viscous block with hourglass control, packed as OpA<float, false>; the control follows
+// the scalar OpA<T, true> (alpha_m, b_m, the H[:,0/1] corrections and the per-corner
+// top-minus-bottom parts), lane x = W0, lane y = W1.
+template <>
+struct OpA<float, true> {
+  static constexpr int NIN = 3, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
+  struct Col {
+    float2 M[9], dM, eL, eR;
+  };
+  int div_term;
+  float hgk;
+  __device__ __forceinline__ Col column(const float (&Mi)[2][9], const float (&dM)[2], int) const {
+    Col c;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) c.M[q] = p2(Mi[0][q], Mi[1][q]);
+    c.dM = p2(dM[0], dM[1]);
+    const HgCol<float> h = hg_column(Mi, dM);
+    c.eL = p2(h.eL[0], h.eL[1]), c.eR = p2(h.eR[0], h.eR[1]);
+    return c;
+  }
+  __device__ __forceinline__ void cell(const float (&s)[4][3], const float (&dd)[4][3], const float (&)[2][9],
+                                       const float (&)[2], const float* lc, const float (&eta)[2],
+                                       float (&accb)[4][3], float (&acct)[4][3], const Col& col) const {
+    const float2 r = p2(lc[4], lc[4]), k9 = p2(lc[8], lc[8]), nk9 = p2(-lc[8], -lc[8]);
+    const float2 third = p2(1.f / 3.f, 1.f / 3.f);
+    const float2* M = col.M;
+    const float2 mr[3] = {mul2(r, M[6]), mul2(r, M[7]), mul2(r, M[8])};
+    float2 G[3][3], al1[3], al2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 s0 = p2(s[0][c], s[3][c]), s1 = p2(s[1][c], s[2][c]), s2 = p2(s[2][c], s[1][c]);
+      const float2 d1 = p2(dd[1][c], dd[2][c]), d2 = p2(dd[2][c], dd[1][c]);
+      const float2 ax = sub2(s1, s0), ay = sub2(s2, s0);
+      const float2 az = add2(add2(p2(dd[0][c], dd[3][c]), d1), d2);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) G[c][x] = fma2(ax, M[x], fma2(ay, M[3 + x], mul2(az, mr[x])));
+      const float2 a3 = mul2(az, third);
+      al1[c] = fma2(nk9, sub2(add2(ax, ax), ay), sub2(d1, a3));
+      al2[c] = fma2(nk9, sub2(add2(ay, ay), ax), sub2(d2, a3));
+    }
+    const float2 ve = mul2(mul2(p2(lc[5], lc[5]), col.dM), p2(eta[0], eta[1]));
+    const float2 ve2 = add2(ve, ve);
+    float2 S[3][3];
+    if (div_term) {
+      const float2 vt = mul2(mul2(ve, p2(-2.f / 3.f, -2.f / 3.f)), add2(add2(G[0][0], G[1][1]), G[2][2]));
+      S[0][0] = fma2(ve2, G[0][0], vt), S[1][1] = fma2(ve2, G[1][1], vt), S[2][2] = fma2(ve2, G[2][2], vt);
+    } else {
+      S[0][0] = mul2(ve2, G[0][0]), S[1][1] = mul2(ve2, G[1][1]), S[2][2] = mul2(ve2, G[2][2]);
+    }
+    S[0][1] = S[1][0] = mul2(ve, add2(G[0][1], G[1][0]));
+    S[0][2] = S[2][0] = mul2(ve, add2(G[0][2], G[2][0]));
+    S[1][2] = S[2][1] = mul2(ve, add2(G[1][2], G[2][1]));
+    const float2 eps = mul2(mul2(p2(hgk, hgk), p2(eta[0], eta[1])),
+                            fma2(p2(lc[5], lc[5]), col.eL, mul2(p2(lc[9], lc[9]), col.eR)));
+    const float2 nek = mul2(eps, nk9), e3 = mul2(eps, third);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float2 b1 = sub2(add2(al1[c], al1[c]), al2[c]), b2 = sub2(add2(al2[c], al2[c]), al1[c]);
+      const float2 h0 = fma2(nek, b1, fma2(S[c][0], M[0], fma2(S[c][1], M[1], mul2(S[c][2], M[2]))));
+      const float2 h1 = fma2(nek, b2, fma2(S[c][0], M[3], fma2(S[c][1], M[4], mul2(S[c][2], M[5]))));
+      const float2 h2 = fma2(S[c][0], mr[0], fma2(S[c][1], mr[1], mul2(S[c][2], mr[2])));
+      const float2 v1 = mul2(e3, b1), v2 = mul2(e3, b2);
+      const float2 y0 = sub2(h2, add2(v1, v2)), y1 = add2(h2, v1), y2 = add2(h2, v2);
+      // X: (00, 11) = -(h0 + h1); (10, 01) = (h0.x + h1.y, h1.x + h0.y).  Y: (00, 11) = y0;
+      // (10, 01) = (y1.x + y2.y, y2.x + y1.y).
+      const float2 x03 = add2(h0, h1);
+      const float2 x12 = add2(p2(h0.x, h1.x), p2(h1.y, h0.y));
+      const float2 y12 = add2(p2(y1.x, y2.x), p2(y2.y, y1.y));
+      const float2 b03 = add2(x03, y0), t03 = sub2(y0, x03);
+      const float2 b12 = sub2(x12, y12), t12 = add2(x12, y12);
+      accb[0][c] = -b03.x, acct[0][c] = t03.x;
+      accb[3][c] = -b03.y, acct[3][c] = t03.y;
+      accb[1][c] = b12.x, acct[1][c] = t12.x;
+      accb[2][c] = b12.y, acct[2][c] = t12.y;
+    }
+  }
+};
+
 // Fine-level divergence: each of the six nodes of a wedge gets -V tr(grad u)(q_c) / 6
 // (pressure test function psi = N_n with N_n(q_c) = 1/6); tr grad u = w0 tr G'.
 template <typename T>
