@@ -326,6 +326,92 @@ __global__ void k_cg_dir(int64_t n, const double* __restrict__ S, Ptr4<T> z, MPt
   const T be = (T)S[S_BETA];
   for (int c = 0; c < 3; ++c) p.c[c][i] = z.c[c][i] + be * p.c[c][i];
 }
+// Coarse CG on a small coarsest level (n <= SMALL_CG): one block runs the whole vector part of a
+// CG step, so a step is the operator apply plus one launch.  Sums over the masked (unique)
+// entries in FP64, in a fixed order (thread-strided partial sums, then a tree over the block).
+constexpr int SMALL_CG = 32768;
+constexpr int SB = 1024;  // threads of the single-block CG kernels
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();  // sh may still be read from a previous sum
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < SB / 32; ++w) s += sh[w];  // every thread, same order
+  return s;
+}
+
+// r = b, z = D^-1 r, p = z, x = 0, rz0 = (r, z); flag = 0 unless rz0 = 0
+template <typename T>
+__global__ void __launch_bounds__(SB) k_cg_start_small(int64_t n, const uint8_t* __restrict__ mask, Ptr4<T> b,
+                                                       B6<T> binv, MPtr4<T> r, MPtr4<T> z, MPtr4<T> p, MPtr4<T> x,
+                                                       double* S, int* flag) {
+  __shared__ double sh[SB / 32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += SB) {
+    T rr[3] = {b.c[0][i], b.c[1][i], b.c[2][i]}, zz[3];
+    bmul(binv, i, rr, zz);
+    T d = (T)0;
+    for (int c = 0; c < 3; ++c) {
+      r.c[c][i] = rr[c], z.c[c][i] = zz[c], p.c[c][i] = zz[c], x.c[c][i] = (T)0;
+      d += rr[c] * zz[c];
+    }
+    if (mask[i]) acc += (double)d;
+  }
+  const double rz0 = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    S[S_RZ0] = rz0, S[S_RZ] = rz0;
+    *flag = rz0 > 0.0 ? 0 : 1;
+  }
+}
+
+// one CG step after q = K p: alpha = (r, z) / (p, q); x += alpha p; r -= alpha q; z = D^-1 r;
+// beta = (r, z)_new / (r, z); p = z + beta p; flag once (r, z) <= tol2 (r0, z0) or at the last step
+template <typename T>
+__global__ void __launch_bounds__(SB) k_cg_step_small(int64_t n, const uint8_t* __restrict__ mask, MPtr4<T> p,
+                                                      Ptr4<T> q, B6<T> binv, MPtr4<T> x, MPtr4<T> r, MPtr4<T> z,
+                                                      double* S, int* flag, double tol2, int last) {
+  if (*flag) return;
+  __shared__ double sh[SB / 32];
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += SB) {
+    if (!mask[i]) continue;
+    T d = (T)0;
+    for (int c = 0; c < 3; ++c) d += p.c[c][i] * q.c[c][i];
+    acc += (double)d;
+  }
+  const double pq = block_sum(acc, sh);
+  const double rz = S[S_RZ];
+  const T al = (T)(rz / pq);
+  acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += SB) {
+    T rr[3], zz[3];
+    for (int c = 0; c < 3; ++c) {
+      x.c[c][i] += al * p.c[c][i];
+      rr[c] = r.c[c][i] - al * q.c[c][i];
+      r.c[c][i] = rr[c];
+    }
+    bmul(binv, i, rr, zz);
+    T d = (T)0;
+    for (int c = 0; c < 3; ++c) z.c[c][i] = zz[c], d += rr[c] * zz[c];
+    if (mask[i]) acc += (double)d;
+  }
+  const double rzn = block_sum(acc, sh);
+  const bool stop = !(rzn > tol2 * S[S_RZ0]) || last;
+  if (!stop) {
+    const T be = (T)(rzn / rz);
+    for (int64_t i = threadIdx.x; i < n; i += SB)
+      for (int c = 0; c < 3; ++c) p.c[c][i] = z.c[c][i] + be * p.c[c][i];
+  }
+  __syncthreads();  // every thread has read S[S_RZ] and S[S_RZ0]
+  if (threadIdx.x == 0) {
+    S[S_RZ] = rzn;
+    if (stop) *flag = 1;
+  }
+}
+
 __global__ void k_set_int(int* f, int v) { *f = v; }
 __global__ void k_cg_start(double* S, int* flag) {
   S[S_RZ] = S[S_RZ0];
@@ -633,6 +719,23 @@ void coarse_cg(MGState* m, const tn_mesh* mesh, int h, cudaStream_t st) {
   const int64_t n = L.n_layout;
   const bool proj = rotations_singular(mesh);
   if (proj) project_rotations<T>(m, L, C.b.mm(), st);
+  const double tol2s = m->opts.coarse_rtol * m->opts.coarse_rtol;
+  if (n <= SMALL_CG) {  // single-block vector kernels: two launches per CG step plus the apply
+    k_cg_start_small<T><<<1, SB, 0, st>>>(n, L.wmask, P4<T>(C.b.cc(), 3), C.bi(), M4<T>(C.r.mm(), 3),
+                                          M4<T>(C.d().mm(), 3), M4<T>(C.p.mm(), 3), M4<T>(C.x().mm(), 3), m->S,
+                                          m->flag);
+    ckl();
+    const int maxit = m->opts.coarse_max_iters;
+    for (int it = 0; it < maxit; ++it) {
+      apply_K_level<T>(mesh, h, C.p.cc(), C.t.mm(), st, m->flag);
+      k_cg_step_small<T><<<1, SB, 0, st>>>(n, L.wmask, M4<T>(C.p.mm(), 3), P4<T>(C.t.cc(), 3), C.bi(),
+                                           M4<T>(C.x().mm(), 3), M4<T>(C.r.mm(), 3), M4<T>(C.d().mm(), 3), m->S,
+                                           m->flag, tol2s, it == maxit - 1);
+      ckl();
+    }
+    if (proj) project_rotations<T>(m, L, C.x().mm(), st);
+    return;
+  }
   // r = b, z = D^-1 r (stored in d), p = z, x = 0
   k_axpby<T><<<nb(n), EB, 0, st>>>(n, 3, 1.0, P4<T>(C.b.cc(), 3), 0.0, M4<T>(C.r.mm(), 3));
   ckl();
