@@ -224,7 +224,7 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=
         tn.tn_buoyancy(m, Td, Ra, f)
         u = [torch.zeros_like(f[0]) for _ in range(3)]
         p = torch.zeros(pinfo["n_layout"], device=dev, dtype=torch.float64)
-        tn.tn_mg_setup(m, torch.float32 if mode == tn.TN_SOLVE_MIXED else torch.float64)
+        tn.tn_mg_setup(m, torch.float64 if mode == tn.TN_SOLVE_F64 else torch.float32)
         torch.cuda.synchronize()
         st = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(mode=mode), check=False)
         nv = 3 * info["n_unique_nodes"]
@@ -238,11 +238,12 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=
         tn.tn_mesh_destroy(m)
 
 
-def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1):
+def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1, mode=None):
     """Serving workload: seeded Stokes requests (lateral level U{3..6}, radial layers U{9,17,33,65},
     viscosity contrast log-uniform in [1, 1e4], temperature perturbation degree U{2..8}, order
-    U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), FP32 inner solves with FP64 refinement to 1e-8,
-    hourglass control kappa = hg_kappa, FP32-path viscosity storage eta_storage (1 = BF16).
+    U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), solved to 1e-8 by FP64 FGMRES with the FP32
+    preconditioner (mode, default TN_SOLVE_F64_PREC32), hourglass control kappa = hg_kappa,
+    FP32-path viscosity storage eta_storage (1 = BF16).
     Phase 1 submits all requests at once (saturated throughput); phase 2 submits them with
     Poisson arrivals at `load` x the saturated rate and reports latency percentiles."""
     rng = np.random.default_rng(seed)
@@ -256,7 +257,9 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1)
         amp = float(rng.uniform(0.01, 0.05))
         reqs.append(dict(lateral_level=l, radial_layers=nr, E=math.log(contrast), Ra=7e3, t_degree=deg,
                          t_order=order, t_amplitude=amp))
-    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4, hg_kappa=hg_kappa, eta_storage=eta_storage))
+    mode = tn.TN_SOLVE_F64_PREC32 if mode is None else mode
+    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4, hg_kappa=hg_kappa, eta_storage=eta_storage,
+                                                        mode=mode))
     try:
         tickets = [tn.tn_server_submit(srv, **q) for q in reqs]
         res = [tn.tn_server_wait(srv, t) for t in tickets]
@@ -283,7 +286,9 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1)
                 "poisson_rate_per_s": rate, "solves_per_s": n_req / span, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "converged": ok,
                 "max_rel_residual": max(r["rel_residual"] for r in res), "median_iterations": float(np.median(its)),
-                "max_active": 4, "mode": "FP32 inner + FP64 refinement, rtol 1e-8",
+                "max_active": 4,
+                "mode": {0: "FP64", 1: "FP32 inner + FP64 refinement", 2: "FP64 FGMRES + FP32 preconditioner"}[mode]
+                + ", rtol 1e-8",
                 "hg_kappa": hg_kappa, "eta_storage": ["f32", "bf16", "f16"][eta_storage]}
     finally:
         tn.tn_server_destroy(srv)
@@ -483,6 +488,10 @@ def main():
                 hbf, tbf = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_MIXED, eta_storage=tn.TN_ETA_BF16,
                                       hg_kappa=HG_KAPPA)
                 hbf["u_rel_diff_vs_fp64"] = float(np.linalg.norm(tbf[0] - t64[0]) / np.linalg.norm(t64[0]))
+                # FP64 FGMRES with the FP32 preconditioner (BF16 viscosity in it)
+                hpc, tpc = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64_PREC32,
+                                      eta_storage=tn.TN_ETA_BF16, hg_kappa=HG_KAPPA)
+                hpc["u_rel_diff_vs_fp64"] = float(np.linalg.norm(tpc[0] - t64[0]) / np.linalg.norm(t64[0]))
                 hbf["p_rel_diff_vs_fp64"] = float(np.linalg.norm(tbf[1] - t64[1]) / np.linalg.norm(t64[1]))
                 # discretisation change of the control: its FP64 solution against the plain one
                 h64["u_rel_diff_vs_plain"] = float(np.linalg.norm(t64[0] - s64[0]) / np.linalg.norm(s64[0]))
@@ -490,6 +499,7 @@ def main():
                                 "mixed_speedup": r64["seconds"] / rmx["seconds"],
                                 "mixed_bf16_eta_speedup": r64["seconds"] / rbf["seconds"],
                                 "hg%.1f_fp64" % HG_KAPPA: h64, "hg%.1f_mixed_bf16_eta" % HG_KAPPA: hbf,
+                                "hg%.1f_fp64_prec32_bf16_eta" % HG_KAPPA: hpc,
                                 "hg_mixed_bf16_eta_speedup_vs_plain_fp64": r64["seconds"] / hbf["seconds"]}
             line["solves"] = solves
             if args.serve_requests > 0:

@@ -269,11 +269,15 @@ tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r_dev, void*
  * surfaces are free-slip; the pressure mean is not projected (under free-slip the constant
  * pressure is not an exact null vector of the discrete system).
  * Mode TN_SOLVE_MIXED: FP64 iterative refinement x += ||r|| d with r = b - K x in FP64 and d
- * from an FP32 FGMRES / FP32 V-cycle solve of K d = r / ||r|| to inner_rtol.
+ * from an FP32 FGMRES / FP32 V-cycle solve of K d = r / ||r|| to inner_rtol.  Holds the Krylov
+ * basis in FP32 (the low-memory mode for the largest shells).
+ * Mode TN_SOLVE_F64_PREC32: FP64 FGMRES (FP64 operator, Krylov basis and orthogonalisation)
+ * whose preconditioner P^-1 runs in FP32 on the normalised Krylov vector (FP32 Schur step,
+ * B^T and V-cycle); FGMRES admits the inexact preconditioner.
  * u, p are outputs (zero initial guess); g may be NULL (zero).  Synchronous.
  * Returns TN_ENOTCONVERGED if ||b - K x|| / ||b|| > rtol on return (stats still filled).
  * ---------------------------------------------------------------------------------------- */
-typedef enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED = 1 } tn_solve_mode;
+typedef enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED = 1, TN_SOLVE_F64_PREC32 = 2 } tn_solve_mode;
 typedef struct {
   double rtol;          /* 1e-8 relative residual */
   int restart;          /* 30 (1..30) */

@@ -59,7 +59,7 @@ class tn_solve_stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("converged", ctypes.c_int)]
 
 
-TN_SOLVE_F64, TN_SOLVE_MIXED = 0, 1
+TN_SOLVE_F64, TN_SOLVE_MIXED, TN_SOLVE_F64_PREC32 = 0, 1, 2
 
 
 class tn_server_opts(ctypes.Structure):

@@ -1110,9 +1110,30 @@ void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStr
 // Solves K x = b from the given x; stops when ||b - K x|| <= abstol (recurrence estimate,
 // confirmed by the true residual at every restart) or after max_iters.  Returns the
 // iterations used; *res gets the final true residual norm.
+// FP64 Krylov vector -> FP32 preconditioner -> FP64 (mode TN_SOLVE_F64_PREC32): the vector is
+// unit-norm, so FP32 holds it without scaling.
+void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<double>& z, cudaStream_t st) {
+  PrecState<float>& F = m->p32;
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  for (int c = 0; c < 3; ++c) {
+    k_convert<double, float><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, r.u[c], F.ir_r.u[c], 1.0);
+    ckl();
+  }
+  k_convert<double, float><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, r.p, F.ir_r.p, 1.0);
+  ckl();
+  apply_prec<float>(m, mesh, F.ir_r, F.ir_c, st);
+  for (int c = 0; c < 3; ++c) {
+    k_convert<float, double><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, F.ir_c.u[c], z.u[c], 1.0);
+    ckl();
+  }
+  k_convert<float, double><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, F.ir_c.p, z.p, 1.0);
+  ckl();
+}
+
 template <typename T>
 int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double abstol, int restart, int max_iters,
-           double* res, cudaStream_t st) {
+           double* res, cudaStream_t st, bool prec32 = false) {
   PrecState<T>& P = ps<T>(m);
   ensure_krylov<T>(m, mesh, restart);
   int its = 0;
@@ -1133,7 +1154,12 @@ int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double absto
     g[0] = beta;
     int j = 0;
     for (; j < restart && its < max_iters; ++j) {
-      apply_prec<T>(m, mesh, P.V[j], P.Z[j], st);
+      if constexpr (sizeof(T) == 8) {
+        if (prec32) apply_prec_f32(m, mesh, P.V[j], P.Z[j], st);
+        else apply_prec<T>(m, mesh, P.V[j], P.Z[j], st);
+      } else {
+        apply_prec<T>(m, mesh, P.V[j], P.Z[j], st);
+      }
       apply_K<T>(m, mesh, P.Z[j], P.w, st);
       std::vector<const KVec<T>*> vb(j + 1);
       for (int i = 0; i <= j; ++i) vb[i] = &P.V[i];
@@ -1408,7 +1434,8 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   tn_solve_opts o;
   tn_solve_default_opts(&o);
   if (opts) o = *opts;
-  if (o.restart < 1 || o.restart > MAX_RESTART || !(o.rtol > 0) || o.max_iters < 1) {
+  if (o.restart < 1 || o.restart > MAX_RESTART || !(o.rtol > 0) || o.max_iters < 1 ||
+      (o.mode != TN_SOLVE_F64 && o.mode != TN_SOLVE_MIXED && o.mode != TN_SOLVE_F64_PREC32)) {
     set_error("tn_stokes_solve: invalid options (restart must be in [1, 30])");
     return TN_EINVAL;
   }
@@ -1416,10 +1443,12 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   auto t0 = std::chrono::steady_clock::now();
   const bool mixed = o.mode == TN_SOLVE_MIXED;
   tn_status s;
-  // the mixed mode needs only the FP32 multigrid and, in FP64, the residual work vectors
-  const tn_prec mg_prec = mixed ? TN_F32 : TN_F64;
-  if (!mesh->mg || !(mixed ? mesh->mg->p32.ready : mesh->mg->p64.ready)) {
-    s = tn_mg_setup(mesh, mg_prec, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
+  // the mixed modes need only the FP32 multigrid; the refinement mode keeps only the residual
+  // work vectors in FP64, the FP32-preconditioner mode the FP64 Krylov basis
+  const bool prec32 = o.mode == TN_SOLVE_F64_PREC32;
+  const bool mg32 = mixed || prec32;
+  if (!mesh->mg || !(mg32 ? mesh->mg->p32.ready : mesh->mg->p64.ready)) {
+    s = tn_mg_setup(mesh, mg32 ? TN_F32 : TN_F64, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
     if (s != TN_OK) return s;
   }
   g_err = cudaSuccess;
@@ -1428,6 +1457,7 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   const Level& L1 = mesh->lv[1];
   ensure_krylov<double>(m, mesh, mixed ? 0 : o.restart);
   if (mixed) ensure_krylov<float>(m, mesh, o.restart);
+  if (prec32) ensure_krylov<float>(m, mesh, 0);
   if (g_err != cudaSuccess) {
     set_error("tn_stokes_solve: workspace allocation failed");
     return TN_ENOMEM;
@@ -1448,7 +1478,7 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   double res = bnorm;
   if (bnorm > 0) {
     if (!mixed) {
-      its = fgmres<double>(m, mesh, b, x, o.rtol * bnorm, o.restart, o.max_iters, &res, st);
+      its = fgmres<double>(m, mesh, b, x, o.rtol * bnorm, o.restart, o.max_iters, &res, st, prec32);
     } else {
       // FP64 iterative refinement around FP32 FGMRES / V-cycle inner solves
       PrecState<float>& F = m->p32;

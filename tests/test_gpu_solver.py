@@ -103,10 +103,11 @@ def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0):
 
 
 @pytest.mark.parametrize("mode,eta_storage,kappa", [(0, 0, 0.0), (1, 0, 0.0), (1, 1, 0.0), (1, 2, 0.0), (0, 0, 0.3),
-                                                    (1, 1, 0.3)])
+                                                    (1, 1, 0.3), (2, 0, 0.0), (2, 1, 0.3)])
 def test_stokes_solve_reaches_1e8_by_the_oracle(tn, mode, eta_storage, kappa):
     # mixed mode with 16-bit viscosity in the FP32 inner solve: the FP64 refinement still meets
-    # 1e-8 on the FP64 system; kappa > 0: the hourglass-controlled system (Eq. hgstab)
+    # 1e-8 on the FP64 system; mode 2: FP64 FGMRES with the FP32 preconditioner; kappa > 0: the
+    # hourglass-controlled system (Eq. hgstab)
     stats, S, b, ug, pg, om = config0(tn, mode=mode, eta_storage=eta_storage, kappa=kappa)
     res = S.residual(b, ug, pg)
     print(f"mode {mode}: {stats}, oracle residual {res:.3e}")
