@@ -66,6 +66,10 @@ constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
 #ifndef TN_WIDE_TILES
 #define TN_WIDE_TILES 1
 #endif
+// 1: the epilogue variants prefetch their per-node operands before the cell arithmetic
+#ifndef TN_EPI_PREFETCH
+#define TN_EPI_PREFETCH 1
+#endif
 // Register cap of the wide tiles: 561 threads are 18 warps, allocated as 20 (a multiple of the 4
 // sub-partitions), so 65536 / (20 x 32) rounds down to 96 registers per thread.
 #ifndef TN_WIDE_MAXREG
@@ -668,6 +672,12 @@ __device__ __forceinline__ void project_vec(T (&v)[3], const T* s, int64_t soff,
   v[0] -= dot * sx, v[1] -= dot * sy, v[2] -= dot * sz;
 }
 
+// L1 prefetch of one global address (no register result).
+template <typename T>
+__device__ __forceinline__ void prefetch_l1(const T* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Fused vector update at node idx from y = (K x)(idx) (see EpiArgs); `in` is the apply input.
 template <typename T, int EPI>
 __device__ __forceinline__ void epilogue(const EpiArgs<T>& E, const T* in0, const T* in1, const T* in2, int idx,
@@ -963,6 +973,19 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
           s[q][c] = SD(c, qi[q - 1], qj[q - 1]);
           if (Op::NEEDS_D) dd[q][c] = SD(NIN + c, qi[q - 1], qj[q - 1]);
         }
+    }
+    // fused vector update: start fetching the owned node's epilogue operands into L1 now, so
+    // their latency overlaps the cell arithmetic (the epilogue runs after the exchange)
+    if (TN_EPI_PREFETCH && EPI != EPI_NONE && own && !own_shared && k >= kc0) {
+      const int idx = c00 + k * LS;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (EPI == EPI_CHEB2) prefetch_l1(E.r[c] + idx), prefetch_l1(E.xacc[c] + idx);
+        else prefetch_l1(E.b[c] + idx);
+      }
+      if (EPI != EPI_RESID)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) prefetch_l1(E.binv[q] + idx);
     }
     T accb[4][NOUT], acct[4][NOUT];  // assigned by the op (zero for a halo cell outside the diamond)
     if (!cell_ok) {

@@ -190,9 +190,16 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
   for (int d = 0; d < 10; ++d)
     for (int i = 0; i <= N; ++i)
       for (int j = 0; j <= N; ++j) owned[((int64_t)d * M + i) * L.P + j] = 1;
+  // groups in layout order of their first copy, so that neighbouring groups along a diamond row
+  // are neighbouring threads of the interface kernels (coalesced accesses)
+  std::vector<std::pair<int64_t, const Key*>> order;
   for (auto& kv : groups) {
-    auto& v = kv.second;
-    std::sort(v.begin(), v.end());
+    std::sort(kv.second.begin(), kv.second.end());
+    order.push_back({kv.second[0], &kv.first});
+  }
+  std::sort(order.begin(), order.end());
+  for (auto& ok : order) {
+    auto& v = groups[*ok.second];
     if (v.size() == 2) ++n2;
     else if (v.size() == 3) ++n3;
     else if (v.size() == 5) ++n5;
@@ -207,7 +214,7 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
     }
     grp_off.insert(grp_off.end(), v.begin(), v.end());
     grp_ptr.push_back((int)grp_off.size());
-    gs.push_back(gpos[kv.first]);
+    gs.push_back(gpos[*ok.second]);
   }
   if (n2 != 20 * (N - 1) || n3 != 10 || n5 != 2) err = "interface groups do not match the icosahedral topology";
   L.n_groups = (int)gs.size();
