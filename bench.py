@@ -41,8 +41,10 @@ A_TRAFFIC_BYTES_PER_CELL = 206.4e6 / 2621440
 HG_KAPPA = 0.3
 # Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
 # restriction, interface), B^T 3 (prolongation, tile, interface), diag 3 (tile, boundary-layer
-# gather, interface).
-LAUNCHES_PER_STEP = 12
+# gather, interface); FP64 levels with N >= 32 add one tile-line pass to each of the four tile
+# kernels.
+def launches_per_step(level):
+    return 12 + (4 if level >= 5 else 0)
 # FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
@@ -470,7 +472,7 @@ def main():
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+            "gpu_launches": launches_per_step(args.level) * args.steps,
         }
         if world == 1 and not args.no_solve:
             # Stokes solves to 1e-8: FP64 against FP32 inner solves with FP64 refinement

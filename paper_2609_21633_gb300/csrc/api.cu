@@ -44,7 +44,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32, L.dcoef64, L.dcoef32};
+                  L.rad32, L.dcoef64, L.dcoef32, L.ring64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -154,6 +154,10 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
   } else {
     chk(cudaMalloc((void**)&L.eta16, sizeof(uint16_t) * L.n_wedges));
     chk(cudaMalloc((void**)&L.eta_cs, sizeof(float) * L.n_tri));
+  }
+  {
+    const int64_t nring = ring_buffer_entries(L.N, L.n_r);
+    if (nring > 0) chk(cudaMalloc((void**)&L.ring64, sizeof(double) * nring));
   }
   chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
   chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));

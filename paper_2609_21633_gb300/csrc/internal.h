@@ -56,6 +56,9 @@ struct Level {
   double* dcoef64 = nullptr;
   float* dcoef32 = nullptr;
   int dcoef_div = -1;
+  // Tile-line partial sums of the FP64 halo-free tile kernels (levels with N >= 32):
+  // [4 slots][3 components][n_r][10][tile-line nodes of a diamond layer].
+  double* ring64 = nullptr;
   uint16_t* eta16 = nullptr;
   float* eta_cs = nullptr;
   // Scratch scalar field in this level's node layout (B / B^T intermediate).
@@ -169,6 +172,8 @@ cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st)
 // Kernel attributes that must be set before the first launch (shared-memory opt-ins); called
 // once per process by tn_mesh_create.
 cudaError_t prepare_tile_kernels();
+// Entries of Level::ring64 for a level (0: the level needs none).
+int64_t ring_buffer_entries(int N, int n_r);
 // The FP32 path's viscosity from eta64: eta32, or eta16 and the column factors (see Level).
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st);
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);

@@ -47,6 +47,8 @@ namespace {
 
 constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
 
+inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
 // Resident CTAs per SM requested from the register allocator for the tile kernel, per precision.
 #ifndef TN_MINB_F64
 #define TN_MINB_F64 2
@@ -65,6 +67,10 @@ constexpr int TILE = 16;  // lateral nodes per tile edge (N >= 16), else N
 #endif
 #ifndef TN_WIDE_TILES
 #define TN_WIDE_TILES 1
+#endif
+// 1: FP64 levels with N >= 32 use halo-free 16 x 32 tiles plus the tile-line pass
+#ifndef TN_HALO_FREE
+#define TN_HALO_FREE 1
 #endif
 // 1: the epilogue variants prefetch their per-node operands before the cell arithmetic
 #ifndef TN_EPI_PREFETCH
@@ -1033,6 +1039,320 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
   }
 }
 
+// ------------------------------------------------------------------------------------ halo-free tiles
+// FP64 levels with N >= 32: a CTA of TI x TJ threads computes exactly its TI x TJ cells (no halo
+// recompute, no idle lanes).  Nodes with all four cells in the tile are finished here; the nodes
+// on the tile's edges (the tile lines i = m TI and j = n TJ) get one partial sum per tile in a
+// ring buffer, summed in a fixed order and finished by k_ring_fix.  A tile-line node (i, j)
+// written by a tile with first cell (i0, j0) goes to slot 2 bi + bj, bi = (i == i0),
+// bj = (j == j0); its index within a diamond layer is ring_index(i, j).
+struct RingDims {
+  int TI, TJ, H, RC;  // tile shape, nodes on horizontal tile lines, all tile-line nodes
+};
+__host__ __device__ inline RingDims ring_dims(int N, int TI, int TJ) {
+  RingDims r;
+  r.TI = TI, r.TJ = TJ;
+  r.H = (N / TI + 1) * (N + 1);
+  r.RC = r.H + (N / TJ + 1) * (N - N / TI);
+  return r;
+}
+__device__ __forceinline__ int ring_index(const RingDims& R, int N, int i, int j) {
+  if (i % R.TI == 0) return (i / R.TI) * (N + 1) + j;
+  return R.H + (j / R.TJ) * (N - N / R.TI) + (i - i / R.TI - 1);
+}
+// ring[((slot * ncomp + c) * n_r + k) * 10 * RC + d RC + rid]
+
+template <typename T, typename Op, int TI, int TJ>
+struct TileSmemHF {
+  static constexpr int NS = Op::LOADS ? (Op::NEEDS_D ? 2 * Op::NIN : Op::NIN) : 0;
+  static constexpr int SD = NS * (TI + 1) * (TJ + 1);
+  static constexpr int SM = 3 * Op::NOUT * TI * TJ;
+  static constexpr size_t bytes = sizeof(T) * (size_t)(SD + SM);
+};
+
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI, int EK>
+__device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ ring) {
+  constexpr int NIN = Op::NIN, NOUT = Op::NOUT;
+  using Sh = TileSmemHF<T, Op, TI, TJ>;
+  constexpr int NS = Sh::NS;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  T* const sd = reinterpret_cast<T*>(tile_smem);  // [NS][TI + 1][TJ + 1]
+  T* const sm = sd + Sh::SD;                        // [3][NOUT][TI][TJ]
+  auto SD = [&](int v, int i, int j) -> T& { return sd[(v * (TI + 1) + i) * (TJ + 1) + j]; };
+  auto SM = [&](int q, int c, int i, int j) -> T& { return sm[((q * NOUT + c) * TI + i) * TJ + j]; };
+  if (skip && *skip) return;
+  const int N = D.N, n_r = D.n_r, P = D.P;
+  const int LS = (int)D.layer_stride, NLL = (int)D.n_lat_layout;
+  const RingDims RD = ring_dims(N, TI, TJ);
+  const int ntj = N / TJ;
+  const int i0 = (blockIdx.x / ntj) * TI, j0 = (blockIdx.x % ntj) * TJ;
+  const int d = blockIdx.z;
+  const int kc0 = blockIdx.y * kc, kc1 = min(n_r - 1, kc0 + kc);
+  const int ti = threadIdx.x / TJ, tj = threadIdx.x % TJ;
+  const int ci = i0 + ti, cj = j0 + tj;  // this thread's cell; its corner 00 is its own node
+  const int c00 = (int)(d * D.diamond_stride) + ci * P + cj;
+  const int lat00 = d * (N + 1) * P + ci * P + cj;
+  T Mi[2][9], dM[2];
+  {
+    const int t0 = ((d * N + ci) * N + cj) * 2, nt = (int)D.n_tri;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Mi[w][q] = geo[q * nt + t0 + w];
+      dM[w] = geo[9 * nt + t0 + w];
+      if (EK != TN_ETA_F32 && Op::USES_ETA) dM[w] *= eta.cs[t0 + w];
+    }
+  }
+  const typename Op::Col col = op.column(Mi, dM, ((d * N + ci) * N + cj) * 2);
+  const int eta_c0 = (((d * (n_r - 1)) * N + ci) * N + cj) * 2;
+  const int eta_ls = N * N * 2;
+  const bool interior = ti >= 1 && tj >= 1;  // own node finished here (never on a diamond edge)
+
+  // extra nodes (input sums and output partials): e < TJ + 1: row node (TI, e); then column
+  // node (e - TJ - 1, TJ); threads 0 .. NX - 1
+  constexpr int NX = TI + TJ + 1;
+  auto extra_node = [&](int e, int& si, int& sj) {
+    si = e <= TJ ? TI : e - TJ - 1;
+    sj = e <= TJ ? e : TJ;
+  };
+  auto load_node = [&](int off, int lat, int k, T (&v)[NIN]) {
+    const int o = off + k * LS;
+    v[0] = in0[o];
+    if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
+    if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
+    if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
+      T vv[3] = {v[0], v[NIN > 1 ? 1 : 0], v[NIN > 2 ? 2 : 0]};
+      project_vec(vv, svec, (int64_t)lat, (int64_t)NLL, k == 0 ? bc_in : bc_out);
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) v[c] = vv[c];
+    }
+  };
+  auto put_node = [&](int i, int j, const T (&b)[NIN], const T (&t)[NIN], T (&sv)[NIN], T (&dv)[NIN]) {
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) {
+      sv[c] = b[c] + t[c];
+      SD(c, i, j) = sv[c];
+      if (Op::NEEDS_D) {
+        dv[c] = t[c] - b[c];
+        SD(NIN + c, i, j) = dv[c];
+      }
+    }
+  };
+  auto store_node = [&](int k, int idx, int so, T (&v)[3]) {  // a finished node off the diamond edges
+    if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
+      const int bc = k == 0 ? bc_in : bc_out;
+      project_vec(v, svec, (int64_t)so, (int64_t)NLL, bc);
+      if (FLAGS & ADD_ID) {
+        T uu[3] = {in0[idx], in1[idx], in2[idx]};
+        T pu[3] = {uu[0], uu[1], uu[2]};
+        project_vec(pu, svec, (int64_t)so, (int64_t)NLL, bc);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] += uu[c] - pu[c];
+      }
+    }
+    if (EPI != EPI_NONE) {
+      epilogue<T, EPI>(E, in0, in1, in2, idx, v);
+      return;
+    }
+    out0[idx] = v[0];
+    if (NOUT > 1) out1[idx] = v[NOUT > 1 ? 1 : 0];
+    if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
+  };
+  const int64_t ring_c = (int64_t)n_r * 10 * RD.RC;  // stride of one (slot, component)
+  auto ring_store = [&](int k, int i, int j, int slot, const T (&v)[3]) {
+    const int64_t base = (int64_t)k * 10 * RD.RC + (int64_t)d * RD.RC + ring_index(RD, N, i, j);
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) ring[(slot * NOUT + c) * ring_c + base] = v[c];
+  };
+  auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) SM(q - 1, c, ti, tj) = acc[q][c];
+    __syncthreads();
+    {
+      // own node (ci, cj): this cell's corner 00 + (ci-1, cj) corner 10 + (ci, cj-1) corner 01 +
+      // (ci-1, cj-1) corner 11, the cells of this tile only
+      T v[3] = {0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) {
+        T a = acc[0][c];
+        if (ti >= 1) a += SM(0, c, ti - 1, tj);
+        if (tj >= 1) a += SM(1, c, ti, tj - 1);
+        if (ti >= 1 && tj >= 1) a += SM(2, c, ti - 1, tj - 1);
+        v[c] = a;
+      }
+      if (interior) store_node(k, c00 + k * LS, lat00, v);
+      else ring_store(k, ci, cj, 2 * (ti == 0) + (tj == 0), v);
+    }
+    for (int e = (int)threadIdx.x; e < NX; e += (int)blockDim.x) {
+      int si, sj;
+      extra_node(e, si, sj);
+      // node (i0 + si, j0 + sj) on the far row / column: cells (si - 1, sj) corner 10,
+      // (si, sj - 1) corner 01, (si - 1, sj - 1) corner 11 where they are in the tile
+      T v[3] = {0, 0, 0};
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) {
+        T a = (T)0;
+        if (si >= 1 && sj < TJ) a += SM(0, c, si - 1, sj);
+        if (sj >= 1 && si < TI) a += SM(1, c, si, sj - 1);
+        if (si >= 1 && sj >= 1) a += SM(2, c, si - 1, sj - 1);
+        v[c] = a;
+      }
+      ring_store(k, i0 + si, j0 + sj, 2 * (si == 0) + (sj == 0), v);
+    }
+  };
+
+  T ub[NIN];
+  T carry[4][NOUT];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) carry[q][c] = 0;
+  const int kstart = kc0 > 0 ? kc0 - 1 : 0;
+  if (NS > 0) load_node(c00, lat00, kstart, ub);
+  for (int k = kstart; k < kc1; ++k) {
+    T s[4][NIN], dd[4][NIN];
+    if (NS > 0) {
+      T ut[NIN];
+      load_node(c00, lat00, k + 1, ut);
+      put_node(ti, tj, ub, ut, s[0], dd[0]);
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) ub[c] = ut[c];
+      for (int e = (int)threadIdx.x; e < NX; e += (int)blockDim.x) {
+        int si, sj;
+        extra_node(e, si, sj);
+        const int ni = i0 + si, nj = j0 + sj;  // <= N
+        const int off = (int)(d * D.diamond_stride) + ni * P + nj;
+        const int lat = d * (N + 1) * P + ni * P + nj;
+        T xb[NIN], xt[NIN], xs[NIN], xd[NIN];
+        load_node(off, lat, k, xb);
+        load_node(off, lat, k + 1, xt);
+        put_node(si, sj, xb, xt, xs, xd);
+      }
+      __syncthreads();
+      const int qi[3] = {ti + 1, ti, ti + 1}, qj[3] = {tj, tj + 1, tj + 1};
+#pragma unroll
+      for (int q = 1; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) {
+          s[q][c] = SD(c, qi[q - 1], qj[q - 1]);
+          if (Op::NEEDS_D) dd[q][c] = SD(NIN + c, qi[q - 1], qj[q - 1]);
+        }
+    }
+    if (TN_EPI_PREFETCH && EPI != EPI_NONE && interior && k >= kc0) {
+      const int idx = c00 + k * LS;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (EPI == EPI_CHEB2) prefetch_l1(E.r[c] + idx), prefetch_l1(E.xacc[c] + idx);
+        else prefetch_l1(E.b[c] + idx);
+      }
+      if (EPI != EPI_RESID)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) prefetch_l1(E.binv[q] + idx);
+    }
+    T accb[4][NOUT], acct[4][NOUT];
+    {
+      T e[2] = {(T)1, (T)1};
+      if (Op::USES_ETA) {
+        const int o = eta_c0 + k * eta_ls;
+        if (EK == TN_ETA_F32) {
+          const double2 p = *reinterpret_cast<const double2*>(eta.v + o);
+          e[0] = (T)p.x, e[1] = (T)p.y;
+        } else {
+          const uint32_t p = *reinterpret_cast<const uint32_t*>(eta.q + o);
+          e[0] = (T)from16<EK>((uint16_t)(p & 0xffffu)), e[1] = (T)from16<EK>((uint16_t)(p >> 16));
+        }
+      }
+      op.cell(s, dd, Mi, dM, lay + kLayerStride * k, e, accb, acct, col);
+    }
+    if (k >= kc0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) accb[q][c] += carry[q][c];
+      exchange_write(k, accb);
+    }
+    if (NS == 0 || k < kc0) __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) carry[q][c] = acct[q][c];
+  }
+  if (kc1 == n_r - 1) {
+    __syncthreads();
+    exchange_write(n_r - 1, carry);
+  }
+}
+
+// Halo-free FP64 tiles: TI x TJ threads, one CTA per SM.
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
+__global__ void __launch_bounds__(TI * TJ, 1) k_tile_hf(TN_TILE_PARAMS, T* __restrict__ ring) {
+  tile_body_hf<T, Op, TI, TJ, FLAGS, EPI, EK>(TN_TILE_ARGS, ring);
+}
+
+// Thread per tile-line node and layer: the fixed-order sum of the tiles' partials (slots 0..3 of
+// the tiles that exist around the node), then the node is finished like in the tile kernel:
+// diamond-edge nodes get the diamond's partial sum (projected) for the interface pass.
+template <typename T, int NOUT, int FLAGS, int EPI>
+__global__ void k_ring_fix(Dims D, RingDims RD, const T* __restrict__ ring, const T* __restrict__ in0,
+                           const T* __restrict__ in1, const T* __restrict__ in2, T* __restrict__ out0,
+                           T* __restrict__ out1, T* __restrict__ out2, const T* __restrict__ svec, int bc_in,
+                           int bc_out, const int* __restrict__ skip, EpiArgs<T> E) {
+  if (skip && *skip) return;
+  const int N = D.N, n_r = D.n_r;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per_k = (int64_t)10 * RD.RC;
+  if (tid >= per_k * n_r) return;
+  const int k = (int)(tid / per_k);
+  const int d = (int)((tid % per_k) / RD.RC), rid = (int)(tid % RD.RC);
+  int i, j;
+  if (rid < RD.H) {
+    i = (rid / (N + 1)) * RD.TI, j = rid % (N + 1);
+  } else {
+    const int r2 = rid - RD.H, per = N - N / RD.TI;
+    const int t = r2 % per;
+    j = (r2 / per) * RD.TJ;
+    i = (t / (RD.TI - 1)) * RD.TI + 1 + t % (RD.TI - 1);
+  }
+  const bool on_h = i % RD.TI == 0, on_v = j % RD.TJ == 0;
+  const int64_t ring_c = (int64_t)n_r * 10 * RD.RC;
+  const int64_t base = (int64_t)k * per_k + (int64_t)d * RD.RC + rid;
+  T v[3] = {0, 0, 0};
+  for (int bi = 0; bi < 2; ++bi) {
+    if (bi == 1 && !on_h) break;
+    if (on_h && ((bi == 0 && i == 0) || (bi == 1 && i == N))) continue;  // no tile there
+    for (int bj = 0; bj < 2; ++bj) {
+      if (bj == 1 && !on_v) break;
+      if (on_v && ((bj == 0 && j == 0) || (bj == 1 && j == N))) continue;
+      const int slot = 2 * bi + bj;
+#pragma unroll
+      for (int c = 0; c < NOUT; ++c) v[c] += ring[(slot * NOUT + c) * ring_c + base];
+    }
+  }
+  const int M = N + 1;
+  const int idx = (int)(d * D.diamond_stride) + k * (int)D.layer_stride + i * D.P + j;
+  const int64_t so = ((int64_t)d * M + i) * D.P + j;
+  const bool shared = i == 0 || i == N || j == 0 || j == N;
+  if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    project_vec(v, svec, so, D.n_lat_layout, bc);
+    if ((FLAGS & ADD_ID) && !shared) {
+      T uu[3] = {in0[idx], in1[idx], in2[idx]};
+      T pu[3] = {uu[0], uu[1], uu[2]};
+      project_vec(pu, svec, so, D.n_lat_layout, bc);
+      for (int c = 0; c < 3; ++c) v[c] += uu[c] - pu[c];
+    }
+  }
+  if (EPI != EPI_NONE && !shared) {
+    epilogue<T, EPI>(E, in0, in1, in2, idx, v);
+    return;
+  }
+  out0[idx] = v[0];
+  if (NOUT > 1) out1[idx] = v[NOUT > 1 ? 1 : 0];
+  if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
+}
+
 // Square tiles: MinBlocks CTAs per SM through the register cap of the launch bounds.
 template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
 __global__ void __launch_bounds__((TI + 1) * (TJ + 1), MinBlocks<T>::value) k_tile(TN_TILE_PARAMS) {
@@ -1089,6 +1409,20 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
     }
   }
   if constexpr (kWideT) {
+    if (wide && TN_HALO_FREE) {
+      // halo-free tiles: grid over the tiles proper, then the tile-line nodes
+      if (!L.ring64) return cudaErrorInvalidValue;  // allocated with the level
+      constexpr int TI = TILE, TJ = 2 * TILE;
+      k_tile_hf<T, Op, TI, TJ, FLAGS, EPI, TN_ETA_F32><<<grid, TI * TJ, TileSmemHF<T, Op, TI, TJ>::bytes, st>>>(
+          D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E, (T*)L.ring64);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      const RingDims RD = ring_dims(L.N, TI, TJ);
+      const int64_t nr = (int64_t)10 * RD.RC * L.n_r;
+      k_ring_fix<T, Op::NOUT, FLAGS, EPI><<<nblk(nr, 256), 256, 0, st>>>(D, RD, (const T*)L.ring64, in[0], i1, i2,
+                                                                        out[0], o1, o2, sv, bc.in, bc.out, skip, E);
+      return cudaGetLastError();
+    }
     if (wide) {
       TN_TILE_LAUNCH(k_tile_wide, TILE, 2 * TILE, TN_ETA_F32);
       return cudaGetLastError();
@@ -1632,8 +1966,6 @@ __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double*
 
 #endif  // TN_PART == 0 || TN_PART == 1
 
-inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------- launchers
@@ -1851,6 +2183,12 @@ __global__ void k_eta_16(Dims D, const double* __restrict__ eta, uint16_t* __res
   }
 }
 
+int64_t ring_buffer_entries(int N, int n_r) {
+  if (!(TN_HALO_FREE && N >= 2 * TILE)) return 0;
+  const RingDims RD = ring_dims(N, TILE, 2 * TILE);
+  return (int64_t)4 * 3 * n_r * 10 * RD.RC;
+}
+
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st) {
   if (L.eta_kind == TN_ETA_F32) return launch_to_f32(L.eta64, L.eta32, L.n_wedges, st);
   if (L.eta_kind == TN_ETA_BF16)
@@ -1903,10 +2241,18 @@ TN_INST_A(double)
 template <bool HG, int EPI>
 cudaError_t set_wide_a_attr() {
   using Op = OpA<double, HG>;
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
   constexpr size_t sh = TileSmem<double, Op, TILE, 2 * TILE>::bytes;
-  if (sh <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k_tile_wide<double, Op, TILE, 2 * TILE, PROJ_IN | PROJ_OUT | ADD_ID, EPI, TN_ETA_F32>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  if (sh > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_wide<double, Op, TILE, 2 * TILE, F, EPI, TN_ETA_F32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    if (e != cudaSuccess) return e;
+  }
+  constexpr size_t shf = TileSmemHF<double, Op, TILE, 2 * TILE>::bytes;
+  if (shf > 48 * 1024)
+    return cudaFuncSetAttribute(k_tile_hf<double, Op, TILE, 2 * TILE, F, EPI, TN_ETA_F32>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+  return cudaSuccess;
 }
 
 cudaError_t prepare_tile_kernels() {

@@ -201,7 +201,7 @@ def test_apply_B_and_BT_f64(tn, level, n_r, bc):
     c.close()
 
 
-@pytest.mark.parametrize("level,n_r,bc", [(1, 3, "free/free"), (2, 5, "free/free"), (3, 9, "noslip/free"),
+@pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"),
                                           (4, 17, "free/free"), (5, 9, "noslip/noslip")])
 def test_diagonals_f64(tn, level, n_r, bc):
     c = Case(tn, level, n_r, BCS[bc])

@@ -35,9 +35,10 @@ def from_dev(mp, ts):
 
 @pytest.mark.parametrize("level,n_r,bc,kappa", [(3, 9, (1, 0), 0.0), (3, 9, (0, 0), 0.0), (4, 9, (0, 0), 0.0),
                                                (2, 17, (0, 0), 0.0), (4, 5, (1, 0), 0.0), (3, 9, (1, 0), 0.3),
-                                               (4, 5, (0, 0), 0.3)])
+                                               (4, 5, (0, 0), 0.3), (5, 5, (1, 0), 0.0), (5, 5, (0, 0), 0.3)])
 def test_vcycle_f64_matches_oracle(tn, level, n_r, bc, kappa):
     """Includes semi-coarsened hierarchies: (2, 17) coarsens radially first, (4, 5) laterally;
+    level 5 runs the FP64 fine level on the halo-free 16 x 32 tiles with the fused smoother;
     kappa > 0: hourglass control (Eq. hgstab) on every level."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     eta = inputs.lognormal_viscosity(om.n_wedges, 3, 0.5)
