@@ -33,10 +33,10 @@ LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, 
 # per wedge 33 (differences) + 9 (scaling) + 45 (grad u) + 20 (stress) + 54 (stress x M^-T)
 # + 21 (test-gradient combination) + 18 (accumulation) = 200.
 A_FLOPS_PER_CELL = 400.0
-# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 206.4 MB for
-# 2,621,440 cells, 16 x 32 tiles with shared corner sums), scaled to the bench size by cells; None
-# once the kernel changes.
-A_TRAFFIC_BYTES_PER_CELL = 206.4e6 / 2621440
+# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 176.8 MB for
+# 2,621,440 cells, halo-free 16 x 32 tiles), scaled to the bench size by cells; None once the
+# kernel changes.
+A_TRAFFIC_BYTES_PER_CELL = 176.77e6 / 2621440
 # Hourglass-control coefficient of the solves and the serving stream that use it.
 HG_KAPPA = 0.3
 # Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
