@@ -19,6 +19,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   the hourglass base vectors of Flanagan & Belytschko (1981) -- so that rigid motions and every
   linear field keep zero stabilisation energy; eps_e = kappa tr(A_e) / 18, kappa times the mean
   diagonal entry of the element matrix ("scaled with the local stiffness").
+* Second radial quadrature point, the other remedy of Sec. 4 for the one-point hourglass modes.
+  Reading (the paper names the variant only): the two-point Gauss-Legendre rule in zeta at the
+  lateral barycentre, points (1/3, 1/3, -/+ 1/sqrt 3), weight 1/2 each (triangle area 1/2 times
+  the Gauss weight 1), so the weights still sum to the reference wedge's volume; eta_e is the same
+  at both points (one viscosity per wedge, as for the one-point rule).  A_e is then
+  sum_q w_q |det J_q| eta_e [2 eps_q(phi_a) : eps_q(phi_b) - 2/3 div_q(phi_a) div_q(phi_b)].
 """
 import numpy as np
 
@@ -49,6 +55,18 @@ def basis_ref_gradients(xi, eta, zeta):
 GHAT = basis_ref_gradients(*QC)
 
 
+def quadrature_rule(radial_points=1):
+    """Quadrature points and weights of the reference wedge: the barycentre with weight 1
+    (radial_points = 1), or the two-point Gauss-Legendre rule in zeta at the lateral barycentre
+    with weights 1/2 (radial_points = 2)."""
+    if radial_points == 1:
+        return [(QC, 1.0)]
+    if radial_points == 2:
+        z = 1.0 / np.sqrt(3.0)
+        return [((1.0 / 3.0, 1.0 / 3.0, -z), 0.5), ((1.0 / 3.0, 1.0 / 3.0, z), 0.5)]
+    raise ValueError(radial_points)
+
+
 def geometry(x):
     """One-point geometry of wedges with node coordinates ``x`` (n, 6, 3).
 
@@ -59,6 +77,16 @@ def geometry(x):
     grad = np.einsum("jm,nmc->njc", GHAT, Jinv)    # grad N_j = J^{-T} ghat_j
     V = 1.0 * np.abs(detJ)                          # w_q = 1
     return J, detJ, grad, V
+
+
+def geometry_at(x, point, weight):
+    """Geometry of wedges with node coordinates ``x`` (n, 6, 3) at one quadrature point.
+
+    Returns (grad (n,6,3) = grad N_j(point), V (n,) = weight |det J(point)|)."""
+    g = basis_ref_gradients(*point)
+    J = np.einsum("njc,jm->ncm", x, g)
+    grad = np.einsum("jm,nmc->njc", g, np.linalg.inv(J))
+    return grad, weight * np.abs(np.linalg.det(J))
 
 
 def vector_basis_strain(grad):
@@ -84,6 +112,16 @@ def viscous_element_matrix(grad, V, eta, div_term=True):
     if div_term:
         A = A - (2.0 / 3.0) * np.einsum("na,nb->nab", div, div)
     return (V * eta)[:, None, None] * A
+
+
+def viscous_element_matrix_rule(x, eta, rule, div_term=True):
+    """(A_e) of Eq. (elemmat) under a quadrature rule [(point, weight), ...], shape (n, 18, 18),
+    with one viscosity per wedge."""
+    A = 0.0
+    for point, weight in rule:
+        grad, V = geometry_at(x, point, weight)
+        A = A + viscous_element_matrix(grad, V, eta, div_term)
+    return A
 
 
 def hourglass_vectors():

@@ -6,7 +6,8 @@ Algorithm (the paper gives the structure: two pre- and two post-smoothing steps 
 degree-2 Chebyshev smoother per level, conjugate gradients on the coarsest level; the
 remaining choices are readings):
 * level operators K_h = P_h A_h P_h + (I - P_h), re-discretised with the coarse viscosity
-  (mean of the 8 children) and, with kappa > 0, the same hourglass control on every level; D_h = the 3x3 node-block diagonal of K_h (block Jacobi; reading:
+  (mean of the 8 children) and, with kappa > 0 or quad = 2, the same hourglass control or
+  radial quadrature on every level; D_h = the 3x3 node-block diagonal of K_h (block Jacobi; reading:
   the paper does not say which diagonal its Chebyshev smoother uses);
 * level shapes: each coarser level halves the lateral and / or radial resolution according
   to the cells' radial / lateral size ratio q (semi-coarsening where the cells are
@@ -129,7 +130,7 @@ def rotation_basis(mesh):
 class Hierarchy:
     def __init__(self, level, n_r, r_in, r_out, eta0, bc=(O.FREE, O.FREE), nlev=None, div_term=True,
                  lo=0.1, hi=1.1, power_iters=15, pre=2, post=2, coarse_max_iters=50, coarse_rtol=1e-3,
-                 kappa=0.0):
+                 kappa=0.0, quad=1):
         self.meshes = [ShellMesh(l, nr, r_in, r_out) for l, nr in mg_shapes(level, n_r, r_in, r_out)]
         if nlev is not None:
             self.meshes = self.meshes[:nlev]
@@ -139,7 +140,7 @@ class Hierarchy:
         for h in range(1, self.nlev):
             self.eta.append(coarsen_viscosity_semi(self.meshes[h - 1], self.meshes[h], self.eta[h - 1]))
         self.Pb = [O.projector_matrix(O.boundary_projectors(m, bc)) for m in self.meshes]
-        self.K = [O.constrain_A(O.assemble_A(m, e, div_term, kappa), Pb)
+        self.K = [O.constrain_A(O.assemble_A(m, e, div_term, kappa, quad), Pb)
                   for m, e, Pb in zip(self.meshes, self.eta, self.Pb)]
         self.Dinv = [block_jacobi_inverse(K) for K in self.K]
         self.T = [vec_prolongation(self.meshes[h], self.meshes[h + 1]) for h in range(self.nlev - 1)]

@@ -26,7 +26,8 @@ Vectors are arrays of shape (3, n_nodes) (velocity) or (n_pnodes,) (pressure).
 import numpy as np
 import scipy.sparse as sp
 
-from .element import geometry, hourglass_base_vectors, hourglass_stabilised, viscous_element_matrix
+from .element import (geometry, hourglass_base_vectors, hourglass_stabilised, quadrature_rule,
+                      viscous_element_matrix, viscous_element_matrix_rule)
 from .mesh import ShellMesh
 
 FREE, NOSLIP = "free", "noslip"
@@ -41,13 +42,17 @@ def wedge_geometry(mesh, wedges=None):
     return grad, V
 
 
-def element_matrices(mesh, eta, wedges, div_term=True, kappa=0.0):
-    """Element matrices (n, 18, 18) of the given wedges: Eq. (elemmat) under the one-point rule,
-    plus the hourglass control of Eq. (hgstab) when kappa > 0 (see ``oracle.element``)."""
+def element_matrices(mesh, eta, wedges, div_term=True, kappa=0.0, quad=1):
+    """Element matrices (n, 18, 18) of the given wedges: Eq. (elemmat) under the one-point rule
+    (quad = 1) or with a second radial point (quad = 2), plus the hourglass control of
+    Eq. (hgstab) when kappa > 0 (see ``oracle.element``)."""
     nodes = mesh.wedge_nodes(wedges)
     x = mesh.node_xyz(nodes.ravel()).reshape(-1, 6, 3)
     _, _, grad, V = geometry(x)
-    A = viscous_element_matrix(grad, V, eta, div_term)
+    if quad == 1:
+        A = viscous_element_matrix(grad, V, eta, div_term)
+    else:
+        A = viscous_element_matrix_rule(x, eta, quadrature_rule(quad), div_term)
     if kappa > 0.0:
         A = hourglass_stabilised(A, hourglass_base_vectors(x, grad), kappa)
     return A
@@ -59,19 +64,19 @@ def _chunks(ids, size):
 
 
 # ----------------------------------------------------------------------------- viscous block A
-def assemble_A(mesh, eta, div_term=True, kappa=0.0):
+def assemble_A(mesh, eta, div_term=True, kappa=0.0, quad=1):
     """Assembled A (3n x 3n CSR) from the element matrices, Eq. (matfree); kappa > 0 adds the
-    hourglass control of Eq. (hgstab)."""
+    hourglass control of Eq. (hgstab), quad = 2 takes the second radial quadrature point."""
     n = mesh.n_nodes
     nodes = mesh.wedge_nodes()
-    Ae = element_matrices(mesh, eta, np.arange(mesh.n_wedges), div_term, kappa)   # a = 3 j + d
+    Ae = element_matrices(mesh, eta, np.arange(mesh.n_wedges), div_term, kappa, quad)   # a = 3 j + d
     dof = (np.arange(3)[None, None, :] * n + nodes[:, :, None]).reshape(-1, 18)
     rows = np.repeat(dof, 18, axis=1).ravel()
     cols = np.tile(dof, (1, 18)).ravel()
     return sp.csr_matrix((Ae.ravel(), (rows, cols)), shape=(3 * n, 3 * n))
 
 
-def apply_A(mesh, eta, u, wedges=None, div_term=True, chunk=50000, kappa=0.0):
+def apply_A(mesh, eta, u, wedges=None, div_term=True, chunk=50000, kappa=0.0, quad=1):
     """Matrix-free y = sum_e I_e^T A_e I_e u over the given wedges (all if None).
 
     u: (3, n_nodes).  Element matrices are formed explicitly per wedge."""
@@ -80,7 +85,7 @@ def apply_A(mesh, eta, u, wedges=None, div_term=True, chunk=50000, kappa=0.0):
     ids = np.arange(mesh.n_wedges) if wedges is None else np.asarray(wedges)
     for ch in _chunks(ids, chunk):
         nodes = mesh.wedge_nodes(ch)
-        Ae = element_matrices(mesh, eta[ch], ch, div_term, kappa)
+        Ae = element_matrices(mesh, eta[ch], ch, div_term, kappa, quad)
         ue = np.transpose(u[:, nodes], (1, 2, 0)).reshape(-1, 18)   # ue[e, 3 j + d]
         ye = np.einsum("eab,eb->ea", Ae, ue).reshape(-1, 6, 3)
         for d in range(3):
@@ -132,10 +137,10 @@ def constrain_A(Amat, Pm):
     return (Pm @ Amat @ Pm + (I - Pm)).tocsr()
 
 
-def apply_A_constrained(mesh, eta, u, P, wedges=None, div_term=True, kappa=0.0):
+def apply_A_constrained(mesh, eta, u, P, wedges=None, div_term=True, kappa=0.0, quad=1):
     """Matrix-free (P A P + (I - P)) u; complete at every node whose wedges are all in ``wedges``."""
     pu = project(P, u)
-    return project(P, apply_A(mesh, eta, pu, wedges, div_term, kappa=kappa)) + (u - pu)
+    return project(P, apply_A(mesh, eta, pu, wedges, div_term, kappa=kappa, quad=quad)) + (u - pu)
 
 
 # ----------------------------------------------------------------------------- pressure space
@@ -227,7 +232,7 @@ def diag_pressure_mass(mesh, Pp, eta):
 
 
 # ----------------------------------------------------------------------------- diagonal of A
-def diag_A_constrained(mesh, eta, P, div_term=True, chunk=50000, wedges=None, kappa=0.0):
+def diag_A_constrained(mesh, eta, P, div_term=True, chunk=50000, wedges=None, kappa=0.0, quad=1):
     """Diagonal of P A P + (I - P), shape (3, n), from the 3x3 node blocks of A.
 
     The node block A_jj is accumulated element by element from the explicit
@@ -238,7 +243,7 @@ def diag_A_constrained(mesh, eta, P, div_term=True, chunk=50000, wedges=None, ka
     ids = np.arange(mesh.n_wedges) if wedges is None else np.asarray(wedges)
     for ch in _chunks(ids, chunk):
         nodes = mesh.wedge_nodes(ch)
-        Ae = element_matrices(mesh, eta[ch], ch, div_term, kappa).reshape(-1, 6, 3, 6, 3)
+        Ae = element_matrices(mesh, eta[ch], ch, div_term, kappa, quad).reshape(-1, 6, 3, 6, 3)
         for j in range(6):
             blk = Ae[:, j, :, j, :]
             for c in range(3):

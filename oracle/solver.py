@@ -16,13 +16,13 @@ from .multigrid import rotation_basis
 
 
 class StokesSystem:
-    def __init__(self, mesh, eta, bc=(O.FREE, O.FREE), div_term=True, kappa=0.0):
+    def __init__(self, mesh, eta, bc=(O.FREE, O.FREE), div_term=True, kappa=0.0, quad=1):
         self.mesh, self.bc = mesh, bc
         self.pmesh = O.pressure_mesh(mesh)
         P = O.boundary_projectors(mesh, bc)
         self.P = P
         Pm = O.projector_matrix(P)
-        A = O.constrain_A(O.assemble_A(mesh, eta, div_term, kappa), Pm)
+        A = O.constrain_A(O.assemble_A(mesh, eta, div_term, kappa, quad), Pm)
         B = O.assemble_B(mesh, O.prolongation(mesh, self.pmesh)) @ Pm
         self.nu, self.np_ = 3 * mesh.n_nodes, self.pmesh.n_nodes
         self.K = sp.bmat([[A, B.T], [B, None]], format="csr")

@@ -4,8 +4,9 @@ u = sin(pi (r - r_in) / (r_out - r_in)) v(x) vanishes on both surfaces (no-slip)
 the strong operator of Eq. (stokes) with the -2/3 div term is -div(2 eps(u) - 2/3 div u I) =
 -(Lap u + 1/3 grad div u), computed symbolically.  The load is lumped (f at the nodes times
 sum_e V_e / 6), and the discrete L2 error at the nodes must fall with second order under uniform
-refinement (lateral and radial), for the plain one-point rule and with hourglass control, whose
-error the paper reports unchanged (Sec. 4, Fig. 2 right)."""
+refinement (lateral and radial), for the plain one-point rule, with hourglass control, whose
+error the paper reports unchanged (Sec. 4, Fig. 2 right), and with a second radial quadrature
+point."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -28,11 +29,11 @@ def _fields():
     return sympy.lambdify((X, Y, Z), u, "numpy"), sympy.lambdify((X, Y, Z), f, "numpy")
 
 
-def _error(level, n_r, kappa, fu, ff):
+def _error(level, n_r, kappa, fu, ff, quad=1):
     m = ShellMesh(level, n_r, R_IN, R_OUT)
     xyz = m.node_xyz()
     P = O.boundary_projectors(m, (O.NOSLIP, O.NOSLIP))
-    K = O.constrain_A(O.assemble_A(m, np.ones(m.n_wedges), True, kappa), O.projector_matrix(P))
+    K = O.constrain_A(O.assemble_A(m, np.ones(m.n_wedges), True, kappa, quad), O.projector_matrix(P))
     _, V = O.wedge_geometry(m)
     mass = np.bincount(m.wedge_nodes().ravel(), weights=np.repeat(V / 6.0, 6), minlength=m.n_nodes)
     F = O.project(P, np.array([np.broadcast_to(c, (m.n_nodes,)) for c in ff(*xyz.T)]) * mass)
@@ -41,11 +42,11 @@ def _error(level, n_r, kappa, fu, ff):
     return np.sqrt(np.sum(mass * (uh - ue) ** 2) / np.sum(mass * ue ** 2))
 
 
-@pytest.mark.parametrize("kappa", [0.0, 0.1])
-def test_second_order_convergence(kappa):
+@pytest.mark.parametrize("kappa,quad", [(0.0, 1), (0.1, 1), (0.0, 2)])
+def test_second_order_convergence(kappa, quad):
     fu, ff = _fields()
-    e2 = _error(2, 5, kappa, fu, ff)
-    e3 = _error(3, 9, kappa, fu, ff)
+    e2 = _error(2, 5, kappa, fu, ff, quad)
+    e3 = _error(3, 9, kappa, fu, ff, quad)
     order = np.log2(e2 / e3)
-    print(f"kappa {kappa}: errors {e2:.3e} {e3:.3e}, order {order:.2f}")
+    print(f"kappa {kappa}, radial points {quad}: errors {e2:.3e} {e3:.3e}, order {order:.2f}")
     assert 1.8 <= order <= 2.4, order

@@ -2,8 +2,9 @@
 import numpy as np
 import pytest
 
-from oracle.element import (GHAT, QC, basis, basis_ref_gradients, geometry, hourglass_base_vectors,
-                            hourglass_stabilised, hourglass_vectors, viscous_element_matrix)
+from oracle.element import (GHAT, QC, basis, basis_ref_gradients, geometry, geometry_at, hourglass_base_vectors,
+                            hourglass_stabilised, hourglass_vectors, quadrature_rule, viscous_element_matrix,
+                            viscous_element_matrix_rule)
 from oracle.mesh import ShellMesh
 
 REF_NODES = [(0.0, 0.0, -1.0), (1.0, 0.0, -1.0), (0.0, 1.0, -1.0),
@@ -55,8 +56,9 @@ def test_gradients_reproduce_linear_fields():
         np.testing.assert_allclose(got, np.broadcast_to(a, got.shape), atol=1e-12)
 
 
-def _energy_by_finite_differences(xe, ue, eta):
-    """Eq. (oneptenergy) evaluated from the interpolants x(q), u(q) by central differences."""
+def _energy_by_finite_differences(xe, ue, eta, q0=QC, w=1.0):
+    """Eq. (oneptenergy) at point q0 with weight w, evaluated from the interpolants x(q), u(q)
+    by central differences."""
     h = 1e-4
 
     def interp(vals, q):
@@ -65,12 +67,12 @@ def _energy_by_finite_differences(xe, ue, eta):
     dx = np.empty((3, 3)); du = np.empty((3, 3))
     for m in range(3):
         e = np.zeros(3); e[m] = h
-        qp, qm = np.array(QC) + e, np.array(QC) - e
+        qp, qm = np.array(q0) + e, np.array(q0) - e
         dx[:, m] = (interp(xe, qp) - interp(xe, qm)) / (2 * h)
         du[:, m] = (interp(ue, qp) - interp(ue, qm)) / (2 * h)
     gradu = du @ np.linalg.inv(dx)              # d u_c / d x_m
     eps = 0.5 * (gradu + gradu.T)
-    V = abs(np.linalg.det(dx)) * 1.0            # w_q = 1 (reference wedge volume)
+    V = abs(np.linalg.det(dx)) * w              # w_q = 1 (reference wedge volume) for q_c
     return V * eta * (2.0 * np.sum(eps * eps) - 2.0 / 3.0 * np.trace(gradu) ** 2)
 
 
@@ -186,3 +188,84 @@ def test_stabilised_element_matrix():
                 got = v.ravel() @ (As[e] - A[e]) @ v.ravel()
                 want = eps * sum((g[e, mm] @ w[m]) ** 2 for mm in range(2))
                 assert abs(got - want) <= 1e-12 * abs(want)
+
+
+# --------------------------------------------------------------- second radial quadrature point
+def test_two_point_rule_energy_and_volume():
+    """Two radial points: u^T A_e u is the sum of Eq. (oneptenergy) at (1/3, 1/3, -/+ 1/sqrt 3)
+    with weights 1/2 (finite differences of the interpolants), and the weights times |det J|
+    add up to |det M| (r_t^3 - r_b^3) / 6: the exact integral of |det J| = rho^2 h |det M| along
+    the wedge's centre line (M = [s1 - s0, s2 - s0, (s0 + s1 + s2) / 3] from the unit directions)."""
+    x, eta = random_wedges()
+    rule = quadrature_rule(2)
+    z = 1.0 / np.sqrt(3.0)
+    assert [p for p, _ in rule] == [(1 / 3, 1 / 3, -z), (1 / 3, 1 / 3, z)] and [w for _, w in rule] == [0.5, 0.5]
+    A2 = viscous_element_matrix_rule(x, eta, rule)
+    rng = np.random.default_rng(6)
+    for e in range(x.shape[0]):
+        for _ in range(3):
+            u = rng.normal(size=(6, 3))
+            E = sum(_energy_by_finite_differences(x[e], u, eta[e], p, w) for p, w in rule)
+            assert abs(u.ravel() @ A2[e] @ u.ravel() - E) <= 1e-7 * abs(E)
+        rb, rt = np.linalg.norm(x[e, 0]), np.linalg.norm(x[e, 3])
+        s = x[e, :3] / rb
+        M = np.stack([s[1] - s[0], s[2] - s[0], s.mean(axis=0)], axis=1)
+        V = sum(geometry_at(x[e:e + 1], p, w)[1][0] for p, w in rule)
+        want = abs(np.linalg.det(M)) * (rt ** 3 - rb ** 3) / 6.0
+        assert abs(V - want) <= 1e-13 * want
+
+
+def test_two_point_rule_is_exact_in_zeta():
+    """On the wedge's centre line the integrand is a quadratic in zeta (rho^2 from |det J| against
+    1 / rho^2, 1 / rho or 1 from the gradients, times the radial basis), so the two-point rule
+    equals a six-point Gauss-Legendre rule in zeta to rounding; the one-point rule does not."""
+    x, eta = random_wedges()
+    zg, wg = np.polynomial.legendre.leggauss(6)
+    rule6 = [((1 / 3, 1 / 3, z), 0.5 * w) for z, w in zip(zg, wg)]
+    for div_term in (True, False):
+        A6 = viscous_element_matrix_rule(x, eta, rule6, div_term)
+        A2 = viscous_element_matrix_rule(x, eta, quadrature_rule(2), div_term)
+        A1 = viscous_element_matrix_rule(x, eta, quadrature_rule(1), div_term)
+        scale = np.abs(A6).max()
+        assert np.abs(A2 - A6).max() <= 1e-13 * scale
+        assert np.abs(A1 - A6).max() >= 1e-3 * scale
+
+
+def test_two_point_rank_and_kernel():
+    """With two radial points five of the six hourglass modes of Eq. (hourglass) get energy.  The
+    one left is the twist u = zeta (sbar x s(xi, eta)) / 2 (top layer turned about the wedge axis
+    sbar, bottom layer back): its lateral gradient is skew and its radial derivative vanishes on
+    the centre line, where the rule samples.  So the element matrix is symmetric positive
+    semi-definite of rank 11 without the -2/3 term (18 - 6 rigid motions - the twist) and 10 with
+    it (the dilatation x too), and on the hourglass span it has rank 5."""
+    x, eta = random_wedges()
+    A = viscous_element_matrix_rule(x, eta, quadrature_rule(2))
+    A0 = viscous_element_matrix_rule(x, eta, quadrature_rule(2), div_term=False)
+    w = hourglass_vectors()
+    for e in range(x.shape[0]):
+        scale = np.abs(A[e]).max()
+        np.testing.assert_allclose(A[e], A[e].T, atol=1e-15 * scale)
+        assert np.linalg.matrix_rank(A[e], tol=1e-10 * scale) == 10
+        assert np.linalg.matrix_rank(A0[e], tol=1e-10 * scale) == 11
+        assert np.linalg.eigvalsh(A0[e]).min() >= -1e-12 * scale
+        kernel = []
+        for d in range(3):
+            t = np.zeros((6, 3)); t[:, d] = 1.0
+            kernel.append(t.ravel())
+        for om in np.eye(3):
+            kernel.append(np.cross(om[None, :], x[e]).ravel())
+        su = x[e, :3] / np.linalg.norm(x[e, 0])
+        tw = 0.5 * np.cross(su.mean(axis=0)[None, :], su)
+        kernel.append(np.concatenate([-tw, tw]).ravel())
+        K = np.stack(kernel)
+        assert np.linalg.matrix_rank(K) == 7
+        assert np.abs(A0[e] @ K.T).max() <= 1e-13 * scale
+        assert np.abs(A[e] @ K.T).max() <= 1e-13 * scale
+        assert np.abs(A[e] @ x[e].ravel()).max() <= 1e-13 * scale
+        Hs = []
+        for m in range(2):
+            for d in range(3):
+                v = np.zeros((6, 3)); v[:, d] = w[m]
+                Hs.append(v.ravel())
+        Hs = np.stack(Hs)
+        assert np.linalg.matrix_rank(Hs @ A0[e] @ Hs.T, tol=1e-10 * scale) == 5

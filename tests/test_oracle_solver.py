@@ -72,14 +72,15 @@ def test_vcycle_is_a_convergent_iteration(hier):
 
 
 def test_hourglass_control_restores_vcycle_contraction():
-    """Eq. (hgstab): with hourglass control the stand-alone V-cycle contracts far faster than
-    with the plain one-point rule (Fig. 2, left), on the same shell and viscosity."""
+    """Eq. (hgstab): with hourglass control, and with a second radial quadrature point, the
+    stand-alone V-cycle contracts far faster than with the plain one-point rule (Fig. 2, left),
+    on the same shell and viscosity."""
     m = ShellMesh(3, 9, 0.55, 1.0)
     eta = inputs.lognormal_viscosity(m.n_wedges, 3, 0.0)
     rates = {}
-    for kappa in (0.0, 0.1):
+    for kappa, quad in ((0.0, 1), (0.1, 1), (0.0, 2)):
         H = Hierarchy(3, 9, 0.55, 1.0, eta, bc=(O.NOSLIP, O.FREE), coarse_rtol=1e-12, coarse_max_iters=1000,
-                      kappa=kappa)
+                      kappa=kappa, quad=quad)
         H.setup(inputs.normal(3 * m.n_nodes, 4))
         K = H.K[0]
         b = inputs.normal(K.shape[0], 7)
@@ -88,8 +89,8 @@ def test_hourglass_control_restores_vcycle_contraction():
         for _ in range(8):
             x = x + H.vcycle(b - K @ x)
             norms.append(np.linalg.norm(b - K @ x))
-        rates[kappa] = norms[-1] / norms[-2]
-    assert rates[0.0] > 0.6 and rates[0.1] < 0.45, rates
+        rates[(kappa, quad)] = norms[-1] / norms[-2]
+    assert rates[(0.0, 1)] > 0.6 and rates[(0.1, 1)] < 0.45 and rates[(0.0, 2)] < 0.45, rates
 
 
 def test_direct_solve_and_invariants():
