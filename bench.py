@@ -214,10 +214,11 @@ def layout_temperature(tn, m, noise_seed=None, noise_scale=0.01):
     return T
 
 
-def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=0.0):
+def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=0.0, quad=1):
     """One Stokes solve to 1e-8 (multigrid set-up excluded from the time).  Returns the stats and
     the solution (u, p) on the unique nodes, as host FP64 arrays."""
-    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, eta_storage=eta_storage, hg_kappa=hg_kappa)
+    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, eta_storage=eta_storage, hg_kappa=hg_kappa,
+                          radial_quad_points=quad)
     try:
         info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
         Td = torch.tensor(layout_temperature(tn, m), device=dev)
@@ -497,11 +498,19 @@ def main():
                 hbf["p_rel_diff_vs_fp64"] = float(np.linalg.norm(tbf[1] - t64[1]) / np.linalg.norm(t64[1]))
                 # discretisation change of the control: its FP64 solution against the plain one
                 h64["u_rel_diff_vs_plain"] = float(np.linalg.norm(t64[0] - s64[0]) / np.linalg.norm(s64[0]))
+                # the other remedy of Sec. 4: the second radial quadrature point, FP64 and FP64
+                # FGMRES with the FP32 preconditioner (BF16 viscosity in it)
+                q64, u64 = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64, quad=2)
+                qpc, upc = solve_case(tn, torch, dev, lvl, nr, E, 7e3, tn.TN_SOLVE_F64_PREC32,
+                                      eta_storage=tn.TN_ETA_BF16, quad=2)
+                q64["u_rel_diff_vs_plain"] = float(np.linalg.norm(u64[0] - s64[0]) / np.linalg.norm(s64[0]))
+                qpc["u_rel_diff_vs_fp64"] = float(np.linalg.norm(upc[0] - u64[0]) / np.linalg.norm(u64[0]))
                 solves[name] = {"fp64": r64, "mixed": rmx, "mixed_bf16_eta": rbf,
                                 "mixed_speedup": r64["seconds"] / rmx["seconds"],
                                 "mixed_bf16_eta_speedup": r64["seconds"] / rbf["seconds"],
                                 "hg%.1f_fp64" % HG_KAPPA: h64, "hg%.1f_mixed_bf16_eta" % HG_KAPPA: hbf,
                                 "hg%.1f_fp64_prec32_bf16_eta" % HG_KAPPA: hpc,
+                                "quad2_fp64": q64, "quad2_fp64_prec32_bf16_eta": qpc,
                                 "hg_mixed_bf16_eta_speedup_vs_plain_fp64": r64["seconds"] / hbf["seconds"]}
             line["solves"] = solves
             if args.serve_requests > 0:

@@ -101,6 +101,11 @@ typedef struct {
                        * element matrices get eps_e sum_m,d (g_m x e_d)(g_m x e_d)^T with
                        * eps_e = hg_kappa tr(A_e) / 18 and g_m the hourglass vectors of Eq. hourglass
                        * minus their physical linear part (rigid motions keep zero energy) */
+  int radial_quad_points; /* quadrature of the A block (0 or 1 = default: one point at the wedge
+                       * barycentre, Sec. 4; 2: the second radial point, the two-point Gauss rule in
+                       * the radial reference coordinate at the lateral barycentre, weights 1/2, one
+                       * viscosity per wedge).  B, B^T and the pressure mass keep the one-point rule.
+                       * 2 together with hg_kappa > 0 is TN_EINVAL (two remedies of the same modes). */
 } tn_mesh_opts;
 
 typedef struct {
@@ -322,6 +327,7 @@ typedef struct {
   int keep_solutions;      /* 1: keep a host copy of every solution for tn_server_solution (0) */
   int eta_storage;         /* tn_mesh_opts.eta_storage of every request's mesh (TN_ETA_F32) */
   double hg_kappa;         /* tn_mesh_opts.hg_kappa of every request's mesh (0: the plain one-point A) */
+  int radial_quad_points;  /* tn_mesh_opts.radial_quad_points of every request's mesh (1) */
 } tn_server_opts;
 typedef struct {
   int lateral_level, radial_layers;

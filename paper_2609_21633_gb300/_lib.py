@@ -27,7 +27,8 @@ class TnError(RuntimeError):
 
 class tn_mesh_opts(ctypes.Structure):
     _fields_ = [("bc_inner", ctypes.c_int), ("bc_outer", ctypes.c_int), ("div_term", ctypes.c_int),
-                ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int), ("hg_kappa", ctypes.c_double)]
+                ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int), ("hg_kappa", ctypes.c_double),
+                ("radial_quad_points", ctypes.c_int)]
 
 
 class tn_level_info(ctypes.Structure):
@@ -65,7 +66,7 @@ TN_SOLVE_F64, TN_SOLVE_MIXED, TN_SOLVE_F64_PREC32 = 0, 1, 2
 class tn_server_opts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("mode", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("keep_solutions", ctypes.c_int), ("eta_storage", ctypes.c_int),
-                ("hg_kappa", ctypes.c_double)]
+                ("hg_kappa", ctypes.c_double), ("radial_quad_points", ctypes.c_int)]
 
 
 class tn_request(ctypes.Structure):
@@ -167,8 +168,9 @@ def _prec(dtype):
 
 
 def tn_mesh_create(lateral_level, radial_layers, r_in, r_out, bc_inner=TN_BC_FREESLIP, bc_outer=TN_BC_FREESLIP,
-                   div_term=True, max_levels=0, eta_storage=0, hg_kappa=0.0):
-    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage, float(hg_kappa))
+                   div_term=True, max_levels=0, eta_storage=0, hg_kappa=0.0, radial_quad_points=1):
+    opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage, float(hg_kappa),
+                        int(radial_quad_points))
     out = P()
     _check(lib().tn_mesh_create(lateral_level, radial_layers, r_in, r_out, ctypes.byref(opts), ctypes.byref(out)))
     return out

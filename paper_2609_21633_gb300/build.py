@@ -12,9 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIBNAME = "libterra_wedge.so"
-# (source, extra flags): kernels.cu is compiled in three parts (the FP64 and the FP32 A-apply
-# launchers apart)
+# (source, extra flags): kernels.cu is compiled in five parts (the FP64 and the FP32 A-apply
+# launchers of each quadrature rule apart)
 SOURCES = [("kernels.cu", ["-DTN_PART=1"]), ("kernels.cu", ["-DTN_PART=2"]), ("kernels.cu", ["-DTN_PART=3"]),
+           ("kernels.cu", ["-DTN_PART=4"]), ("kernels.cu", ["-DTN_PART=5"]),
            ("solver.cu", []), ("server.cu", []), ("api.cu", []), ("noalloc.cu", []), ("mesh.cpp", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -211,11 +211,16 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   if (radial_layers < 3 || (radial_layers - 1) % 2 != 0)
     return inval("tn_mesh_create: radial_layers must be >= 3 with radial_layers - 1 even");
   if (!(r_in > 0.0) || !(r_out > r_in)) return inval("tn_mesh_create: need 0 < r_in < r_out");
-  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, TN_ETA_F32, 0.0};
+  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, TN_ETA_F32, 0.0, 1};
   if (opts) o = *opts;
+  if (o.radial_quad_points == 0) o.radial_quad_points = 1;
+  if (o.radial_quad_points != 1 && o.radial_quad_points != 2)
+    return inval("tn_mesh_create: radial_quad_points must be 1 or 2");
   if (o.eta_storage != TN_ETA_F32 && o.eta_storage != TN_ETA_BF16 && o.eta_storage != TN_ETA_F16)
     return inval("tn_mesh_create: unknown viscosity storage");
   if (!(o.hg_kappa >= 0.0) || o.hg_kappa > 1e6) return inval("tn_mesh_create: hg_kappa must be in [0, 1e6]");
+  if (o.radial_quad_points == 2 && o.hg_kappa > 0.0)
+    return inval("tn_mesh_create: hourglass control and the second radial point exclude each other");
   if ((o.bc_inner != TN_BC_FREESLIP && o.bc_inner != TN_BC_NOSLIP) ||
       (o.bc_outer != TN_BC_FREESLIP && o.bc_outer != TN_BC_NOSLIP))
     return inval("tn_mesh_create: unknown boundary condition");
@@ -236,6 +241,7 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   m->div_term = o.div_term ? 1 : 0;
   m->eta_storage = o.eta_storage;
   m->hg_kappa = o.hg_kappa;
+  m->quad = o.radial_quad_points;
   m->r_in = r_in;
   m->r_out = r_out;
   cudaGetDevice(&m->device);
@@ -244,6 +250,7 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
     m->lv.emplace_back();
     tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage, m->div_term);
     m->lv.back().hg_kappa = o.hg_kappa;
+    m->lv.back().quad = o.radial_quad_points;
     if (s != TN_OK) {
       std::string msg = tn_last_error();
       tn_mesh_destroy(m);

@@ -52,6 +52,8 @@ struct Level {
   int eta_kind = TN_ETA_F32;
   // Hourglass control of the A block (0: off): eps_e = hg_kappa tr(A_e) / 18.
   double hg_kappa = 0;
+  // Radial quadrature points of the A block (1: the barycentre; 2: two-point Gauss in zeta).
+  int quad = 1;
   // Per-triangle factors of the diagonal of A ([24][n_tri], see OpDiag), for div term dcoef_div.
   double* dcoef64 = nullptr;
   float* dcoef32 = nullptr;
@@ -95,6 +97,7 @@ struct tn_mesh {
   bool eta_set = false;
   int eta_storage = TN_ETA_F32;
   double hg_kappa = 0;
+  int quad = 1;
   int device = 0;
   double r_in = 0, r_out = 0;
 };

@@ -34,9 +34,10 @@
 
 #include "internal.h"
 
-// The file is compiled three times: TN_PART 1 holds everything but the A-apply launchers, TN_PART 2
-// the FP64 and TN_PART 3 the FP32 A-apply launchers (their many tile-kernel instantiations then
-// compile in parallel); 0 = all.
+// The file is compiled five times: TN_PART 1 holds everything but the A-apply launchers, TN_PART 2
+// the FP64 and TN_PART 3 the FP32 A-apply launchers, TN_PART 4 and 5 those of the A apply with
+// the second radial quadrature point (their many tile-kernel instantiations then compile in
+// parallel); 0 = all.
 #ifndef TN_PART
 #define TN_PART 0
 #endif
@@ -462,6 +463,88 @@ struct OpA<float, true> {
   }
 };
 
+// Viscous block with a second radial quadrature point: the two-point Gauss rule in zeta at the
+// lateral barycentre, zeta = -/+ z (z = 1/sqrt 3), weight 1/2 each, one eta per wedge.  At
+// zeta the scaled strain is G0 + zeta G1: G0 is the one-point G' above and
+// G1 = b_xi M^-1[0,:] + b_eta M^-1[1,:] + (a_zeta / 3) M^-1[2,:], b_xi = d_c1 - d_c0,
+// b_eta = d_c2 - d_c0 (the lateral gradient of the radial differences; r_q = r + zeta / 3), and
+// V_q w0_q^2 = vol w0^2 / 2 at both points.  Summed over the two points, with S0 the stress of
+// G0 (factor vol w0^2 |det M| eta) and S1' that of G1 with a third of that factor, node
+// (a, bottom / top) receives X_a -/+ D_a: X = (-S0 m0 - S0 m1, S0 m0, S0 m1) as in OpA and
+// D_a = (-(S1' m0 + S1' m1), S1' m0, S1' m1)_a + S0 r m2 + S1' m2 / 3.
+template <typename T>
+struct OpA2 {
+  static constexpr int NIN = 3, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
+  using Col = NoCol;
+  int div_term;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ static void stress(const T (&G)[3][3], T f, int div_term, T (&S)[3][3]) {
+    const T f2 = f + f;
+    if (div_term) {
+      const T vt = (f * (T)(-2.0 / 3.0)) * ((G[0][0] + G[1][1]) + G[2][2]);
+      S[0][0] = f2 * G[0][0] + vt, S[1][1] = f2 * G[1][1] + vt, S[2][2] = f2 * G[2][2] + vt;
+    } else {
+      S[0][0] = f2 * G[0][0], S[1][1] = f2 * G[1][1], S[2][2] = f2 * G[2][2];
+    }
+    S[0][1] = S[1][0] = f * (G[0][1] + G[1][0]);
+    S[0][2] = S[2][0] = f * (G[0][2] + G[2][0]);
+    S[1][2] = S[2][1] = f * (G[1][2] + G[2][1]);
+  }
+  __device__ __forceinline__ void cell(const T (&s)[4][3], const T (&dd)[4][3], const T (&Mi)[2][9],
+                                       const T (&dM)[2], const T* lc, const T (&eta)[2], T (&accb)[4][3],
+                                       T (&acct)[4][3], const Col&) const {
+    const T r = lc[4], vw2 = lc[5];
+    T X[4][3], Y[4][3];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const T* M = Mi[w];
+      const T mr[3] = {r * M[6], r * M[7], r * M[8]};
+      const T m3[3] = {M[6] * (T)(1.0 / 3.0), M[7] * (T)(1.0 / 3.0), M[8] * (T)(1.0 / 3.0)};
+      T S0[3][3], S1[3][3];
+      {
+        T G0[3][3], G1[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c], az = (dd[c0][c] + dd[c1][c]) + dd[c2][c];
+          const T bx = dd[c1][c] - dd[c0][c], by = dd[c2][c] - dd[c0][c];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            G0[c][x] = ax * M[x] + ay * M[3 + x] + az * mr[x];
+            G1[c][x] = bx * M[x] + by * M[3 + x] + az * m3[x];
+          }
+        }
+        const T ve = vw2 * dM[w] * eta[w];
+        stress(G0, ve, div_term, S0);
+        stress(G1, ve * (T)(1.0 / 3.0), div_term, S1);
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T h0 = S0[c][0] * M[0] + S0[c][1] * M[1] + S0[c][2] * M[2];
+        const T h1 = S0[c][0] * M[3] + S0[c][1] * M[4] + S0[c][2] * M[5];
+        const T k0 = S1[c][0] * M[0] + S1[c][1] * M[1] + S1[c][2] * M[2];
+        const T k1 = S1[c][0] * M[3] + S1[c][1] * M[4] + S1[c][2] * M[5];
+        const T hc = (S0[c][0] * mr[0] + S0[c][1] * mr[1] + S0[c][2] * mr[2]) +
+                     (S1[c][0] * m3[0] + S1[c][1] * m3[1] + S1[c][2] * m3[2]);
+        Y[c0][c] = hc - (k0 + k1);
+        X[c0][c] = -(h0 + h1);
+        if (w == 0) {
+          Y[c1][c] = hc + k0, Y[c2][c] = hc + k1;
+          X[c1][c] = h0, X[c2][c] = h1;
+        } else {
+          Y[c1][c] += hc + k0, Y[c2][c] += hc + k1;
+          X[c1][c] += h0, X[c2][c] += h1;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) accb[q][c] = X[q][c] - Y[q][c], acct[q][c] = X[q][c] + Y[q][c];
+  }
+};
+
 // Fine-level divergence: each of the six nodes of a wedge gets -V tr(grad u)(q_c) / 6
 // (pressure test function psi = N_n with N_n(q_c) = 1/6); tr grad u = w0 tr G'.
 template <typename T>
@@ -654,6 +737,62 @@ struct OpDiagG {
           for (int c = 0; c < 3; ++c) {
             T v = ve * (g2 + third * (g[c] * g[c]));
             if constexpr (HG) v += hs;
+            if (side == 0) accb[q][c] += v;
+            else acct[q][c] += v;
+          }
+        }
+      }
+    }
+  }
+};
+
+// Diagonal with the second radial quadrature point (see OpA2): node (a, side) of a wedge gets
+// ve (|g0|^2 + c g0_d^2) + ve / 3 (|g1|^2 + c g1_d^2), ve = vol w0^2 |det M| eta, with the
+// one-point gradient g0 = l_a -/+ r m2 and g1 = l_a + m2 / 3 (the same on both sides), l_a the
+// lateral gradient (-(m0 + m1), m0, m1)_a: the two points' gradients are g0 +/- z g1 (signed by
+// side), whose squares sum to 2 (|g0|^2 + |g1|^2 / 3) times the weight 1/2.
+template <typename T>
+struct OpDiag2 {
+  static constexpr int NIN = 1, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false;
+  using Col = NoCol;
+  int div_term;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&Mi)[2][9], const T (&dM)[2],
+                                       const T* lc, const T (&eta)[2], T (&accb)[4][3], T (&acct)[4][3],
+                                       const Col&) const {
+    const T r = lc[4], vw2 = lc[5];
+    const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) accb[q][c] = acct[q][c] = 0;
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const T* M = Mi[w];
+      const T ve = vw2 * dM[w] * eta[w], ve3 = ve * (T)(1.0 / 3.0);
+      T lat[3][3], mr[3], m3[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        lat[0][x] = -(M[x] + M[3 + x]), lat[1][x] = M[x], lat[2][x] = M[3 + x];
+        mr[x] = r * M[6 + x], m3[x] = M[6 + x] * (T)(1.0 / 3.0);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = kCorner[w][a];
+        T g1[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) g1[x] = lat[a][x] + m3[x];
+        const T n1 = g1[0] * g1[0] + g1[1] * g1[1] + g1[2] * g1[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          T g[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) g[x] = side == 0 ? lat[a][x] - mr[x] : lat[a][x] + mr[x];
+          const T n0 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const T v = ve * (n0 + third * (g[c] * g[c])) + ve3 * (n1 + third * (g1[c] * g1[c]));
             if (side == 0) accb[q][c] += v;
             else acct[q][c] += v;
           }
@@ -1534,10 +1673,23 @@ __device__ __forceinline__ T hg_node_diag(const T (&Mi)[9], T dM, T et, const T*
   return eps * (a == 0 ? (T)2 : (T)5) * (kz * kz);
 }
 
+// Second radial quadrature point (see OpDiag2): the wedge adds ve / 3 (|g1|^2 I + c g1 g1^T) with
+// g1 = w0 (l_a + m2 / 3) to the node block, the same for its bottom and top node.
+template <typename T>
+__device__ __forceinline__ void add_second_point(const T (&Mi)[9], T cxi, T ceta, T c2, T ve, T third, T& alpha,
+                                                 T (&B)[6]) {
+  T g[3];
+  for (int x = 0; x < 3; ++x) g[x] = Mi[x] * cxi + Mi[3 + x] * ceta + Mi[6 + x] * c2;
+  const T v3 = ve * (T)(1.0 / 3.0), tv = v3 * third;
+  alpha += v3 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
+  B[3] += tv * g[0] * g[1], B[4] += tv * g[0] * g[2], B[5] += tv * g[1] * g[2];
+}
+
 template <typename T>
 __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
-                         const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, T* d0, T* d1,
-                         T* d2) {
+                         const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, int nq, T* d0,
+                         T* d1, T* d2) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)10 * 2 * M * M;
@@ -1573,6 +1725,7 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
       const T tv = ve * third;
       B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
       B[3] += tv * g[0] * g[1], B[4] += tv * g[0] * g[2], B[5] += tv * g[1] * g[2];
+      if (nq == 2) add_second_point(Mi, w0 * gxi[a], w0 * geta[a], w0 * (T)(1.0 / 3.0), ve, third, alpha, B);
     }
   }
   T A[3][3] = {{alpha + B[0], B[3], B[4]}, {B[3], alpha + B[1], B[5]}, {B[4], B[5], alpha + B[2]}};
@@ -1613,8 +1766,8 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
 // P A_partial P per diamond and the identity part is added once by k_interface_block.
 template <typename T>
 __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict__ lay, EtaView<T> eta,
-                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, T* b0, T* b1,
-                          T* b2, T* b3, T* b4, T* b5) {
+                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, int nq, T* b0,
+                          T* b1, T* b2, T* b3, T* b4, T* b5) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)10 * D.n_r * M * M;
@@ -1647,6 +1800,7 @@ __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict
       const T tv = ve * third;
       B[0] += tv * g[0] * g[0], B[1] += tv * g[1] * g[1], B[2] += tv * g[2] * g[2];
       B[3] += tv * g[0] * g[1], B[4] += tv * g[0] * g[2], B[5] += tv * g[1] * g[2];
+      if (nq == 2) add_second_point(Mi, w0 * gxi[a], w0 * geta[a], w0 * (T)(1.0 / 3.0), ve, third, alpha, B);
     }
   }
   T A[3][3] = {{alpha + B[0], B[3], B[4]}, {B[3], alpha + B[1], B[5]}, {B[4], B[5], alpha + B[2]}};
@@ -1981,11 +2135,23 @@ cudaError_t apply_A_hg(const Level& L, BC bc, int div_term, const T* const* u, T
   return launch_tile<T, OpA<T, HG>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, etav<T>(L), st, skip);
 }
 
+// The tile launches of the A apply with the second radial quadrature point (OpA2; their own
+// translation units): plain, and with one of the fused epilogues.
+template <typename T>
+cudaError_t apply_A_q2(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
+                       const int* skip);
+template <typename T>
+cudaError_t apply_A_q2_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
+                           T* const* t, cudaStream_t st, const int* skip);
+// Shared-memory opt-ins of the OpA2 tile kernels (see prepare_tile_kernels).
+cudaError_t prepare_tile_kernels_q2();
+
 template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                            const int* skip) {
-  cudaError_t e = L.hg_kappa > 0 ? apply_A_hg<T, true>(L, bc, div_term, u, y, st, skip)
-                                 : apply_A_hg<T, false>(L, bc, div_term, u, y, st, skip);
+  cudaError_t e = L.quad == 2      ? apply_A_q2<T>(L, bc, div_term, u, y, st, skip)
+                  : L.hg_kappa > 0 ? apply_A_hg<T, true>(L, bc, div_term, u, y, st, skip)
+                                   : apply_A_hg<T, false>(L, bc, div_term, u, y, st, skip);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 1, y, u, st, skip);
 }
@@ -2007,8 +2173,9 @@ cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T
 template <typename T>
 cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
                                T* const* t, cudaStream_t st, const int* skip) {
-  cudaError_t e = L.hg_kappa > 0 ? apply_A_epi_hg<T, true>(L, bc, div_term, epi, in, E, t, st, skip)
-                                 : apply_A_epi_hg<T, false>(L, bc, div_term, epi, in, E, t, st, skip);
+  cudaError_t e = L.quad == 2      ? apply_A_q2_epi<T>(L, bc, div_term, epi, in, E, t, st, skip)
+                  : L.hg_kappa > 0 ? apply_A_epi_hg<T, true>(L, bc, div_term, epi, in, E, t, st, skip)
+                                   : apply_A_epi_hg<T, false>(L, bc, div_term, epi, in, E, t, st, skip);
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)L.n_groups * L.n_r;
   if (n == 0) return cudaSuccess;
@@ -2049,7 +2216,9 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
   const T hgk = (T)hg_coef(L, div_term);
   const bool hg = L.hg_kappa > 0;
   cudaError_t e;
-  if constexpr (sizeof(T) == 8) {  // FP64: per-triangle factor table
+  if (L.quad == 2) {  // second radial quadrature point: gradient form, both precisions
+    e = launch_tile<T, OpDiag2<T>, 0>(L, bc, OpDiag2<T>{div_term}, none, d, etav<T>(L), st);
+  } else if constexpr (sizeof(T) == 8) {  // FP64: per-triangle factor table
     if (!L.dcoef64 || L.dcoef_div != div_term) return cudaErrorInvalidValue;  // built with the level
     const T* coef = Tab<T>::dcoef(L);
     const int nt = (int)L.n_tri;
@@ -2064,7 +2233,7 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
   k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
-                                            bc.out, div_term, hgk, d[0], d[1], d[2]);
+                                            bc.out, div_term, hgk, L.quad, d[0], d[1], d[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 2, d, nullptr, st);
@@ -2075,7 +2244,8 @@ cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b,
   Dims D = dims(L);
   const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
   k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
-                                             bc.out, div_term, (T)hg_coef(L, div_term), b[0], b[1], b[2], b[3], b[4],
+                                             bc.out, div_term, (T)hg_coef(L, div_term), L.quad, b[0], b[1], b[2], b[3],
+                                             b[4],
                                              b[5]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -2233,14 +2403,10 @@ TN_INST(float)
                                          const int*);                                                            \
   template cudaError_t launch_apply_A_epi<T>(const Level&, BC, int, int, const T* const*, const EpiArgs<T>&,     \
                                              T* const*, cudaStream_t, const int*);
-#if TN_PART == 0 || TN_PART == 2
-TN_INST_A(double)
-
 // Opt the tile kernels that need more than 48 KB of shared memory (FP64 A on 16 x 32 tiles,
-// every epilogue, with and without hourglass control) into their dynamic size.
-template <bool HG, int EPI>
+// every epilogue, each A op) into their dynamic size.
+template <typename Op, int EPI>
 cudaError_t set_wide_a_attr() {
-  using Op = OpA<double, HG>;
   constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
   constexpr size_t sh = TileSmem<double, Op, TILE, 2 * TILE>::bytes;
   if (sh > 48 * 1024) {
@@ -2255,11 +2421,21 @@ cudaError_t set_wide_a_attr() {
   return cudaSuccess;
 }
 
+template <typename Op>
+cudaError_t set_wide_attrs() {
+  const cudaError_t e[4] = {set_wide_a_attr<Op, EPI_NONE>(), set_wide_a_attr<Op, EPI_RESID>(),
+                            set_wide_a_attr<Op, EPI_CHEB1>(), set_wide_a_attr<Op, EPI_CHEB2>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+
+#if TN_PART == 0 || TN_PART == 2
+TN_INST_A(double)
+
 cudaError_t prepare_tile_kernels() {
-  const cudaError_t e[8] = {set_wide_a_attr<false, EPI_NONE>(), set_wide_a_attr<false, EPI_RESID>(),
-                            set_wide_a_attr<false, EPI_CHEB1>(), set_wide_a_attr<false, EPI_CHEB2>(),
-                            set_wide_a_attr<true, EPI_NONE>(),  set_wide_a_attr<true, EPI_RESID>(),
-                            set_wide_a_attr<true, EPI_CHEB1>(),  set_wide_a_attr<true, EPI_CHEB2>()};
+  const cudaError_t e[3] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
+                            prepare_tile_kernels_q2()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
@@ -2269,5 +2445,45 @@ cudaError_t prepare_tile_kernels() {
 TN_INST_A(float)
 #endif
 #undef TN_INST_A
+
+// ------------------------------------------------------------ A with the second radial point
+// Defined in parts 4 and 5 only: the other parts link to these instantiations (an implicit one
+// elsewhere would launch that part's own copy of the tile kernels, without the shared-memory
+// opt-in of prepare_tile_kernels_q2).
+#if TN_PART == 0 || TN_PART == 4 || TN_PART == 5
+template <typename T>
+cudaError_t apply_A_q2(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
+                       const int* skip) {
+  return launch_tile<T, OpA2<T>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, OpA2<T>{div_term}, u, y, etav<T>(L), st, skip);
+}
+
+template <typename T>
+cudaError_t apply_A_q2_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
+                           T* const* t, cudaStream_t st, const int* skip) {
+  using Op = OpA2<T>;
+  const Op op{div_term};
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  switch (epi) {
+    case EPI_RESID: return launch_tile<T, Op, F, EPI_RESID>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    case EPI_CHEB1: return launch_tile<T, Op, F, EPI_CHEB1>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    case EPI_CHEB2: return launch_tile<T, Op, F, EPI_CHEB2>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+#endif
+
+#define TN_INST_Q2(T)                                                                                            \
+  template cudaError_t apply_A_q2<T>(const Level&, BC, int, const T* const*, T* const*, cudaStream_t, const int*); \
+  template cudaError_t apply_A_q2_epi<T>(const Level&, BC, int, int, const T* const*, const EpiArgs<T>&,         \
+                                         T* const*, cudaStream_t, const int*);
+#if TN_PART == 0 || TN_PART == 4
+TN_INST_Q2(double)
+cudaError_t prepare_tile_kernels_q2() { return set_wide_attrs<OpA2<double>>(); }
+#endif
+#if TN_PART == 0 || TN_PART == 5
+TN_INST_Q2(float)
+#endif
+#undef TN_INST_Q2
 
 }  // namespace tn

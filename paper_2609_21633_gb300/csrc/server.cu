@@ -170,7 +170,8 @@ void run_job(tn_server* S, Job* J, tn_mesh* mesh, cudaStream_t st) {
   const tn_request& R = J->req;
   tn_status s = TN_OK;
   if (!mesh) {
-    tn_mesh_opts mo = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, S->opts.eta_storage, S->opts.hg_kappa};
+    tn_mesh_opts mo = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, S->opts.eta_storage, S->opts.hg_kappa,
+                       S->opts.radial_quad_points};
     s = tn_mesh_create(R.lateral_level, R.radial_layers, R.r_in, R.r_out, &mo, &mesh);
   }
   J->res.status = s;
@@ -288,6 +289,7 @@ tn_status tn_server_default_opts(tn_server_opts* o) {
   o->keep_solutions = 0;
   o->eta_storage = TN_ETA_F32;
   o->hg_kappa = 0.0;
+  o->radial_quad_points = 1;
   return TN_OK;
 }
 
@@ -297,7 +299,8 @@ tn_status tn_server_create(const tn_server_opts* opts, tn_server** out) {
   tn_server_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_active < 1 || o.max_active > 64 || !(o.memory_fraction > 0.0) || o.memory_fraction > 1.0 ||
-      !(o.rtol > 0.0) || o.eta_storage < TN_ETA_F32 || o.eta_storage > TN_ETA_F16 || !(o.hg_kappa >= 0.0)) {
+      !(o.rtol > 0.0) || o.eta_storage < TN_ETA_F32 || o.eta_storage > TN_ETA_F16 || !(o.hg_kappa >= 0.0) ||
+      o.radial_quad_points < 0 || o.radial_quad_points > 2 || (o.radial_quad_points == 2 && o.hg_kappa > 0.0)) {
     set_error("tn_server_create: invalid options");
     return TN_EINVAL;
   }

@@ -1342,6 +1342,7 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
       tn_status cs = create_level(*L, shapes[h].first, shapes[h].second, mesh->r_in, mesh->r_out, mesh->eta_storage,
                                   mesh->div_term);
       L->hg_kappa = mesh->hg_kappa;
+      L->quad = mesh->quad;
       m->owned_levels.push_back(L);
       if (cs != TN_OK) {
         mesh->mg = m;

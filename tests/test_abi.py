@@ -29,5 +29,9 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert b"lateral_level" in lib.tn_last_error()
     assert lib.tn_mesh_create(3, 4, 0.55, 1.0, None, ctypes.byref(out)) == tn.TN_EINVAL
     assert lib.tn_mesh_create(3, 5, 1.0, 0.55, None, ctypes.byref(out)) == tn.TN_EINVAL
+    for quad, kappa in ((3, 0.0), (-1, 0.0), (2, 0.3)):  # radial points 1 or 2, not with hourglass control
+        o = tn._lib.tn_mesh_opts(0, 0, 1, 0, 0, kappa, quad)
+        assert lib.tn_mesh_create(3, 5, 0.55, 1.0, ctypes.byref(o), ctypes.byref(out)) == tn.TN_EINVAL
+        assert b"radial" in lib.tn_last_error()
     assert lib.tn_mesh_info(None, 0, None) == tn.TN_EINVAL
     assert lib.tn_mesh_destroy(None) == tn.TN_OK

@@ -34,9 +34,9 @@ def tn():
 class FullShell:
     """The full-size mesh on both sides; only per-sample index maps are built on the host."""
 
-    def __init__(self, tn, kappa):
+    def __init__(self, tn, kappa, quad=1):
         self.tn = tn
-        self.m = tn.tn_mesh_create(LEVEL, NR, R_IN, R_OUT, hg_kappa=kappa)
+        self.m = tn.tn_mesh_create(LEVEL, NR, R_IN, R_OUT, hg_kappa=kappa, radial_quad_points=quad)
         self.info = tn.tn_mesh_info(self.m, 0)
         self.om = ShellMesh(LEVEL, NR, R_IN, R_OUT)
         N, P = self.info["N"], self.info["pitch"]
@@ -78,10 +78,10 @@ class FullShell:
         self.tn.tn_mesh_destroy(self.m)
 
 
-@pytest.fixture(scope="module", params=[0.0, 0.3], ids=["plain", "hg0.3"])
+@pytest.fixture(scope="module", params=[(0.0, 1), (0.3, 1), (0.0, 2)], ids=["plain", "hg0.3", "quad2"])
 def shell(tn, request):
-    s = FullShell(tn, request.param)
-    s.kappa = request.param
+    s = FullShell(tn, *request.param)
+    s.kappa, s.quad = request.param
     yield s
     s.close()
 
@@ -102,8 +102,8 @@ def test_sampled_A_and_diag_at_full_size(tn, shell):
     for c in range(3):
         u[c, near] = u_l[c][s.layout_of_nodes(near)]
     P = O.boundary_projectors(om)
-    want = O.apply_A_constrained(om, eta, u, P, wedges=wedges, kappa=s.kappa)[:, nodes]
-    want_d = O.diag_A_constrained(om, eta, P, wedges=wedges, kappa=s.kappa)[:, nodes]
+    want = O.apply_A_constrained(om, eta, u, P, wedges=wedges, kappa=s.kappa, quad=s.quad)[:, nodes]
+    want_d = O.diag_A_constrained(om, eta, P, wedges=wedges, kappa=s.kappa, quad=s.quad)[:, nodes]
     idx = s.layout_of_nodes(nodes)
     for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
         y = [torch.zeros(s.info["n_layout"], device="cuda", dtype=dtype) for _ in range(3)]
@@ -122,8 +122,8 @@ def test_sampled_A_and_diag_at_full_size(tn, shell):
 
 def test_symmetry_and_adjointness_at_full_size(tn, shell):
     s = shell
-    if s.kappa != 0.0:
-        pytest.skip("the B blocks do not depend on the hourglass control")
+    if s.kappa != 0.0 or s.quad != 1:
+        pytest.skip("the B blocks do not depend on the hourglass control or the quadrature of A")
     n = s.info["n_layout"]
     pinfo = tn.tn_mesh_info(s.m, 1)
     tn.tn_set_viscosity(s.m, torch.tensor(inputs.lognormal_viscosity(s.info["n_wedges"], 12), device="cuda"))

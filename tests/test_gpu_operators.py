@@ -35,10 +35,10 @@ class Case:
     """One mesh on both sides with random fields (seeded)."""
 
     def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0, eta_storage=0,
-                 hg_kappa=0.0):
+                 hg_kappa=0.0, quad=1):
         self.tn = tn
         self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term, eta_storage=eta_storage,
-                                   hg_kappa=hg_kappa)
+                                   hg_kappa=hg_kappa, radial_quad_points=quad)
         self.info = tn.tn_mesh_info(self.m, 0)
         self.om = ShellMesh(level, n_r, r_in, r_out)
         self.map = LayoutMap(self.info, self.om)
@@ -138,6 +138,40 @@ def test_hourglass_control_apply_and_diag(tn, level, n_r, bc, div_term):
     want_d = O.diag_A_constrained(c.om, c.eta, c.P, div_term=div_term, kappa=kappa)
     assert max_rel(np.stack([c.host(t) for t in d]), want_d) <= TOL64
     c.close()
+
+
+@pytest.mark.parametrize("level,n_r,bc,div_term", [(2, 5, "free/free", True), (3, 9, "noslip/free", True),
+                                                  (4, 17, "free/free", True), (4, 9, "free/free", False),
+                                                  (5, 9, "noslip/noslip", True), (5, 5, "free/free", True)])
+def test_second_radial_point_apply_and_diag(tn, level, n_r, bc, div_term):
+    """The A block with the second radial quadrature point (two-point Gauss rule in zeta): FP64
+    apply and diagonal at the FP64 bar, FP32 apply at the FP32 bar, against the oracle's element
+    matrices summed over the two points.  Level 5 runs the 16 x 32 halo-free FP64 tiles."""
+    c = Case(tn, level, n_r, BCS[bc], div_term=div_term, quad=2)
+    u = c.vec(23)
+    want = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=div_term, quad=2)
+    plain = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=div_term)
+    assert max_rel(plain, want) > 1e-3  # the rule changes the result
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        y = c.zeros(dtype=dtype)
+        tn.tn_apply_A(c.m, 0, [c.dev(u[i], dtype) for i in range(3)], y)
+        err = max_rel(np.stack([c.host(t) for t in y]), want)
+        print(f"l{level} n_r {n_r} {bc} div {div_term} {dtype}: {err:.2e}")
+        assert err <= tol, dtype
+    want_d = O.diag_A_constrained(c.om, c.eta, c.P, div_term=div_term, quad=2)
+    for dtype, tol in ((torch.float64, TOL64), (torch.float32, TOL32)):
+        d = c.zeros(dtype=dtype)
+        tn.tn_diag_A(c.m, 0, d)
+        assert max_rel(np.stack([c.host(t) for t in d]), want_d) <= tol, dtype
+    c.close()
+
+
+def test_second_radial_point_options(tn):
+    """radial_quad_points is 1 or 2 (0 means 1) and excludes hourglass control."""
+    for q, kappa in ((3, 0.0), (-1, 0.0), (2, 0.3)):
+        with pytest.raises(tn.TnError):
+            tn.tn_mesh_create(2, 5, 0.55, 1.0, radial_quad_points=q, hg_kappa=kappa)
+    tn.tn_mesh_destroy(tn.tn_mesh_create(2, 5, 0.55, 1.0, radial_quad_points=0))
 
 
 def _bf16_round(x32):

@@ -33,16 +33,18 @@ def from_dev(mp, ts):
     return np.stack([mp.from_layout(t.double().cpu().numpy()) for t in ts])
 
 
-@pytest.mark.parametrize("level,n_r,bc,kappa", [(3, 9, (1, 0), 0.0), (3, 9, (0, 0), 0.0), (4, 9, (0, 0), 0.0),
-                                               (2, 17, (0, 0), 0.0), (4, 5, (1, 0), 0.0), (3, 9, (1, 0), 0.3),
-                                               (4, 5, (0, 0), 0.3), (5, 5, (1, 0), 0.0), (5, 5, (0, 0), 0.3)])
-def test_vcycle_f64_matches_oracle(tn, level, n_r, bc, kappa):
+@pytest.mark.parametrize("level,n_r,bc,kappa,quad", [
+    (3, 9, (1, 0), 0.0, 1), (3, 9, (0, 0), 0.0, 1), (4, 9, (0, 0), 0.0, 1), (2, 17, (0, 0), 0.0, 1),
+    (4, 5, (1, 0), 0.0, 1), (3, 9, (1, 0), 0.3, 1), (4, 5, (0, 0), 0.3, 1), (5, 5, (1, 0), 0.0, 1),
+    (5, 5, (0, 0), 0.3, 1), (3, 9, (1, 0), 0.0, 2), (4, 5, (0, 0), 0.0, 2), (5, 5, (0, 0), 0.0, 2)])
+def test_vcycle_f64_matches_oracle(tn, level, n_r, bc, kappa, quad):
     """Includes semi-coarsened hierarchies: (2, 17) coarsens radially first, (4, 5) laterally;
     level 5 runs the FP64 fine level on the halo-free 16 x 32 tiles with the fused smoother;
-    kappa > 0: hourglass control (Eq. hgstab) on every level."""
+    kappa > 0: hourglass control (Eq. hgstab) on every level; quad = 2: the second radial
+    quadrature point on every level."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     eta = inputs.lognormal_viscosity(om.n_wedges, 3, 0.5)
-    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, bc[0], bc[1], hg_kappa=kappa)
+    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, bc[0], bc[1], hg_kappa=kappa, radial_quad_points=quad)
     mp = LayoutMap(tn.tn_mesh_info(m, 0), om)
     tn.tn_set_viscosity(m, torch.tensor(mp.wedges_to_layout(eta), device="cuda"))
     # a fixed coarse-CG iteration count keeps the comparison away from a stopping-test tie
@@ -50,7 +52,7 @@ def test_vcycle_f64_matches_oracle(tn, level, n_r, bc, kappa):
     v0 = inputs.normal((3, om.n_nodes), 4)
     tn.tn_mg_setup(m, torch.float64, opts, to_dev(mp, v0))
     H = Hierarchy(level, n_r, 0.55, 1.0, eta, bc=(ORACLE_BC[bc[0]], ORACLE_BC[bc[1]]), coarse_rtol=0.0,
-                  coarse_max_iters=20, kappa=kappa)
+                  coarse_max_iters=20, kappa=kappa, quad=quad)
     H.setup(v0.ravel())
     for h in range(H.nlev - 1):
         assert abs(tn.tn_mg_lambda(m, torch.float64, h) / H.lam[h] - 1) < 1e-12
@@ -79,11 +81,11 @@ def test_vcycle_f32_close_to_f64(tn):
     tn.tn_mesh_destroy(m)
 
 
-def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0):
+def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0, quad=1):
     """Spherical benchmark-like solve: T of the A-series shape, eta = exp(ln 10 (1/2 - T)), Ra = 7e3."""
     om = ShellMesh(level, n_r, 0.55, 1.0)
     T = inputs.temperature(om.node_xyz(), 0.55, 1.0)
-    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, eta_storage=eta_storage, hg_kappa=kappa)
+    m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, eta_storage=eta_storage, hg_kappa=kappa, radial_quad_points=quad)
     info = tn.tn_mesh_info(m, 0)
     mp = LayoutMap(info, om)
     Td = torch.tensor(mp.to_layout(T), device="cuda")
@@ -94,7 +96,7 @@ def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0):
     u = [torch.zeros_like(f[0]) for _ in range(3)]
     p = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
     stats = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(rtol=rtol, mode=mode))
-    S = StokesSystem(om, viscosity(om, T, np.log(10.0)), kappa=kappa)
+    S = StokesSystem(om, viscosity(om, T, np.log(10.0)), kappa=kappa, quad=quad)
     b = S.rhs(T, 7e3)
     pm = LayoutMap(pinfo, S.pmesh)
     ug = from_dev(mp, u)
@@ -103,13 +105,14 @@ def config0(tn, level=4, n_r=17, mode=0, rtol=1e-8, eta_storage=0, kappa=0.0):
     return stats, S, b, ug, pg, om
 
 
-@pytest.mark.parametrize("mode,eta_storage,kappa", [(0, 0, 0.0), (1, 0, 0.0), (1, 1, 0.0), (1, 2, 0.0), (0, 0, 0.3),
-                                                    (1, 1, 0.3), (2, 0, 0.0), (2, 1, 0.3)])
-def test_stokes_solve_reaches_1e8_by_the_oracle(tn, mode, eta_storage, kappa):
+@pytest.mark.parametrize("mode,eta_storage,kappa,quad", [
+    (0, 0, 0.0, 1), (1, 0, 0.0, 1), (1, 1, 0.0, 1), (1, 2, 0.0, 1), (0, 0, 0.3, 1), (1, 1, 0.3, 1), (2, 0, 0.0, 1),
+    (2, 1, 0.3, 1), (0, 0, 0.0, 2), (1, 1, 0.0, 2), (2, 1, 0.0, 2)])
+def test_stokes_solve_reaches_1e8_by_the_oracle(tn, mode, eta_storage, kappa, quad):
     # mixed mode with 16-bit viscosity in the FP32 inner solve: the FP64 refinement still meets
     # 1e-8 on the FP64 system; mode 2: FP64 FGMRES with the FP32 preconditioner; kappa > 0: the
-    # hourglass-controlled system (Eq. hgstab)
-    stats, S, b, ug, pg, om = config0(tn, mode=mode, eta_storage=eta_storage, kappa=kappa)
+    # hourglass-controlled system (Eq. hgstab); quad = 2: the system with the second radial point
+    stats, S, b, ug, pg, om = config0(tn, mode=mode, eta_storage=eta_storage, kappa=kappa, quad=quad)
     res = S.residual(b, ug, pg)
     print(f"mode {mode}: {stats}, oracle residual {res:.3e}")
     assert stats["converged"] == 1
