@@ -35,10 +35,10 @@ def valid_mask(level, n_r):
     return j <= N
 
 
-@pytest.mark.parametrize("eta_storage,hg_kappa", [(0, 0.0), (1, 0.3)])
-def test_same_request_alone_and_in_a_mix(tn, eta_storage, hg_kappa):
+@pytest.mark.parametrize("eta_storage,hg_kappa,quad", [(0, 0.0, 1), (1, 0.3, 1), (1, 0.0, 2)])
+def test_same_request_alone_and_in_a_mix(tn, eta_storage, hg_kappa, quad):
     srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4, keep_solutions=1, eta_storage=eta_storage,
-                                                        hg_kappa=hg_kappa))
+                                                        hg_kappa=hg_kappa, radial_quad_points=quad))
     try:
         ref = dict(lateral_level=3, radial_layers=9, E=math.log(100.0), Ra=7e3, t_degree=3, t_order=2,
                    t_amplitude=0.03)
