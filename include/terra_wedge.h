@@ -205,6 +205,25 @@ tn_status tn_diag_A(tn_mesh* mesh, int level, tn_prec prec, void* const* d_dev, 
  * level h+1): sum_e V_e / eta_e psi_k(q_c^e)^2 over the fine wedges.  Stream-ordered. */
 tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m_dev, void* stream);
 
+/* n_steps operator steps on level 0 from and to HOST memory.  Step i copies its inputs
+ * u_host[3 i + c] (c = 0..2, node layout of level 0) and p_host[i] (node layout of level 1) to
+ * the device, computes exactly what tn_apply_A, tn_apply_B, tn_apply_BT and tn_diag_A compute
+ * (same kernels, bitwise the same results):
+ *   y_A = A u, q = B u, y_BT = B^T p, d = diag(A),
+ * and copies them back to out_host[10 i + k]: k = 0..2 y_A, 3 q (level-1 layout), 4..6 y_BT,
+ * 7..9 d.  Element type double (TN_F64) or float (TN_F32) throughout.
+ * The steps are pipelined over two device buffer sets and two copy streams of the library's own:
+ * the copies of one step overlap the compute of its neighbours, which runs on `stream`.  The
+ * device buffers (14 vectors per set) are allocated on the first call and kept with the mesh
+ * (reallocated when prec changes; freed by tn_mesh_destroy).  Host buffers should be pinned
+ * (page-locked): with pageable memory the copies do not overlap.  Output host buffers must not
+ * overlap each other or the inputs.  Stream-ordered: the outputs are complete once `stream`
+ * reaches the point after this call; the host pointers must stay valid until then.
+ * Errors: TN_EINVAL (NULL pointer, n_steps < 0, precision, mesh without a pressure level),
+ * TN_ESTATE (viscosity not set), TN_ENOMEM (device buffers), TN_ECUDA. */
+tn_status tn_operator_steps_host(tn_mesh* mesh, tn_prec prec, int n_steps, const void* const* u_host,
+                                 const void* const* p_host, void* const* out_host, void* stream);
+
 /* Nested iso-interpolation between level h+1 (coarse) and level h (fine), ncomp = 1 or 3
  * arrays: prolongation fine = P coarse, restriction coarse = P^T fine.  With
  * apply_bc != 0 the velocity boundary projector of the target level is applied to

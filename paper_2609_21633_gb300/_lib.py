@@ -101,6 +101,7 @@ _SIGS = {
     "tn_apply_B_static": ([P, ctypes.c_int, ctypes.c_int, PP, P, P], ctypes.c_int),
     "tn_diag_A": ([P, ctypes.c_int, ctypes.c_int, PP, P], ctypes.c_int),
     "tn_diag_pmass": ([P, ctypes.c_int, ctypes.c_int, P, P], ctypes.c_int),
+    "tn_operator_steps_host": ([P, ctypes.c_int, ctypes.c_int, PP, PP, PP, P], ctypes.c_int),
     "tn_prolong": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_restrict": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_buoyancy": ([P, P, ctypes.c_double, PP, P], ctypes.c_int),
@@ -243,6 +244,24 @@ def tn_diag_A(mesh, level, d, stream=None):
 
 def tn_diag_pmass(mesh, level, m, stream=None):
     _check(lib().tn_diag_pmass(mesh, level, _prec(m.dtype), _ptr(m), _stream(stream)))
+
+
+def tn_operator_steps_host(mesh, u_steps, p_steps, out_steps, stream=None):
+    """len(u_steps) operator steps from and to host memory (see the header): u_steps[i] is 3 host
+    tensors, p_steps[i] one, out_steps[i] 10 (y_A 3, q, y_BT 3, d 3), all of one dtype; pinned
+    CPU tensors let the copies overlap the compute.  Stream-ordered on `stream`."""
+    n = len(u_steps)
+    if len(p_steps) != n or len(out_steps) != n:
+        raise ValueError("u_steps, p_steps and out_steps need one entry per step")
+    if any(len(s) != 3 for s in u_steps) or any(len(s) != 10 for s in out_steps):
+        raise ValueError("3 input and 10 output tensors per step")
+    if n == 0:
+        _check(lib().tn_operator_steps_host(mesh, TN_F64, 0, None, None, None, _stream(stream)))
+        return
+    pu, _a = _ptrs([t for s in u_steps for t in s])
+    pp, _b = _ptrs(list(p_steps))
+    po, _c = _ptrs([t for s in out_steps for t in s])
+    _check(lib().tn_operator_steps_host(mesh, _prec(p_steps[0].dtype), n, pu, pp, po, _stream(stream)))
 
 
 def tn_prolong(mesh, level, coarse, fine, apply_bc=False, stream=None):

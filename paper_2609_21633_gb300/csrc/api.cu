@@ -266,10 +266,13 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   return TN_OK;
 }
 
+static void free_step_buffers(tn_mesh* m);
+
 tn_status tn_mesh_destroy(tn_mesh* mesh) {
   if (!mesh) return TN_OK;
   mg_free(mesh->mg);
   mesh->mg = nullptr;
+  free_step_buffers(mesh);
   for (auto& L : mesh->lv) free_level(L);
   delete mesh;
   return TN_OK;
@@ -444,6 +447,111 @@ tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m, void* s
   else if (prec == TN_F32) e = launch_diag_pmass<float>(mesh->lv[level], mesh->lv[level + 1], (float*)m, S(stream));
   else return inval("tn_diag_pmass: unknown precision");
   return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_diag_pmass");
+}
+
+// ------------------------------------------------------------ operator steps from host memory
+static void free_step_buffers(tn_mesh* m) {
+  for (auto& set : m->hs_buf)
+    for (void*& p : set)
+      if (p) {
+        cudaFree(p);
+        p = nullptr;
+      }
+  m->hs_elem = 0;
+}
+
+// Steps i = 0, 1, ... use buffer set i & 1.  Events order the three streams:
+//   copy-in of step i   waits compute of step i - 2 (it overwrites that step's inputs);
+//   compute of step i   waits copy-in of step i and copy-out of step i - 2 (it overwrites the
+//                       outputs that copy-out reads);
+//   copy-out of step i  waits compute of step i.
+tn_status tn_operator_steps_host(tn_mesh* mesh, tn_prec prec, int n_steps, const void* const* u_host,
+                                 const void* const* p_host, void* const* out_host, void* stream) {
+  if (!mesh || mesh->lv.size() < 2) return inval("tn_operator_steps_host: bad mesh (needs a pressure level)");
+  if (prec != TN_F64 && prec != TN_F32) return inval("tn_operator_steps_host: unknown precision");
+  if (n_steps < 0) return inval("tn_operator_steps_host: n_steps < 0");
+  if (n_steps > 0 && (!u_host || !p_host || !out_host)) return inval("tn_operator_steps_host: NULL pointer array");
+  for (int i = 0; i < n_steps; ++i) {
+    if (!u_host[3 * i] || !u_host[3 * i + 1] || !u_host[3 * i + 2] || !p_host[i])
+      return inval("tn_operator_steps_host: NULL input buffer");
+    for (int k = 0; k < 10; ++k)
+      if (!out_host[10 * i + k]) return inval("tn_operator_steps_host: NULL output buffer");
+  }
+  if (!mesh->eta_set) {
+    set_error("tn_operator_steps_host: viscosity not set");
+    return TN_ESTATE;
+  }
+  if (n_steps == 0) return TN_OK;
+  const size_t es = prec == TN_F64 ? sizeof(double) : sizeof(float);
+  const int64_t n0 = mesh->lv[0].n_layout, n1 = mesh->lv[1].n_layout;
+  const int64_t len[14] = {n0, n0, n0, n1, n0, n0, n0, n1, n0, n0, n0, n0, n0, n0};
+  if (mesh->hs_elem != es) {
+    free_step_buffers(mesh);
+    for (auto& set : mesh->hs_buf)
+      for (int v = 0; v < 14; ++v)
+        if (cudaMalloc(&set[v], es * len[v]) != cudaSuccess) {
+          cudaGetLastError();
+          free_step_buffers(mesh);
+          set_error("tn_operator_steps_host: device buffers");
+          return TN_ENOMEM;
+        }
+    mesh->hs_elem = es;
+  }
+  const cudaStream_t cs = S(stream);
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t start = nullptr, ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {};
+  cudaError_t e = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+    e = cudaEventCreateWithFlags(&ev_in[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_comp[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[s], cudaEventDisableTiming);
+  }
+  tn_status st = TN_OK;
+  int done = 0;  // steps whose copy-out was enqueued
+  if (e == cudaSuccess) e = cudaEventRecord(start, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h2d, start, 0);
+  for (int i = 0; i < n_steps && e == cudaSuccess && st == TN_OK; ++i) {
+    const int s = i & 1;
+    void* const* B = mesh->hs_buf[s];
+    if (i >= 2) e = cudaStreamWaitEvent(h2d, ev_comp[s], 0);
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(B[c], u_host[3 * i + c], es * n0, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B[3], p_host[i], es * n1, cudaMemcpyHostToDevice, h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[s], h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_in[s], 0);
+    if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(cs, ev_out[s], 0);
+    if (e != cudaSuccess) break;
+    const void* u[3] = {B[0], B[1], B[2]};
+    void* yA[3] = {B[4], B[5], B[6]};
+    void* yBT[3] = {B[8], B[9], B[10]};
+    void* d[3] = {B[11], B[12], B[13]};
+    st = tn_apply_A(mesh, 0, prec, u, yA, stream);
+    if (st == TN_OK) st = tn_apply_B(mesh, 0, prec, u, B[7], stream);
+    if (st == TN_OK) st = tn_apply_BT(mesh, 0, prec, B[3], yBT, stream);
+    if (st == TN_OK) st = tn_diag_A(mesh, 0, prec, d, stream);
+    if (st != TN_OK) break;
+    e = cudaEventRecord(ev_comp[s], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(d2h, ev_comp[s], 0);
+    for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync(out_host[10 * i + k], B[4 + k], es * len[4 + k], cudaMemcpyDeviceToHost, d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[s], d2h);
+    if (e == cudaSuccess) done = i + 1;
+  }
+  // `stream` waits for the last copies, so the caller's stream order covers the whole call
+  for (int s = 0; s < 2 && s < done; ++s) {
+    const cudaError_t w = cudaStreamWaitEvent(cs, ev_out[s], 0);
+    if (e == cudaSuccess) e = w;
+  }
+  // destruction is deferred by the runtime until the enqueued work is complete
+  cudaEvent_t evs[7] = {start, ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_out[0], ev_out[1]};
+  for (cudaEvent_t x : evs)
+    if (x) cudaEventDestroy(x);
+  if (h2d) cudaStreamDestroy(h2d);
+  if (d2h) cudaStreamDestroy(d2h);
+  if (st != TN_OK) return st;
+  return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_operator_steps_host");
 }
 
 tn_status tn_prolong(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int apply_bc, const void* const* c,

@@ -100,6 +100,10 @@ struct tn_mesh {
   int quad = 1;
   int device = 0;
   double r_in = 0, r_out = 0;
+  // Device buffers of tn_operator_steps_host: two sets of the step's 14 vectors (u 3, p, y_A 3,
+  // q, y_BT 3, d 3), element size hs_elem (0: not allocated).
+  void* hs_buf[2][14] = {};
+  size_t hs_elem = 0;
 };
 
 namespace tn {

@@ -33,6 +33,7 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
         o = tn._lib.tn_mesh_opts(0, 0, 1, 0, 0, kappa, quad)
         assert lib.tn_mesh_create(3, 5, 0.55, 1.0, ctypes.byref(o), ctypes.byref(out)) == tn.TN_EINVAL
         assert b"radial" in lib.tn_last_error()
+    assert lib.tn_operator_steps_host(None, 0, 1, None, None, None, None) == tn.TN_EINVAL
     so = tn._lib.tn_server_opts(4, 0.8, 1, 1e-8, 0, 0, 0.3, 2)  # the server checks the same pair
     srv = ctypes.c_void_p()
     assert lib.tn_server_create(ctypes.byref(so), ctypes.byref(srv)) == tn.TN_EINVAL

@@ -235,6 +235,43 @@ def test_apply_B_and_BT_f64(tn, level, n_r, bc):
     c.close()
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_operator_steps_from_host_memory(tn, dtype):
+    """tn_operator_steps_host: five pipelined steps with distinct pinned host inputs return, bitwise,
+    what the device-side calls return (steps 0, 2, 4 share one device buffer set, 1 and 3 the
+    other, so a missing wait between the streams would mix steps), and A u matches the oracle."""
+    c = Case(tn, 5, 9, BCS["free/free"])
+    pm = O.pressure_mesh(c.om)
+    pinfo = tn.tn_mesh_info(c.m, 1)
+    pmap = LayoutMap(pinfo, pm)
+    n, npr = c.info["n_layout"], pinfo["n_layout"]
+    steps = 5
+    u_h = [[torch.tensor(c.map.to_layout(c.vec(60 + i)[k]), dtype=dtype).pin_memory() for k in range(3)]
+           for i in range(steps)]
+    p_h = [torch.tensor(pmap.to_layout(inputs.normal(pm.n_nodes, 70 + i)), dtype=dtype).pin_memory()
+           for i in range(steps)]
+    sizes = [n, n, n, npr, n, n, n, n, n, n]
+    out_h = [[torch.full((m,), float("nan"), dtype=dtype).pin_memory() for m in sizes] for _ in range(steps)]
+    tn.tn_operator_steps_host(c.m, u_h, p_h, out_h)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        u = [t.cuda() for t in u_h[i]]
+        yA = [torch.empty(n, device="cuda", dtype=dtype) for _ in range(3)]
+        q = torch.empty(npr, device="cuda", dtype=dtype)
+        yBT = [torch.empty(n, device="cuda", dtype=dtype) for _ in range(3)]
+        d = [torch.empty(n, device="cuda", dtype=dtype) for _ in range(3)]
+        tn.tn_apply_A(c.m, 0, u, yA)
+        tn.tn_apply_B(c.m, 0, u, q)
+        tn.tn_apply_BT(c.m, 0, p_h[i].cuda(), yBT)
+        tn.tn_diag_A(c.m, 0, d)
+        for k, t in enumerate(yA + [q] + yBT + d):
+            assert torch.equal(out_h[i][k], t.cpu()), (i, k)
+        want = O.apply_A_constrained(c.om, c.eta, c.vec(60 + i), c.P)
+        tol = TOL64 if dtype == torch.float64 else TOL32
+        assert max_rel(np.stack([c.map.from_layout(out_h[i][k].double().numpy()) for k in range(3)]), want) <= tol
+    c.close()
+
+
 @pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"),
                                           (4, 17, "free/free"), (5, 9, "noslip/noslip")])
 def test_diagonals_f64(tn, level, n_r, bc):
