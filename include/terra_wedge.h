@@ -215,7 +215,8 @@ tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m_dev, voi
  * The steps are pipelined over two device buffer sets and two copy streams of the library's own:
  * the copies of one step overlap the compute of its neighbours, which runs on `stream`.  The
  * device buffers (14 vectors per set) are allocated on the first call and kept with the mesh
- * (reallocated when prec changes; freed by tn_mesh_destroy).  Host buffers should be pinned
+ * (reallocated when prec changes; freed by tn_mesh_destroy) and zeroed when allocated, so the
+ * layout's padding entries (j > N), which no kernel writes, come back as 0.  Host buffers should be pinned
  * (page-locked): with pageable memory the copies do not overlap.  Output host buffers must not
  * overlap each other or the inputs.  Stream-ordered: the outputs are complete once `stream`
  * reaches the point after this call; the host pointers must stay valid until then.

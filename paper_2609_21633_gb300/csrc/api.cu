@@ -489,7 +489,8 @@ tn_status tn_operator_steps_host(tn_mesh* mesh, tn_prec prec, int n_steps, const
     free_step_buffers(mesh);
     for (auto& set : mesh->hs_buf)
       for (int v = 0; v < 14; ++v)
-        if (cudaMalloc(&set[v], es * len[v]) != cudaSuccess) {
+        // zeroed once: the layout's padding entries, which no kernel writes, read back as 0
+        if (cudaMalloc(&set[v], es * len[v]) != cudaSuccess || cudaMemset(set[v], 0, es * len[v]) != cudaSuccess) {
           cudaGetLastError();
           free_step_buffers(mesh);
           set_error("tn_operator_steps_host: device buffers");
