@@ -166,7 +166,8 @@ tn_status tn_set_temperature(tn_mesh* mesh, const double* T_node_dev, const tn_v
 /* Copy the current level-h viscosity (wedge layout, doubles) to eta_dev.  Stream-ordered. */
 tn_status tn_get_viscosity(const tn_mesh* mesh, int level, double* eta_dev, void* stream);
 
-/* y = (P A P + (I - P)) u on level h (Eq. matfree with Eq. elemmat, one-point rule).
+/* y = (P A P + (I - P)) u on level h (Eq. matfree with Eq. elemmat; the one-point rule, or the
+ * mesh's tn_mesh_opts.hg_kappa / radial_quad_points variant of Sec. 4).
  * u_dev[3], y_dev[3]: node layout of level h, type double (TN_F64) or float (TN_F32);
  * y must not alias u.  Stream-ordered. */
 tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* const* y_dev,
@@ -198,7 +199,8 @@ tn_status tn_apply_B_static(tn_mesh* mesh, int level, tn_prec prec, const void* 
  * space of level h.  Stream-ordered. */
 tn_status tn_apply_BT(tn_mesh* mesh, int level, tn_prec prec, const void* p_dev, void* const* y_dev, void* stream);
 
-/* d = diag(P A P + (I - P)) on level h (3 arrays, node layout).  Stream-ordered. */
+/* d = diag(P A P + (I - P)) on level h (3 arrays, node layout), for the mesh's A (one-point rule,
+ * hourglass control or the second radial point).  Stream-ordered. */
 tn_status tn_diag_A(tn_mesh* mesh, int level, tn_prec prec, void* const* d_dev, void* stream);
 
 /* m = diag(M_{1/eta}) of Eq. (pmass) on the pressure space of level h (node layout of
