@@ -68,12 +68,15 @@ def coarsen_viscosity(fine, coarse, eta_fine):
     return acc / 8.0
 
 
-def buoyancy_rhs(mesh, T_nodes, Ra, P=None):
-    """Right-hand side f (3, n): sum_e V_e Ra T(q_c) r_hat(q_c) / 6, projected by P if given."""
+def buoyancy_rhs(mesh, T_nodes, Ra, P=None, wedges=None):
+    """Right-hand side f (3, n): sum_e V_e Ra T(q_c) r_hat(q_c) / 6, projected by P if given.
+
+    Summed over the given wedges (all if None): complete at every node whose wedges are all in
+    ``wedges``."""
     n = mesh.n_nodes
-    nodes = mesh.wedge_nodes()
-    _, V = wedge_geometry(mesh)
-    Te = wedge_temperature(mesh, T_nodes)
+    nodes = mesh.wedge_nodes(wedges)
+    _, V = wedge_geometry(mesh, wedges)
+    Te = wedge_temperature(mesh, T_nodes, wedges)
     xc = mesh.node_xyz(nodes.ravel()).reshape(-1, 6, 3).sum(axis=1) / 6.0
     rhat = xc / np.linalg.norm(xc, axis=1)[:, None]
     f = np.zeros((3, n))

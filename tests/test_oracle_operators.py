@@ -163,3 +163,23 @@ def test_viscosity_law_and_coarsening():
     # and picking the wrong children would move the average by about a cell width
     wrong = coarsen_viscosity(f, c, np.roll(xf[:, 0], 2))
     assert np.abs(wrong - xc[:, 0]).max() > 0.05
+
+
+def test_buoyancy_rhs_magnitude_converges_to_the_shell_integral():
+    """Scale of the Boussinesq load of Eq. (stokes), f_j = sum_e V_e Ra T(q_c) r_hat(q_c) N_j(q_c).
+
+    With T = 1 and no projection, sum_j f_j . x_j = Ra sum_e V_e r_hat_e . (sum_j N_j(q_c) x_j)
+    = Ra sum_e V_e |x(q_c)|, the one-point rule for Ra times the integral of r over the shell,
+    Ra pi (r_out^4 - r_in^4).  The mesh and the rule are both second order, so the relative error
+    must fall by ~4 per refinement; a dropped 1/6 (N_j(q_c)), a dropped V_e or a doubled Ra
+    changes the limit itself."""
+    r_in, r_out, Ra = 0.55, 1.0, 2.5
+    exact = Ra * np.pi * (r_out ** 4 - r_in ** 4)
+    errs = []
+    for level, n_r in ((2, 3), (3, 5), (4, 9)):
+        m = ShellMesh(level, n_r, r_in, r_out)
+        f = buoyancy_rhs(m, np.ones(m.n_nodes), Ra)
+        errs.append(abs(np.sum(f * m.node_xyz().T) - exact) / exact)
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert errs[-1] < 5e-3, errs
+    assert np.all((orders > 1.9) & (orders < 2.1)), orders
