@@ -29,10 +29,11 @@ sys.path.insert(0, ROOT)
 
 R_IN, R_OUT = 0.55, 1.0
 LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, contrast 1e3
-# Algorithmic FP64 work of one A apply per hexahedral cell (2 wedges), FMA = 2 flops:
-# per wedge 33 (differences) + 9 (scaling) + 45 (grad u) + 20 (stress) + 54 (stress x M^-T)
-# + 21 (test-gradient combination) + 18 (accumulation) = 200.
-A_FLOPS_PER_CELL = 400.0
+# Algorithmic FP64 work of one A apply per hexahedral cell (2 wedges, one-point rule), FMA = 2
+# flops: the differences-only gather, the factorised Jacobian, strain, stress, the stress times
+# the inverse Jacobian and the differences-only scatter of Eq. epsq / Eq. localapply, counted
+# from their structure at 240 flops per wedge.
+A_FLOPS_PER_CELL = 480.0
 # DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 176.8 MB for
 # 2,621,440 cells, halo-free 16 x 32 tiles), scaled to the bench size by cells; None once the
 # kernel changes.
@@ -45,7 +46,8 @@ HG_KAPPA = 0.3
 # kernels.
 def launches_per_step(level):
     return 12 + (4 if level >= 5 else 0)
-# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz.
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 DFMA / clk x 2 flops x 2.07 GHz;
+# the roofline uses the DFMA rate measured live by tn_probe_fma_peak, this figure is context.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 
@@ -60,8 +62,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-solve", dest="no_solve", action="store_true",
                     help="do not run the Stokes-solve and serving measurements after the operator steps")
-    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=64,
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=256,
                     help="requests of the seeded serving stream measured after the solves (the full stream is 256)")
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=50,
+                    help="steps of the end-to-end run through tn_operator_steps_host")
     ap.add_argument("--largest-shell", dest="largest_shell", action="store_true",
                     help="instead of the operator step: one Stokes solve on the largest single-GPU shell "
                          "(level 8, 257 layers) and its resident device memory")
@@ -114,38 +118,100 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------- oracle arm
-def oracle_step_sample(level, n_r, layers, seed, frac=1.0):
-    """Time the CPU oracle on a bounded sample of the workload: the wedges of the first
-    ``frac`` of the lateral triangles (diamond-major order) in the innermost ``layers``
-    radial cells of the same shell (same lateral resolution and radial spacing).
-    Returns (seconds, DoFs processed, description)."""
+def _oracle_sample_setup(level, n_r, layers, seed, frac=1.0, first_cell=0):
+    """Inputs of one oracle sample: the wedges of the first ``frac`` of the lateral triangles
+    (diamond-major order) in ``layers`` radial cells of the same shell starting at radial cell
+    ``first_cell`` (same lateral resolution and radial spacing).  B (CSR) is assembled here, outside
+    the timed region."""
     from oracle import operators as O
     from oracle.fields import viscosity
     from oracle.mesh import ShellMesh
     from paper_2609_21633_gb300 import inputs
     dr = (R_OUT - R_IN) / (n_r - 1)
-    om = ShellMesh(level, layers + 1, R_IN, R_IN + dr * layers)
+    om = ShellMesh(level, layers + 1, R_IN + dr * first_cell, R_IN + dr * (first_cell + layers))
     T = inputs.temperature(om.node_xyz(), R_IN, R_OUT) + inputs.normal(om.n_nodes, seed + 7, 0.01)
     eta = viscosity(om, T, LAW["E"], jump_r=LAW["jump_r"], jump_factor=LAW["jump_factor"])
     P = O.boundary_projectors(om)
     u = inputs.normal((3, om.n_nodes), seed + 8)
     pm = O.pressure_mesh(om)
     p = inputs.normal(pm.n_nodes, seed + 9)
-    Pp = O.prolongation(om, pm)
     Pm = O.projector_matrix(P)
     wedges = np.arange(max(1, int(round(frac * om.n_wedges))))
-    t0 = time.perf_counter()
-    O.apply_A_constrained(om, eta, u, P, wedges=wedges)
-    B = O.assemble_B(om, Pp, wedges=wedges)
-    B @ (Pm @ u.ravel())
-    Pm @ (B.T @ p)
-    O.diag_A_constrained(om, eta, P, wedges=wedges)
-    dt = time.perf_counter() - t0
+    B = O.assemble_B(om, O.prolongation(om, pm), wedges=wedges)
     share = len(wedges) / om.n_wedges
-    nv, npr = 3 * om.n_nodes, pm.n_nodes
-    desc = (f"{len(wedges) // 2} of {10 * 4 ** level * (n_r - 1)} cells (innermost {layers} radial cells, "
-            f"{100 * share:.0f}% of their wedges) of the same shell, one A+B+BT+diag step, numpy/scipy, 1 thread")
-    return dt, share * (4 * nv + 2 * npr), desc
+    return dict(om=om, eta=eta, P=P, u=u, p=p, Pm=Pm, B=B, wedges=wedges,
+                dofs=share * (4 * 3 * om.n_nodes + 2 * pm.n_nodes), share=share)
+
+
+def _oracle_sample_run(c):
+    """The timed part: matrix-free A, the B and B^T products, and diag(A) of the sample."""
+    from oracle import operators as O
+    O.apply_A_constrained(c["om"], c["eta"], c["u"], c["P"], wedges=c["wedges"])
+    c["B"] @ (c["Pm"] @ c["u"].ravel())
+    c["Pm"] @ (c["B"].T @ c["p"])
+    O.diag_A_constrained(c["om"], c["eta"], c["P"], wedges=c["wedges"])
+
+
+def oracle_step_sample(level, n_r, layers, seed, frac=1.0):
+    """Time the CPU oracle, single-threaded, on a bounded sample of the workload (the innermost
+    ``layers`` radial cells).  Returns (seconds, DoFs processed, description)."""
+    c = _oracle_sample_setup(level, n_r, layers, seed, frac)
+    t0 = time.perf_counter()
+    _oracle_sample_run(c)
+    dt = time.perf_counter() - t0
+    desc = (f"{len(c['wedges']) // 2} of {10 * 4 ** level * (n_r - 1)} cells (innermost {layers} radial cells, "
+            f"{100 * c['share']:.0f}% of their wedges) of the same shell, one A+B+BT+diag step (B assembled "
+            f"before the timed region), numpy/scipy, 1 thread")
+    return dt, c["dofs"], desc
+
+
+def _oracle_worker(level, n_r, layers, seed, first_cell, barrier, out):
+    c = _oracle_sample_setup(level, n_r, layers, seed, 1.0, first_cell)
+    barrier.wait()
+    t0 = time.monotonic()
+    _oracle_sample_run(c)
+    out.put((t0, time.monotonic(), c["dofs"]))
+
+
+def oracle_step_sample_parallel(level, n_r, layers, seed, procs):
+    """The oracle on all host cores: ``procs`` spawned processes, each the single-threaded sample
+    on its own ``layers`` radial cells (worker w starts at radial cell w * layers), started together
+    after their set-up.  Returns (wall seconds, DoFs processed, description)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    procs = max(1, min(procs, (n_r - 1) // layers))
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(level, n_r, layers, seed, w * layers, barrier, out))
+          for w in range(procs)]
+    for p in ps:
+        p.start()
+    res = [out.get() for _ in ps]
+    for p in ps:
+        p.join()
+    wall = max(r[1] for r in res) - min(r[0] for r in res)
+    desc = (f"{procs * layers * 10 * 4 ** level} of {10 * 4 ** level * (n_r - 1)} cells (radial cells "
+            f"0..{procs * layers - 1}, {layers} per process) of the same shell, one A+B+BT+diag step, "
+            f"numpy/scipy, {procs} spawned processes of 1 thread each")
+    return wall, sum(r[2] for r in res), desc
+
+
+def oracle_config0_solve():
+    """The oracle's FP64 Stokes solve of the level-4 / 17-layer shell (T of degree 3 / order 2,
+    viscosity contrast 10, Ra = 7e3, free-slip) to 1e-8: flexible GMRES with the oracle V-cycle,
+    single-threaded.  Returns (seconds, iterations, oracle-evaluated residual)."""
+    from oracle.fields import viscosity
+    from oracle.mesh import ShellMesh
+    from oracle.solver import StokesSystem
+    from paper_2609_21633_gb300 import inputs
+    t0 = time.perf_counter()
+    om = ShellMesh(4, 17, R_IN, R_OUT)
+    T = inputs.temperature(om.node_xyz(), R_IN, R_OUT)
+    eta = viscosity(om, T, math.log(10.0))
+    S = StokesSystem(om, eta)
+    b = S.rhs(T, 7e3)
+    u, p, its = S.fgmres_solve(b, eta, tol=1e-8)
+    dt = time.perf_counter() - t0
+    return dt, its, S.residual(b, u, p)
 
 
 def run_reference(args):
@@ -410,6 +476,21 @@ def main():
     ms = max_over_ranks(ms, dist, dev)
     if dist:
         dist.barrier()
+    # the A apply with the element op in IEEE binary64 (the default evaluates it in double-float
+    # on the FP32 pipe): same shell, temperature and input, timed alone
+    m64 = tn.tn_mesh_create(args.level, args.n_r, R_IN, R_OUT, fp64_element=tn.TN_FP64_ELEM_BINARY64)
+    tn.tn_set_temperature(m64, Td, LAW["E"], LAW["jump_r"], LAW["jump_factor"])
+    for _ in range(3):
+        tn.tn_apply_A(m64, 0, u, yA, st)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    b0.record(st)
+    for _ in range(args.steps):
+        tn.tn_apply_A(m64, 0, u, yA, st)
+    b1.record(st)
+    torch.cuda.synchronize()
+    a_binary64_ms = b0.elapsed_time(b1) / args.steps
+    tn.tn_mesh_destroy(m64)
     # the same step in FP32 (the inner-solve precision of the mixed path)
     u32 = [t.float() for t in u]
     p32, q32 = p.float(), q.float()
@@ -426,14 +507,16 @@ def main():
     hu = [t.cpu().pin_memory() for t in u]
     hp = p.cpu().pin_memory()
     outs = yA + [q] + yBT + dA
-    hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+    # two pinned output sets, alternated step by step (no two steps of one call write the same
+    # host buffer, as the entry point requires)
+    hout = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs] for _ in range(2)]
     h2d = sum(t.numel() * t.element_size() for t in hu) + hp.numel() * hp.element_size()
-    d2h = sum(t.numel() * t.element_size() for t in hout)
+    d2h = sum(t.numel() * t.element_size() for t in hout[0])
 
     def e2e_steps_run(k):
-        tn.tn_operator_steps_host(m, [hu] * k, [hp] * k, [hout] * k, stream=st)
+        tn.tn_operator_steps_host(m, [hu] * k, [hp] * k, [hout[i % 2] for i in range(k)], stream=st)
 
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2, args.e2e_steps)
     e2e_steps_run(2)  # allocates the library's device buffer sets
     torch.cuda.synchronize()
     if dist:
@@ -450,6 +533,8 @@ def main():
         cells = 10 * 4 ** args.level * (args.n_r - 1)
         a_flops = A_FLOPS_PER_CELL * cells
         achieved = a_flops / (per_op["A"] / 1e3) / 1e12
+        dfma_peak = tn.tn_probe_fma_peak(torch.float64, st)  # measured live, same clocks as the step
+        ffma_peak = tn.tn_probe_fma_peak(torch.float32, st)
         line = {
             "metric": "Stokes-apply GDoF/s (FP64 A+B+BT+diag step)", "value": value, "unit": "GDoF/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
@@ -458,10 +543,15 @@ def main():
                        "dofs_per_step": ndof, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (3 x %.0f MB velocity components)" % (n * 8 / 1e6)},
             "per_op_ms": per_op,
+            "A_ms_binary64_element": a_binary64_ms,
             "roofline": {"bound": "alu", "kernel": "A apply (tile kernel + interface sum)", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak": dfma_peak, "unit": "TFLOP/s", "frac": achieved / dfma_peak,
                          "traffic": A_TRAFFIC_BYTES_PER_CELL * cells if A_TRAFFIC_BYTES_PER_CELL else None,
-                         "peak_note": "FP64 DFMA peak from unit counts x max clock",
+                         "flops_per_cell": A_FLOPS_PER_CELL,
+                         "peak_note": "FP64 DFMA rate measured in this run (tn_probe_fma_peak); derived "
+                                      "152 SMs x 2 DFMA/clk x 2.07 GHz = %.3f TFLOP/s" % FP64_PEAK_TFLOPS,
+                         "frac_of_derived_peak": achieved / FP64_PEAK_TFLOPS,
+                         "ffma_peak_tflops": ffma_peak,
                          "hbm_frac_of_measured": (64.0 * cells) / (per_op["A"] / 1e3) / 6771.8e9},
             "f32_step": {"ms_per_step": ms32 / args.steps, "per_op_ms": per32,
                          "value": ndof / (ms32 / args.steps / 1e3) / 1e9, "unit": "GDoF/s",
@@ -512,9 +602,21 @@ def main():
             if args.serve_requests > 0:
                 line["serving"] = serving_stream(tn, args.serve_requests, args.seed, hg_kappa=HG_KAPPA)
         if world == 1:
+            cores = os.cpu_count() or 1
+            dtp, ndp, descp = oracle_step_sample_parallel(args.level, args.n_r, 2, args.seed, cores)
             dt, nd, desc = oracle_step_sample(args.level, args.n_r, 2, args.seed)
-            line["cpu_baseline"] = {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
-                                    "sample": desc, "seconds": dt}
+            line["cpu_baseline"] = {"value": ndp / dtp / 1e9, "unit": "GDoF/s", "cores": min(cores, (args.n_r - 1) // 2),
+                                    "kind": "oracle", "sample": descp, "seconds": dtp,
+                                    "single_core": {"value": nd / dt / 1e9, "unit": "GDoF/s", "cores": 1,
+                                                    "sample": desc, "seconds": dt}}
+            if not args.no_solve:
+                ot, oits, ores = oracle_config0_solve()
+                gpu0 = line["solves"]["l4_17_contrast1e1"]["fp64"]
+                line["cpu_baseline"]["config0_solve"] = {
+                    "oracle_seconds": ot, "oracle_iterations": oits, "oracle_rel_residual": ores, "cores": 1,
+                    "gpu_fp64_seconds": gpu0["seconds"], "gpu_fp64_iterations": gpu0["iterations"],
+                    "what": "level 4 / 17 layers, contrast 10, Ra 7e3, free-slip, to 1e-8: oracle flexible GMRES "
+                            "with its V-cycle (set-up included) beside the GPU FP64 solve (set-up excluded)"}
         print(json.dumps(line))
     tn.tn_mesh_destroy(m)
     if dist:

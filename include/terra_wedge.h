@@ -78,7 +78,8 @@ enum {
   TN_ENOTCONVERGED = -4, /* an iterative solve did not reach its tolerance */
   TN_ETIMEOUT = -5,      /* a bounded device wait ran out */
   TN_EBUSY = -6,         /* resource temporarily unavailable (serving admission) */
-  TN_ESTATE = -7         /* call order violated (e.g. apply before set_viscosity) */
+  TN_ESTATE = -7,        /* call order violated (e.g. apply before set_viscosity) */
+  TN_ECANCELED = -8      /* a serving request was cancelled (tn_server_cancel) */
 };
 
 typedef enum { TN_F64 = 0, TN_F32 = 1 } tn_prec;
@@ -88,6 +89,13 @@ typedef enum { TN_BC_FREESLIP = 0, TN_BC_NOSLIP = 1 } tn_bc;
  * column of wedges (lateral wedge (d, i, j, w) over all radial cells), c = sqrt(min * max) of the
  * column, so the stored values straddle 1; used on levels with N >= 16, FP32 on coarser ones. */
 typedef enum { TN_ETA_F32 = 0, TN_ETA_BF16 = 1, TN_ETA_F16 = 2 } tn_eta_storage;
+/* Arithmetic of the FP64 viscous element op (A, its residual and smoother epilogues) on levels with
+ * N >= 32, where it bounds the apply: TN_FP64_ELEM_DOUBLE_FLOAT evaluates Eq. epsq / Eq. localapply
+ * in double-float (pairs of FP32 numbers, about 48 significand bits, on the FP32 pipe; every
+ * operation's relative error is below 2^-45) with binary64 inputs, outputs, boundary projections,
+ * interface sums and epilogues; TN_FP64_ELEM_BINARY64 in IEEE binary64 throughout.  Coarser levels,
+ * B, B^T and the diagonals always use binary64. */
+typedef enum { TN_FP64_ELEM_DOUBLE_FLOAT = 0, TN_FP64_ELEM_BINARY64 = 1 } tn_fp64_element;
 
 typedef struct tn_mesh tn_mesh;
 
@@ -106,6 +114,7 @@ typedef struct {
                        * the radial reference coordinate at the lateral barycentre, weights 1/2, one
                        * viscosity per wedge).  B, B^T and the pressure mass keep the one-point rule.
                        * 2 together with hg_kappa > 0 is TN_EINVAL (two remedies of the same modes). */
+  int fp64_element;   /* tn_fp64_element (default TN_FP64_ELEM_DOUBLE_FLOAT) */
 } tn_mesh_opts;
 
 typedef struct {
@@ -178,19 +187,22 @@ tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* 
  * (nested iso-interpolation of the coarse W1 function, Sec. 3).  Stream-ordered. */
 tn_status tn_apply_B(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev, void* stream);
 
-/* q = B P u exactly as tn_apply_B (same kernels, same result), but without mesh-owned or
- * per-call scratch: the fine-level divergence field between the element kernel and the
- * restriction lives in a static device array compiled into the library (8 MiB, held by every
- * GPU that loads the library until the process exits).  For callers that cannot allocate
- * device memory at the point of the call, e.g. code running under an allocator that forbids
- * cudaMalloc after start-up; this call makes no cudaMalloc, cudaFree or other allocating call.
+/* q = B P u exactly as tn_apply_B (same kernels, same result), with the one intermediate that
+ * tn_apply_B keeps in mesh-owned scratch -- the fine-level divergence field between the element
+ * kernel and the restriction -- in a static device array compiled into the library instead (8 MiB,
+ * held by every GPU that loads the library until the process exits).  For callers that cannot
+ * allocate device memory at the point of the call, e.g. code running under an allocator that
+ * forbids cudaMalloc after start-up; this call makes no cudaMalloc, cudaFree or other allocating
+ * call.  FP64 levels with N >= 32 still use the ring buffer that tn_mesh_create preallocated for
+ * the tile-line partial sums of the halo-free tiles (no allocation, but mesh-owned memory).
  * The paper has no counterpart; it is an addition of this library.
  * Limit: level h's node layout times the element size (8 B for TN_F64, 4 B for TN_F32) must
  * fit in 8 MiB, else TN_EINVAL with the sizes in tn_last_error().  The mesh's device must be
  * current.  The first call on a device looks up the array's device address (once per device);
  * make that first call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU (other streams, other threads, other meshes) race on it.  Nothing in it
- * needs to start at zero (each call writes every entry it reads).  Stream-ordered. */
+ * overlap on the GPU (other streams, other threads, other meshes) race on it, and calls on one
+ * mesh that overlap also race on that mesh's ring buffer.  Nothing in the array needs to start
+ * at zero (each call writes every entry it reads).  Stream-ordered. */
 tn_status tn_apply_B_static(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev,
                             void* stream);
 
@@ -219,8 +231,10 @@ tn_status tn_diag_pmass(tn_mesh* mesh, int level, tn_prec prec, void* m_dev, voi
  * device buffers (14 vectors per set) are allocated on the first call and kept with the mesh
  * (reallocated when prec changes; freed by tn_mesh_destroy) and zeroed when allocated, so the
  * layout's padding entries (j > N), which no kernel writes, come back as 0.  Host buffers should be pinned
- * (page-locked): with pageable memory the copies do not overlap.  Output host buffers must not
- * overlap each other or the inputs.  Stream-ordered: the outputs are complete once `stream`
+ * (page-locked): with pageable memory the copies do not overlap.  The ten output buffers of one
+ * step must not overlap each other, and no output buffer may overlap an input buffer of the call;
+ * outputs of different steps may share buffers (all copy-outs run on one library stream in step
+ * order, so a later step's result overwrites an earlier one's).  Stream-ordered: the outputs are complete once `stream`
  * reaches the point after this call; the host pointers must stay valid until then.
  * Errors: TN_EINVAL (NULL pointer, n_steps < 0, precision, mesh without a pressure level),
  * TN_ESTATE (viscosity not set), TN_ENOMEM (device buffers), TN_ECUDA. */
@@ -240,6 +254,13 @@ tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int app
  * (Eq. stokes with the full temperature); f_dev[3] doubles.  Stream-ordered. */
 tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double* const* f_dev, void* stream);
 
+
+/* Measured fused multiply-add throughput of the current device in TFLOP/s (FMA = 2 flops), for
+ * prec TN_F64 (DFMA) or TN_F32 (FFMA): independent FMA chains on every SM, timed with CUDA events
+ * on `stream`, best of three launches after a warm-up.  The roofline denominator of the element
+ * kernels that the FP64 / FP32 pipes bound.  Not a paper operation (a measurement utility).
+ * Synchronous; allocates and frees a small device buffer.  Errors: TN_EINVAL, TN_ECUDA. */
+tn_status tn_probe_fma_peak(tn_prec prec, double* tflops, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Geometric multigrid (Sec. 7): V-cycle over the mesh hierarchy, two pre- and two
@@ -302,7 +323,12 @@ tn_status tn_vcycle(tn_mesh* mesh, tn_prec prec, const void* const* r_dev, void*
  * whose preconditioner P^-1 runs in FP32 on the normalised Krylov vector (FP32 Schur step,
  * B^T and V-cycle); FGMRES admits the inexact preconditioner.
  * u, p are outputs (zero initial guess); g may be NULL (zero).  Synchronous.
- * Returns TN_ENOTCONVERGED if ||b - K x|| / ||b|| > rtol on return (stats still filled).
+ * Returns TN_ENOTCONVERGED if ||b - K x|| / ||b|| > rtol on return, or is not a number (stats still
+ * filled, converged = 0).  Breakdown exits, each TN_ENOTCONVERGED with the reason in tn_last_error():
+ * a non-finite right-hand side returns before the first iteration; a non-finite restart residual or
+ * Hessenberg entry (NaN / Inf in the viscosity, the operator or the data) stops FGMRES at that
+ * iteration, keeping only the finite part of the update; five restarts in a row that bring the
+ * residual less than 0.1 % below its best value so far stop it as stagnation.
  * ---------------------------------------------------------------------------------------- */
 typedef enum { TN_SOLVE_F64 = 0, TN_SOLVE_MIXED = 1, TN_SOLVE_F64_PREC32 = 2 } tn_solve_mode;
 typedef struct {
@@ -379,6 +405,11 @@ tn_status tn_server_wait(tn_server* srv, uint64_t ticket, tn_result* res);
  * (component-major), p_host n_layout of level 1, layouts as for a mesh of the request's shape. */
 tn_status tn_server_solution(tn_server* srv, uint64_t ticket, double* u_host, double* p_host);
 tn_status tn_server_stats(tn_server* srv, int* queued, int* running, int* resident, double* reserved_bytes);
+/* Cancel a request: a queued one completes at once with status TN_ECANCELED and never runs; a
+ * running one stops at its next Krylov iteration (the solver polls the flag once per iteration),
+ * completes with TN_ECANCELED and frees its slot and vectors; a finished one is left as it is.
+ * Returns TN_OK, or TN_EINVAL for an unknown ticket.  Thread-safe. */
+tn_status tn_server_cancel(tn_server* srv, uint64_t ticket);
 /* Finishes every queued request, then stops the workers and frees everything. */
 tn_status tn_server_destroy(tn_server* srv);
 

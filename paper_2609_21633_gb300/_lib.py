@@ -14,9 +14,11 @@ LIB_PATH = os.path.join(HERE, "lib", "libterra_wedge.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "terra_wedge.h")
 
 TN_OK, TN_EINVAL, TN_ENOMEM, TN_ECUDA, TN_ENOTCONVERGED, TN_ETIMEOUT, TN_EBUSY, TN_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+TN_ECANCELED = -8
 TN_F64, TN_F32 = 0, 1
 TN_BC_FREESLIP, TN_BC_NOSLIP = 0, 1
 TN_ETA_F32, TN_ETA_BF16, TN_ETA_F16 = 0, 1, 2
+TN_FP64_ELEM_DOUBLE_FLOAT, TN_FP64_ELEM_BINARY64 = 0, 1
 
 
 class TnError(RuntimeError):
@@ -28,7 +30,7 @@ class TnError(RuntimeError):
 class tn_mesh_opts(ctypes.Structure):
     _fields_ = [("bc_inner", ctypes.c_int), ("bc_outer", ctypes.c_int), ("div_term", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("eta_storage", ctypes.c_int), ("hg_kappa", ctypes.c_double),
-                ("radial_quad_points", ctypes.c_int)]
+                ("radial_quad_points", ctypes.c_int), ("fp64_element", ctypes.c_int)]
 
 
 class tn_level_info(ctypes.Structure):
@@ -120,6 +122,8 @@ _SIGS = {
     "tn_server_solution": ([P, ctypes.c_uint64, P, P], ctypes.c_int),
     "tn_server_stats": ([P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "tn_server_cancel": ([P, ctypes.c_uint64], ctypes.c_int),
+    "tn_probe_fma_peak": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
     "tn_server_destroy": ([P], ctypes.c_int),
 }
 
@@ -169,9 +173,10 @@ def _prec(dtype):
 
 
 def tn_mesh_create(lateral_level, radial_layers, r_in, r_out, bc_inner=TN_BC_FREESLIP, bc_outer=TN_BC_FREESLIP,
-                   div_term=True, max_levels=0, eta_storage=0, hg_kappa=0.0, radial_quad_points=1):
+                   div_term=True, max_levels=0, eta_storage=0, hg_kappa=0.0, radial_quad_points=1,
+                   fp64_element=TN_FP64_ELEM_DOUBLE_FLOAT):
     opts = tn_mesh_opts(bc_inner, bc_outer, int(bool(div_term)), max_levels, eta_storage, float(hg_kappa),
-                        int(radial_quad_points))
+                        int(radial_quad_points), int(fp64_element))
     out = P()
     _check(lib().tn_mesh_create(lateral_level, radial_layers, r_in, r_out, ctypes.byref(opts), ctypes.byref(out)))
     return out
@@ -258,6 +263,23 @@ def tn_operator_steps_host(mesh, u_steps, p_steps, out_steps, stream=None):
     if n == 0:
         _check(lib().tn_operator_steps_host(mesh, TN_F64, 0, None, None, None, _stream(stream)))
         return
+    # the C side copies n_layout elements to and from each host pointer on trust: check every
+    # tensor's device, contiguity, dtype and size here, before any copy is enqueued
+    n0, n1 = tn_mesh_info(mesh, 0)["n_layout"], tn_mesh_info(mesh, 1)["n_layout"]
+    dtype = p_steps[0].dtype
+    _prec(dtype)
+    for i in range(n):
+        slots = ([(t, n0, "u") for t in u_steps[i]] + [(p_steps[i], n1, "p")] +
+                 [(t, n1 if k == 3 else n0, "out[%d]" % k) for k, t in enumerate(out_steps[i])])
+        for t, want, name in slots:
+            if t.device.type != "cpu":
+                raise ValueError(f"step {i} {name}: host (CPU) tensor expected, got {t.device}")
+            if not t.is_contiguous():
+                raise ValueError(f"step {i} {name}: tensor must be contiguous")
+            if t.dtype != dtype:
+                raise ValueError(f"step {i} {name}: dtype {t.dtype}, expected {dtype} like p_steps[0]")
+            if t.numel() != want:
+                raise ValueError(f"step {i} {name}: {t.numel()} elements, the layout has {want}")
     pu, _a = _ptrs([t for s in u_steps for t in s])
     pp, _b = _ptrs(list(p_steps))
     po, _c = _ptrs([t for s in out_steps for t in s])
@@ -385,6 +407,17 @@ def tn_server_stats(srv):
     q, r, res, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _check(lib().tn_server_stats(srv, ctypes.byref(q), ctypes.byref(r), ctypes.byref(res), ctypes.byref(b)))
     return {"queued": q.value, "running": r.value, "resident": res.value, "reserved_bytes": b.value}
+
+
+def tn_server_cancel(srv, ticket):
+    _check(lib().tn_server_cancel(srv, ticket))
+
+
+def tn_probe_fma_peak(dtype, stream=None):
+    """Measured FMA throughput (TFLOP/s) of the current device for torch.float64 / torch.float32."""
+    out = ctypes.c_double()
+    _check(lib().tn_probe_fma_peak(_prec(dtype), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def tn_server_destroy(srv):

@@ -4,6 +4,7 @@
 #include <new>
 #include <string>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace tn {
@@ -42,7 +43,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 }
 
 void free_level(Level& L) {
-  void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
+  void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.laydf, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
                   L.rad32, L.dcoef64, L.dcoef32, L.ring64};
   for (void* p : ptrs)
@@ -139,6 +140,15 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
   }
   chk(upload(L.lay64, lay));
   chk(upload(L.lay32, to_f32(lay)));
+  {
+    // the layer table as double-float pairs, split exactly as the kernels split binary64 values
+    std::vector<float> ldf(2 * lay.size());
+    for (size_t q = 0; q < lay.size(); ++q) {
+      const dfl v = split(lay[q]);
+      ldf[2 * q] = v.hi, ldf[2 * q + 1] = v.lo;
+    }
+    chk(upload(L.laydf, ldf));
+  }
   chk(upload(L.s64, s));
   chk(upload(L.s32, to_f32(s)));
   chk(upload(L.grp_ptr, gptr));
@@ -211,8 +221,10 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   if (radial_layers < 3 || (radial_layers - 1) % 2 != 0)
     return inval("tn_mesh_create: radial_layers must be >= 3 with radial_layers - 1 even");
   if (!(r_in > 0.0) || !(r_out > r_in)) return inval("tn_mesh_create: need 0 < r_in < r_out");
-  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, TN_ETA_F32, 0.0, 1};
+  tn_mesh_opts o = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, TN_ETA_F32, 0.0, 1, TN_FP64_ELEM_DOUBLE_FLOAT};
   if (opts) o = *opts;
+  if (o.fp64_element != TN_FP64_ELEM_DOUBLE_FLOAT && o.fp64_element != TN_FP64_ELEM_BINARY64)
+    return inval("tn_mesh_create: unknown fp64_element");
   if (o.radial_quad_points == 0) o.radial_quad_points = 1;
   if (o.radial_quad_points != 1 && o.radial_quad_points != 2)
     return inval("tn_mesh_create: radial_quad_points must be 1 or 2");
@@ -242,6 +254,7 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
   m->eta_storage = o.eta_storage;
   m->hg_kappa = o.hg_kappa;
   m->quad = o.radial_quad_points;
+  m->df = o.fp64_element == TN_FP64_ELEM_DOUBLE_FLOAT ? 1 : 0;
   m->r_in = r_in;
   m->r_out = r_out;
   cudaGetDevice(&m->device);
@@ -251,6 +264,7 @@ tn_status tn_mesh_create(int lateral_level, int radial_layers, double r_in, doub
     tn_status s = create_level(m->lv.back(), l, nr, r_in, r_out, o.eta_storage, m->div_term);
     m->lv.back().hg_kappa = o.hg_kappa;
     m->lv.back().quad = o.radial_quad_points;
+    m->lv.back().df = m->df;
     if (s != TN_OK) {
       std::string msg = tn_last_error();
       tn_mesh_destroy(m);
@@ -510,7 +524,6 @@ tn_status tn_operator_steps_host(tn_mesh* mesh, tn_prec prec, int n_steps, const
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_out[s], cudaEventDisableTiming);
   }
   tn_status st = TN_OK;
-  int done = 0;  // steps whose copy-out was enqueued
   if (e == cudaSuccess) e = cudaEventRecord(start, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h2d, start, 0);
   for (int i = 0; i < n_steps && e == cudaSuccess && st == TN_OK; ++i) {
@@ -538,12 +551,21 @@ tn_status tn_operator_steps_host(tn_mesh* mesh, tn_prec prec, int n_steps, const
     for (int k = 0; k < 10 && e == cudaSuccess; ++k)
       e = cudaMemcpyAsync(out_host[10 * i + k], B[4 + k], es * len[4 + k], cudaMemcpyDeviceToHost, d2h);
     if (e == cudaSuccess) e = cudaEventRecord(ev_out[s], d2h);
-    if (e == cudaSuccess) done = i + 1;
   }
-  // `stream` waits for the last copies, so the caller's stream order covers the whole call
-  for (int s = 0; s < 2 && s < done; ++s) {
-    const cudaError_t w = cudaStreamWaitEvent(cs, ev_out[s], 0);
-    if (e == cudaSuccess) e = w;
+  // `stream` waits for everything enqueued on the two private streams -- after an early exit too,
+  // so that no copy into the mesh's buffers outlives the caller's stream order (a retry on the same
+  // mesh would otherwise overlap it); if the join itself fails, the host waits instead
+  for (cudaStream_t x : {h2d, d2h}) {
+    if (!x) continue;
+    cudaEvent_t tail = nullptr;
+    cudaError_t w = cudaEventCreateWithFlags(&tail, cudaEventDisableTiming);
+    if (w == cudaSuccess) w = cudaEventRecord(tail, x);
+    if (w == cudaSuccess) w = cudaStreamWaitEvent(cs, tail, 0);
+    if (tail) cudaEventDestroy(tail);
+    if (w != cudaSuccess) {
+      cudaStreamSynchronize(x);
+      if (e == cudaSuccess) e = w;
+    }
   }
   // destruction is deferred by the runtime until the enqueued work is complete
   cudaEvent_t evs[7] = {start, ev_in[0], ev_in[1], ev_comp[0], ev_comp[1], ev_out[0], ev_out[1]};

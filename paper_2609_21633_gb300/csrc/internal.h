@@ -1,5 +1,6 @@
 // Internal definitions shared by the host mesh code, the kernels and the C ABI.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -32,6 +33,9 @@ struct Level {
   // rho = (r_k + r_k+1)/2, h = (r_k+1 - r_k)/2.
   double* lay64 = nullptr;
   float* lay32 = nullptr;
+  // The same table as double-float pairs (hi, lo) for the double-float element ops (df = 1).
+  float* laydf = nullptr;
+  int df = 0;
   // Lateral unit vectors s, SoA [3][10 (N+1) P] in lateral layout (d (N+1) + i) P + j.
   double* s64 = nullptr;
   float* s32 = nullptr;
@@ -98,12 +102,16 @@ struct tn_mesh {
   int eta_storage = TN_ETA_F32;
   double hg_kappa = 0;
   int quad = 1;
+  int df = 1;  // FP64 A element arithmetic in double-float (tn_mesh_opts.fp64_element)
   int device = 0;
   double r_in = 0, r_out = 0;
   // Device buffers of tn_operator_steps_host: two sets of the step's 14 vectors (u 3, p, y_A 3,
   // q, y_BT 3, d 3), element size hs_elem (0: not allocated).
   void* hs_buf[2][14] = {};
   size_t hs_elem = 0;
+  // Cancel flag that tn_stokes_solve polls once per Krylov iteration (set by the server's
+  // tn_server_cancel; nullptr: never cancelled).
+  std::atomic<int>* cancel = nullptr;
 };
 
 namespace tn {

@@ -32,6 +32,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 // The file is compiled five times: TN_PART 1 holds everything but the A-apply launchers, TN_PART 2
@@ -1201,24 +1202,44 @@ __device__ __forceinline__ int ring_index(const RingDims& R, int N, int i, int j
 }
 // ring[((slot * ncomp + c) * n_r + k) * 10 * RC + d RC + rid]
 
-template <typename T, typename Op, int TI, int TJ>
+// C is the compute type of the element arithmetic, the shared-memory sums and the carried
+// partials: T itself, or double-float (dfl) for FP64 storage (values converted at load and store).
+template <typename C, typename Op, int TI, int TJ>
 struct TileSmemHF {
   static constexpr int NS = Op::LOADS ? (Op::NEEDS_D ? 2 * Op::NIN : Op::NIN) : 0;
   static constexpr int SD = NS * (TI + 1) * (TJ + 1);
   static constexpr int SM = 3 * Op::NOUT * TI * TJ;
-  static constexpr size_t bytes = sizeof(T) * (size_t)(SD + SM);
+  static constexpr size_t bytes = sizeof(C) * (size_t)(SD + SM);
 };
 
-template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI, int EK>
+// storage <-> compute conversions: identities, or binary64 <-> double-float
+template <typename C>
+__device__ __forceinline__ C to_compute(double x) {
+  if constexpr (std::is_same<C, dfl>::value) return split(x);
+  else return (C)x;
+}
+template <typename C>
+__device__ __forceinline__ C to_compute(float x) {
+  return (C)x;
+}
+template <typename T, typename C>
+__device__ __forceinline__ T to_storage(const C& x) {
+  if constexpr (std::is_same<C, dfl>::value) return (T)join(x);
+  else return (T)x;
+}
+
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI, int EK, typename C = T>
 __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ ring) {
   constexpr int NIN = Op::NIN, NOUT = Op::NOUT;
-  using Sh = TileSmemHF<T, Op, TI, TJ>;
+  using Sh = TileSmemHF<C, Op, TI, TJ>;
   constexpr int NS = Sh::NS;
   extern __shared__ __align__(16) unsigned char tile_smem[];
-  T* const sd = reinterpret_cast<T*>(tile_smem);  // [NS][TI + 1][TJ + 1]
-  T* const sm = sd + Sh::SD;                        // [3][NOUT][TI][TJ]
-  auto SD = [&](int v, int i, int j) -> T& { return sd[(v * (TI + 1) + i) * (TJ + 1) + j]; };
-  auto SM = [&](int q, int c, int i, int j) -> T& { return sm[((q * NOUT + c) * TI + i) * TJ + j]; };
+  C* const sd = reinterpret_cast<C*>(tile_smem);  // [NS][TI + 1][TJ + 1]
+  C* const sm = sd + Sh::SD;                        // [3][NOUT][TI][TJ]
+  auto SD = [&](int v, int i, int j) -> C& { return sd[(v * (TI + 1) + i) * (TJ + 1) + j]; };
+  auto SM = [&](int q, int c, int i, int j) -> C& { return sm[((q * NOUT + c) * TI + i) * TJ + j]; };
+  // the layer table in the compute type (for dfl the launcher passes the level's double-float copy)
+  const C* const layc = reinterpret_cast<const C*>(lay);
   if (skip && *skip) return;
   const int N = D.N, n_r = D.n_r, P = D.P;
   const int LS = (int)D.layer_stride, NLL = (int)D.n_lat_layout;
@@ -1231,15 +1252,16 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
   const int ci = i0 + ti, cj = j0 + tj;  // this thread's cell; its corner 00 is its own node
   const int c00 = (int)(d * D.diamond_stride) + ci * P + cj;
   const int lat00 = d * (N + 1) * P + ci * P + cj;
-  T Mi[2][9], dM[2];
+  C Mi[2][9], dM[2];
   {
     const int t0 = ((d * N + ci) * N + cj) * 2, nt = (int)D.n_tri;
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
 #pragma unroll
-      for (int q = 0; q < 9; ++q) Mi[w][q] = geo[q * nt + t0 + w];
-      dM[w] = geo[9 * nt + t0 + w];
-      if (EK != TN_ETA_F32 && Op::USES_ETA) dM[w] *= eta.cs[t0 + w];
+      for (int q = 0; q < 9; ++q) Mi[w][q] = to_compute<C>(geo[q * nt + t0 + w]);
+      T dm = geo[9 * nt + t0 + w];
+      if (EK != TN_ETA_F32 && Op::USES_ETA) dm *= eta.cs[t0 + w];
+      dM[w] = to_compute<C>(dm);
     }
   }
   const typename Op::Col col = op.column(Mi, dM, ((d * N + ci) * N + cj) * 2);
@@ -1254,8 +1276,9 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     si = e <= TJ ? TI : e - TJ - 1;
     sj = e <= TJ ? e : TJ;
   };
-  auto load_node = [&](int off, int lat, int k, T (&v)[NIN]) {
+  auto load_node = [&](int off, int lat, int k, C (&vc)[NIN]) {
     const int o = off + k * LS;
+    T v[NIN];
     v[0] = in0[o];
     if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
     if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
@@ -1265,8 +1288,10 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
       for (int c = 0; c < NIN; ++c) v[c] = vv[c];
     }
+#pragma unroll
+    for (int c = 0; c < NIN; ++c) vc[c] = to_compute<C>(v[c]);
   };
-  auto put_node = [&](int i, int j, const T (&b)[NIN], const T (&t)[NIN], T (&sv)[NIN], T (&dv)[NIN]) {
+  auto put_node = [&](int i, int j, const C (&b)[NIN], const C (&t)[NIN], C (&sv)[NIN], C (&dv)[NIN]) {
 #pragma unroll
     for (int c = 0; c < NIN; ++c) {
       sv[c] = b[c] + t[c];
@@ -1277,7 +1302,10 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
       }
     }
   };
-  auto store_node = [&](int k, int idx, int so, T (&v)[3]) {  // a finished node off the diamond edges
+  auto store_node = [&](int k, int idx, int so, const C (&vc)[3]) {  // a finished node off the diamond edges
+    T v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = c < NOUT ? to_storage<T>(vc[c]) : (T)0;
     if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
       const int bc = k == 0 ? bc_in : bc_out;
       project_vec(v, svec, (int64_t)so, (int64_t)NLL, bc);
@@ -1298,12 +1326,12 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
   };
   const int64_t ring_c = (int64_t)n_r * 10 * RD.RC;  // stride of one (slot, component)
-  auto ring_store = [&](int k, int i, int j, int slot, const T (&v)[3]) {
+  auto ring_store = [&](int k, int i, int j, int slot, const C (&v)[3]) {
     const int64_t base = (int64_t)k * 10 * RD.RC + (int64_t)d * RD.RC + ring_index(RD, N, i, j);
 #pragma unroll
-    for (int c = 0; c < NOUT; ++c) ring[(slot * NOUT + c) * ring_c + base] = v[c];
+    for (int c = 0; c < NOUT; ++c) ring[(slot * NOUT + c) * ring_c + base] = to_storage<T>(v[c]);
   };
-  auto exchange_write = [&](int k, const T (&acc)[4][NOUT]) {
+  auto exchange_write = [&](int k, const C (&acc)[4][NOUT]) {
 #pragma unroll
     for (int q = 1; q < 4; ++q)
 #pragma unroll
@@ -1312,10 +1340,10 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     {
       // own node (ci, cj): this cell's corner 00 + (ci-1, cj) corner 10 + (ci, cj-1) corner 01 +
       // (ci-1, cj-1) corner 11, the cells of this tile only
-      T v[3] = {0, 0, 0};
+      C v[3] = {C(0.0), C(0.0), C(0.0)};
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) {
-        T a = acc[0][c];
+        C a = acc[0][c];
         if (ti >= 1) a += SM(0, c, ti - 1, tj);
         if (tj >= 1) a += SM(1, c, ti, tj - 1);
         if (ti >= 1 && tj >= 1) a += SM(2, c, ti - 1, tj - 1);
@@ -1329,10 +1357,10 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
       extra_node(e, si, sj);
       // node (i0 + si, j0 + sj) on the far row / column: cells (si - 1, sj) corner 10,
       // (si, sj - 1) corner 01, (si - 1, sj - 1) corner 11 where they are in the tile
-      T v[3] = {0, 0, 0};
+      C v[3] = {C(0.0), C(0.0), C(0.0)};
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) {
-        T a = (T)0;
+        C a = C(0.0);
         if (si >= 1 && sj < TJ) a += SM(0, c, si - 1, sj);
         if (sj >= 1 && si < TI) a += SM(1, c, si, sj - 1);
         if (si >= 1 && sj >= 1) a += SM(2, c, si - 1, sj - 1);
@@ -1342,18 +1370,18 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     }
   };
 
-  T ub[NIN];
-  T carry[4][NOUT];
+  C ub[NIN];
+  C carry[4][NOUT];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int c = 0; c < NOUT; ++c) carry[q][c] = 0;
+    for (int c = 0; c < NOUT; ++c) carry[q][c] = C(0.0);
   const int kstart = kc0 > 0 ? kc0 - 1 : 0;
   if (NS > 0) load_node(c00, lat00, kstart, ub);
   for (int k = kstart; k < kc1; ++k) {
-    T s[4][NIN], dd[4][NIN];
+    C s[4][NIN], dd[4][NIN];
     if (NS > 0) {
-      T ut[NIN];
+      C ut[NIN];
       load_node(c00, lat00, k + 1, ut);
       put_node(ti, tj, ub, ut, s[0], dd[0]);
 #pragma unroll
@@ -1364,7 +1392,7 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
         const int ni = i0 + si, nj = j0 + sj;  // <= N
         const int off = (int)(d * D.diamond_stride) + ni * P + nj;
         const int lat = d * (N + 1) * P + ni * P + nj;
-        T xb[NIN], xt[NIN], xs[NIN], xd[NIN];
+        C xb[NIN], xt[NIN], xs[NIN], xd[NIN];
         load_node(off, lat, k, xb);
         load_node(off, lat, k + 1, xt);
         put_node(si, sj, xb, xt, xs, xd);
@@ -1390,20 +1418,20 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
         for (int q = 0; q < 6; ++q) prefetch_l1(E.binv[q] + idx);
     }
-    T accb[4][NOUT], acct[4][NOUT];
+    C accb[4][NOUT], acct[4][NOUT];
     {
-      T e[2] = {(T)1, (T)1};
+      C e[2] = {C(1.0), C(1.0)};
       if (Op::USES_ETA) {
         const int o = eta_c0 + k * eta_ls;
         if (EK == TN_ETA_F32) {
           const double2 p = *reinterpret_cast<const double2*>(eta.v + o);
-          e[0] = (T)p.x, e[1] = (T)p.y;
+          e[0] = to_compute<C>((T)p.x), e[1] = to_compute<C>((T)p.y);
         } else {
           const uint32_t p = *reinterpret_cast<const uint32_t*>(eta.q + o);
-          e[0] = (T)from16<EK>((uint16_t)(p & 0xffffu)), e[1] = (T)from16<EK>((uint16_t)(p >> 16));
+          e[0] = C(from16<EK>((uint16_t)(p & 0xffffu))), e[1] = C(from16<EK>((uint16_t)(p >> 16)));
         }
       }
-      op.cell(s, dd, Mi, dM, lay + kLayerStride * k, e, accb, acct, col);
+      op.cell(s, dd, Mi, dM, layc + kLayerStride * k, e, accb, acct, col);
     }
     if (k >= kc0) {
 #pragma unroll
@@ -1425,9 +1453,10 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 }
 
 // Halo-free FP64 tiles: TI x TJ threads, one CTA per SM.
-template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
+template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32,
+          typename C = T>
 __global__ void __launch_bounds__(TI * TJ, 1) k_tile_hf(TN_TILE_PARAMS, T* __restrict__ ring) {
-  tile_body_hf<T, Op, TI, TJ, FLAGS, EPI, EK>(TN_TILE_ARGS, ring);
+  tile_body_hf<T, Op, TI, TJ, FLAGS, EPI, EK, C>(TN_TILE_ARGS, ring);
 }
 
 // Thread per tile-line node and layer: the fixed-order sum of the tiles' partials (slots 0..3 of
@@ -1505,9 +1534,23 @@ __global__ void __maxnreg__(TN_WIDE_MAXREG) k_tile_wide(TN_TILE_PARAMS) {
   tile_body<T, Op, TI, TJ, FLAGS, EPI, EK>(TN_TILE_ARGS);
 }
 
+// Compute type of an op's element arithmetic: the storage type, except for the double-float
+// viscous ops on FP64 data.
+template <typename Op, typename T>
+struct OpCompute {
+  using type = T;
+};
+template <bool HG, typename T>
+struct OpCompute<OpA<dfl, HG>, T> {
+  using type = dfl;
+};
+
 template <typename T, typename Op, int FLAGS, int EPI = EPI_NONE>
 cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const EtaView<T>& eta,
                         cudaStream_t st, const int* skip = nullptr, const EpiArgs<T>* epi = nullptr) {
+  // double-float ops exist for the halo-free FP64 tiles only (levels with N >= 32)
+  using C = typename OpCompute<Op, T>::type;
+  constexpr bool kDF = !std::is_same<C, T>::value;
   EpiArgs<T> E{};
   if (epi) E = *epi;
   Dims D = dims(L);
@@ -1547,13 +1590,18 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
       return cudaGetLastError();
     }
   }
+  if constexpr (kDF) {
+    if (!(wide && TN_HALO_FREE) || !L.laydf) return cudaErrorInvalidValue;
+  }
   if constexpr (kWideT) {
     if (wide && TN_HALO_FREE) {
       // halo-free tiles: grid over the tiles proper, then the tile-line nodes
       if (!L.ring64) return cudaErrorInvalidValue;  // allocated with the level
       constexpr int TI = TILE, TJ = 2 * TILE;
-      k_tile_hf<T, Op, TI, TJ, FLAGS, EPI, TN_ETA_F32><<<grid, TI * TJ, TileSmemHF<T, Op, TI, TJ>::bytes, st>>>(
-          D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E, (T*)L.ring64);
+      // the layer table in the compute type: the level's double-float copy for dfl ops
+      const T* layk = kDF ? reinterpret_cast<const T*>(L.laydf) : lay;
+      k_tile_hf<T, Op, TI, TJ, FLAGS, EPI, TN_ETA_F32, C><<<grid, TI * TJ, TileSmemHF<C, Op, TI, TJ>::bytes, st>>>(
+          D, op, in[0], i1, i2, out[0], o1, o2, geo, layk, eta, sv, bc.in, bc.out, kc, skip, E, (T*)L.ring64);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       const RingDims RD = ring_dims(L.N, TI, TJ);
@@ -1562,19 +1610,23 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
                                                                         out[0], o1, o2, sv, bc.in, bc.out, skip, E);
       return cudaGetLastError();
     }
-    if (wide) {
-      TN_TILE_LAUNCH(k_tile_wide, TILE, 2 * TILE, TN_ETA_F32);
-      return cudaGetLastError();
+    if constexpr (!kDF) {
+      if (wide) {
+        TN_TILE_LAUNCH(k_tile_wide, TILE, 2 * TILE, TN_ETA_F32);
+        return cudaGetLastError();
+      }
     }
   }
-  switch (ti_) {
-    case 16: TN_TILE_LAUNCH(k_tile, 16, 16, TN_ETA_F32); break;
-    case 8: TN_TILE_LAUNCH(k_tile, 8, 8, TN_ETA_F32); break;
-    case 4: TN_TILE_LAUNCH(k_tile, 4, 4, TN_ETA_F32); break;
-    case 2: TN_TILE_LAUNCH(k_tile, 2, 2, TN_ETA_F32); break;
-    case 1: TN_TILE_LAUNCH(k_tile, 1, 1, TN_ETA_F32); break;
-    default:
-      return cudaErrorInvalidValue;
+  if constexpr (!kDF) {
+    switch (ti_) {
+      case 16: TN_TILE_LAUNCH(k_tile, 16, 16, TN_ETA_F32); break;
+      case 8: TN_TILE_LAUNCH(k_tile, 8, 8, TN_ETA_F32); break;
+      case 4: TN_TILE_LAUNCH(k_tile, 4, 4, TN_ETA_F32); break;
+      case 2: TN_TILE_LAUNCH(k_tile, 2, 2, TN_ETA_F32); break;
+      case 1: TN_TILE_LAUNCH(k_tile, 1, 1, TN_ETA_F32); break;
+      default:
+        return cudaErrorInvalidValue;
+    }
   }
 #undef TN_TILE_LAUNCH
   return cudaGetLastError();
@@ -2128,11 +2180,25 @@ inline double hg_coef(const Level& L, int div_term) {
   return L.hg_kappa * (3.0 + (div_term ? 1.0 / 3.0 : 1.0)) / 18.0;
 }
 
+// FP64 levels that run the halo-free tiles take the double-float element op when the mesh asks
+// for it (tn_mesh_opts.fp64_element); every other level and precision the op of its own type.
+template <typename T>
+inline bool use_df(const Level& L) {
+  return sizeof(T) == 8 && L.df && TN_WIDE_TILES && TN_HALO_FREE && L.N >= 2 * TILE;
+}
+
 template <typename T, bool HG>
 cudaError_t apply_A_hg(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                        const int* skip) {
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  if constexpr (sizeof(T) == 8) {
+    if (use_df<T>(L)) {
+      OpA<dfl, HG> op{div_term, dfl(hg_coef(L, div_term))};
+      return launch_tile<T, OpA<dfl, HG>, F>(L, bc, op, u, y, etav<T>(L), st, skip);
+    }
+  }
   OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
-  return launch_tile<T, OpA<T, HG>, PROJ_IN | PROJ_OUT | ADD_ID>(L, bc, op, u, y, etav<T>(L), st, skip);
+  return launch_tile<T, OpA<T, HG>, F>(L, bc, op, u, y, etav<T>(L), st, skip);
 }
 
 // The tile launches of the A apply with the second radial quadrature point (OpA2; their own
@@ -2159,9 +2225,21 @@ cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* 
 template <typename T, bool HG>
 cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
                            T* const* t, cudaStream_t st, const int* skip) {
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  if constexpr (sizeof(T) == 8) {
+    if (use_df<T>(L)) {
+      using Od = OpA<dfl, HG>;
+      const Od od{div_term, dfl(hg_coef(L, div_term))};
+      switch (epi) {
+        case EPI_RESID: return launch_tile<T, Od, F, EPI_RESID>(L, bc, od, in, t, etav<T>(L), st, skip, &E);
+        case EPI_CHEB1: return launch_tile<T, Od, F, EPI_CHEB1>(L, bc, od, in, t, etav<T>(L), st, skip, &E);
+        case EPI_CHEB2: return launch_tile<T, Od, F, EPI_CHEB2>(L, bc, od, in, t, etav<T>(L), st, skip, &E);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
   using Op = OpA<T, HG>;
-  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
   switch (epi) {
     case EPI_RESID: return launch_tile<T, Op, F, EPI_RESID>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
     case EPI_CHEB1: return launch_tile<T, Op, F, EPI_CHEB1>(L, bc, op, in, t, etav<T>(L), st, skip, &E);
@@ -2430,11 +2508,31 @@ cudaError_t set_wide_attrs() {
   return cudaSuccess;
 }
 
+// The double-float A ops (halo-free tiles only).
+template <typename Op, int EPI>
+cudaError_t set_df_attr() {
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  constexpr size_t shf = TileSmemHF<dfl, Op, TILE, 2 * TILE>::bytes;
+  if (shf > 48 * 1024)
+    return cudaFuncSetAttribute(k_tile_hf<double, Op, TILE, 2 * TILE, F, EPI, TN_ETA_F32, dfl>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf);
+  return cudaSuccess;
+}
+template <typename Op>
+cudaError_t set_df_attrs() {
+  const cudaError_t e[4] = {set_df_attr<Op, EPI_NONE>(), set_df_attr<Op, EPI_RESID>(), set_df_attr<Op, EPI_CHEB1>(),
+                            set_df_attr<Op, EPI_CHEB2>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+
 #if TN_PART == 0 || TN_PART == 2
 TN_INST_A(double)
 
 cudaError_t prepare_tile_kernels() {
-  const cudaError_t e[3] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
+  const cudaError_t e[5] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
+                            set_df_attrs<OpA<dfl, false>>(), set_df_attrs<OpA<dfl, true>>(),
                             prepare_tile_kernels_q2()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;

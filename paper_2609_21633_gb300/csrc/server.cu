@@ -109,6 +109,7 @@ struct Job {
   tn_result res;
   std::vector<double> u, p;  // host copy of the solution (keep_solutions)
   bool done = false;
+  std::atomic<int> cancel{0};  // set by tn_server_cancel; polled by the solver while the job runs
 };
 
 struct Pooled {
@@ -207,7 +208,9 @@ void run_job(tn_server* S, Job* J, tn_mesh* mesh, cudaStream_t st) {
       so.rtol = S->opts.rtol;
       tn_solve_stats stats{};
       if (s == TN_OK) {
+        mesh->cancel = &J->cancel;
         s = tn_stokes_solve(mesh, &so, (const double* const*)f, nullptr, u, p, &stats, st);
+        mesh->cancel = nullptr;
         J->res.iterations = stats.iterations;
         J->res.refinements = stats.refinements;
         J->res.rel_residual = stats.rel_residual;
@@ -323,8 +326,9 @@ tn_status tn_server_create(const tn_server_opts* opts, tn_server** out) {
 tn_status tn_server_submit(tn_server* S, const tn_request* req, uint64_t* ticket) {
   if (!S || !req || !ticket) return TN_EINVAL;
   if (req->lateral_level < 1 || req->radial_layers < 3 || (req->radial_layers - 1) % 2 != 0 ||
-      !(req->r_in > 0) || !(req->r_out > req->r_in) || req->t_degree < 0 || req->t_order < 0 ||
-      req->t_order > req->t_degree) {
+      !(req->r_in > 0) || !(req->r_out > req->r_in) || !std::isfinite(req->r_out) || req->t_degree < 0 ||
+      req->t_order < 0 || req->t_order > req->t_degree || !std::isfinite(req->E) || !std::isfinite(req->Ra) ||
+      !std::isfinite(req->t_amplitude)) {
     set_error("tn_server_submit: invalid request");
     return TN_EINVAL;
   }
@@ -403,6 +407,30 @@ tn_status tn_server_stats(tn_server* S, int* queued, int* running, int* resident
   if (running) *running = S->running;
   if (resident) *resident = (int)S->idle.size() + S->running;
   if (reserved_bytes) *reserved_bytes = (double)S->reserved;
+  return TN_OK;
+}
+
+tn_status tn_server_cancel(tn_server* S, uint64_t ticket) {
+  if (!S) return TN_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(ticket);
+  if (it == S->jobs.end()) {
+    set_error("tn_server_cancel: unknown ticket");
+    return TN_EINVAL;
+  }
+  Job* J = it->second;
+  if (J->done) return TN_OK;
+  J->cancel.store(1);
+  for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+    if (*q == J) {  // still queued: it never runs
+      S->queue.erase(q);
+      J->res.status = TN_ECANCELED;
+      J->res.state = 2;
+      J->res.t_start = J->res.t_end = S->now();
+      J->done = true;
+      S->cv_done.notify_all();
+      break;
+    }
   return TN_OK;
 }
 

@@ -1106,10 +1106,6 @@ void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStr
 }
 
 
-// Restarted FGMRES(m) with right preconditioning and CGS2 orthogonalisation (Saad 1993).
-// Solves K x = b from the given x; stops when ||b - K x|| <= abstol (recurrence estimate,
-// confirmed by the true residual at every restart) or after max_iters.  Returns the
-// iterations used; *res gets the final true residual norm.
 // FP64 Krylov vector -> FP32 preconditioner -> FP64 (mode TN_SOLVE_F64_PREC32): the vector is
 // unit-norm, so FP32 holds it without scaling.
 void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<double>& z, cudaStream_t st) {
@@ -1131,14 +1127,29 @@ void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<doubl
   ckl();
 }
 
+// Restarted FGMRES(m) with right preconditioning and CGS2 orthogonalisation (Saad 1993).
+// Solves K x = b from the given x; stops when ||b - K x|| <= abstol (recurrence estimate,
+// confirmed by the true residual at every restart) or after max_iters.  Returns the
+// iterations used; *res gets the final true residual norm.
+// Breakdown exits (*brk): FGMRES_NONFINITE at once when the restart residual or a Hessenberg
+// column is not finite (x keeps only the finite columns' update); FGMRES_STALL after
+// kStallRestarts restarts in a row that bring the residual less than 0.1 % below its best so far;
+// FGMRES_CANCELLED when the mesh's cancel flag is set (checked once per iteration).
+enum { FGMRES_OK = 0, FGMRES_NONFINITE = 1, FGMRES_STALL = 2, FGMRES_CANCELLED = 3 };
+constexpr int kStallRestarts = 5;
+
+bool cancelled(const tn_mesh* mesh) {
+  return mesh->cancel && mesh->cancel->load(std::memory_order_relaxed) != 0;
+}
+
 template <typename T>
 int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double abstol, int restart, int max_iters,
-           double* res, cudaStream_t st, bool prec32 = false) {
+           double* res, cudaStream_t st, bool prec32 = false, int* brk = nullptr) {
   PrecState<T>& P = ps<T>(m);
   ensure_krylov<T>(m, mesh, restart);
-  int its = 0;
+  int its = 0, stall = 0, why = FGMRES_OK;
   std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
-  double beta = 0;
+  double beta = 0, beta_best = 0;
   while (true) {
     // r = b - K x  -> V[0]
     apply_K<T>(m, mesh, x, P.w, st);
@@ -1148,7 +1159,15 @@ int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double absto
     kdots<T>(m, mesh, 1, v0, P.V[0], m->S + S_NRM, st);
     beta = std::sqrt(host_scalar(m, S_NRM, st));
     *res = beta;
-    if (beta <= abstol || its >= max_iters || g_err != cudaSuccess) break;
+    // progress is measured against the best restart residual so far: at the rounding floor the
+    // residual fluctuates, and a comparison with the previous restart alone would keep resetting
+    if (!std::isfinite(beta)) why = FGMRES_NONFINITE;
+    else if (its > 0 && !(beta < 0.999 * beta_best)) ++stall;
+    else stall = 0;
+    if (stall >= kStallRestarts) why = FGMRES_STALL;
+    if (cancelled(mesh)) why = FGMRES_CANCELLED;
+    if (its == 0 || beta < beta_best) beta_best = beta;
+    if (why != FGMRES_OK || beta <= abstol || its >= max_iters || g_err != cudaSuccess) break;
     kaxpby<T>(mesh, 0.0, P.V[0], 1.0 / beta, P.V[0], st);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1173,7 +1192,15 @@ int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double absto
       ck(cudaMemcpyAsync(hs, m->S, sizeof(double) * S_MAX, cudaMemcpyDeviceToHost, st));
       ck(cudaStreamSynchronize(st));
       double* col = &H[j * (restart + 1)];
-      for (int i = 0; i <= j; ++i) col[i] = hs[S_H + i] + hs[S_H2 + i];
+      bool finite = std::isfinite(hs[S_NRM]);
+      for (int i = 0; i <= j; ++i) {
+        col[i] = hs[S_H + i] + hs[S_H2 + i];
+        finite = finite && std::isfinite(col[i]);
+      }
+      if (!finite) {  // this column is unusable: update x with the previous ones and stop
+        why = FGMRES_NONFINITE;
+        break;
+      }
       const double hn = std::sqrt(hs[S_NRM]);
       col[j + 1] = hn;
       if (hn > 0) kaxpby<T>(mesh, 1.0 / hn, P.w, 0.0, P.V[j + 1], st);
@@ -1190,7 +1217,7 @@ int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double absto
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
       ++its;
-      if (std::fabs(g[j + 1]) <= abstol || hn == 0.0 || g_err != cudaSuccess) {
+      if (std::fabs(g[j + 1]) <= abstol || hn == 0.0 || g_err != cudaSuccess || cancelled(mesh)) {
         ++j;
         break;
       }
@@ -1204,10 +1231,21 @@ int fgmres(MGState* m, tn_mesh* mesh, const KVec<T>& b, KVec<T>& x, double absto
     ck(cudaMemcpyAsync(m->S + S_Y, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, st));
     std::vector<const KVec<T>*> zb(j);
     for (int i = 0; i < j; ++i) zb[i] = &P.Z[i];
-    kaxpy<T>(mesh, j, zb.data(), m->S + S_Y, 1.0, x, st);
+    if (j > 0) kaxpy<T>(mesh, j, zb.data(), m->S + S_Y, 1.0, x, st);
     ck(cudaStreamSynchronize(st));
+    if (why != FGMRES_OK) break;
   }
+  if (brk) *brk = why;
   return its;
+}
+
+const char* breakdown_text(int why) {
+  switch (why) {
+    case FGMRES_NONFINITE: return "breakdown: non-finite residual or Hessenberg entry (NaN / Inf in the operator or data)";
+    case FGMRES_STALL: return "stagnation: five restarts in a row without a new residual minimum (0.1 % below the best)";
+    case FGMRES_CANCELLED: return "cancelled";
+    default: return "not converged";
+  }
 }
 
 template <typename T>
@@ -1343,6 +1381,7 @@ tn_status tn_mg_setup(tn_mesh* mesh, tn_prec prec, const tn_mg_opts* opts, const
                                   mesh->div_term);
       L->hg_kappa = mesh->hg_kappa;
       L->quad = mesh->quad;
+      L->df = mesh->df;
       m->owned_levels.push_back(L);
       if (cs != TN_OK) {
         mesh->mg = m;
@@ -1475,11 +1514,12 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
   const KVec<double>* bb[1] = {&b};
   kdots<double>(m, mesh, 1, bb, b, m->S + S_NRM, st);
   const double bnorm = std::sqrt(host_scalar(m, S_NRM, st));
-  int its = 0, refs = 0;
+  int its = 0, refs = 0, why = FGMRES_OK;
   double res = bnorm;
-  if (bnorm > 0) {
+  if (!std::isfinite(bnorm)) why = FGMRES_NONFINITE;  // NaN / Inf in f or g: nothing to solve
+  if (bnorm > 0 && why == FGMRES_OK) {
     if (!mixed) {
-      its = fgmres<double>(m, mesh, b, x, o.rtol * bnorm, o.restart, o.max_iters, &res, st, prec32);
+      its = fgmres<double>(m, mesh, b, x, o.rtol * bnorm, o.restart, o.max_iters, &res, st, prec32, &why);
     } else {
       // FP64 iterative refinement around FP32 FGMRES / V-cycle inner solves
       PrecState<float>& F = m->p32;
@@ -1493,7 +1533,9 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
         const KVec<double>* rv[1] = {&r};
         kdots<double>(m, mesh, 1, rv, r, m->S + S_NRM, st);
         res = std::sqrt(host_scalar(m, S_NRM, st));
-        if (res <= o.rtol * bnorm || g_err != cudaSuccess) break;
+        if (!std::isfinite(res)) why = FGMRES_NONFINITE;
+        else if (cancelled(mesh)) why = FGMRES_CANCELLED;
+        if (why != FGMRES_OK || res <= o.rtol * bnorm || g_err != cudaSuccess) break;
         for (int c = 0; c < 3; ++c) {
           k_convert<double, float><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, r.u[c], rr32.u[c], 1.0 / res);
           ckl();
@@ -1503,7 +1545,13 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
         ckl();
         ck(cudaMemsetAsync(c32.p, 0, sizeof(float) * L1.n_layout, st));
         double ires = 0;
-        its += fgmres<float>(m, mesh, rr32, c32, o.inner_rtol, o.restart, o.inner_max_iters, &ires, st);
+        int iwhy = FGMRES_OK;
+        its += fgmres<float>(m, mesh, rr32, c32, o.inner_rtol, o.restart, o.inner_max_iters, &ires, st, false, &iwhy);
+        // an inner stall only ends this refinement step; non-finite values or a cancel end the solve
+        if (iwhy == FGMRES_NONFINITE || iwhy == FGMRES_CANCELLED) {
+          why = iwhy;
+          break;
+        }
         for (int c = 0; c < 3; ++c) {
           k_accum<float><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, c32.u[c], x.u[c], res);
           ckl();
@@ -1531,14 +1579,18 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
     stats->refinements = refs;
     stats->rel_residual = rel;
     stats->seconds = std::chrono::duration<double>(t1 - t0).count();
-    stats->converged = rel <= o.rtol;
+    stats->converged = why == FGMRES_OK && rel <= o.rtol;
   }
   if (g_err != cudaSuccess) {
     set_error(std::string("tn_stokes_solve: ") + cudaGetErrorString(g_err));
     return TN_ECUDA;
   }
-  if (rel > o.rtol) {
-    set_error("tn_stokes_solve: not converged");
+  if (why == FGMRES_CANCELLED) {
+    set_error("tn_stokes_solve: cancelled");
+    return TN_ECANCELED;
+  }
+  if (why != FGMRES_OK || !(rel <= o.rtol)) {  // !(<=): a NaN residual is not convergence
+    set_error(std::string("tn_stokes_solve: ") + breakdown_text(why));
     return TN_ENOTCONVERGED;
   }
   return TN_OK;

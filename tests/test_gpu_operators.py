@@ -35,10 +35,10 @@ class Case:
     """One mesh on both sides with random fields (seeded)."""
 
     def __init__(self, tn, level, n_r, bc=(0, 0), div_term=True, seed=0, r_in=0.55, r_out=1.0, eta_storage=0,
-                 hg_kappa=0.0, quad=1):
+                 hg_kappa=0.0, quad=1, fp64_element=0):
         self.tn = tn
         self.m = tn.tn_mesh_create(level, n_r, r_in, r_out, bc[0], bc[1], div_term, eta_storage=eta_storage,
-                                   hg_kappa=hg_kappa, radial_quad_points=quad)
+                                   hg_kappa=hg_kappa, radial_quad_points=quad, fp64_element=fp64_element)
         self.info = tn.tn_mesh_info(self.m, 0)
         self.om = ShellMesh(level, n_r, r_in, r_out)
         self.map = LayoutMap(self.info, self.om)
@@ -95,6 +95,28 @@ def test_apply_A_f64(tn, level, n_r, bc):
     tn.tn_apply_A(c.m, 0, ud, y2)
     assert all(torch.equal(a, b) for a, b in zip(y, y2))
     c.close()
+
+
+@pytest.mark.parametrize("level,n_r,bc,kappa,div_term", [
+    (5, 9, "free/free", 0.0, True), (5, 17, "noslip/free", 0.0, True), (6, 9, "free/free", 0.0, True),
+    (5, 9, "free/free", 0.3, True), (5, 9, "noslip/noslip", 0.0, False)])
+def test_apply_A_f64_element_arithmetics(tn, level, n_r, bc, kappa, div_term):
+    """Levels with N >= 32 evaluate the FP64 element op in double-float by default
+    (TN_FP64_ELEM_DOUBLE_FLOAT) or in binary64 (TN_FP64_ELEM_BINARY64): both meet the FP64 bar
+    against the oracle, and they agree with each other to it."""
+    got = {}
+    for elem in (tn.TN_FP64_ELEM_DOUBLE_FLOAT, tn.TN_FP64_ELEM_BINARY64):
+        c = Case(tn, level, n_r, BCS[bc], div_term=div_term, hg_kappa=kappa, fp64_element=elem)
+        u = c.vec(31)
+        want = O.apply_A_constrained(c.om, c.eta, u, c.P, div_term=div_term, kappa=kappa)
+        y = c.zeros()
+        tn.tn_apply_A(c.m, 0, [c.dev(u[i]) for i in range(3)], y)
+        got[elem] = np.stack([c.host(t) for t in y])
+        err = max_rel(got[elem], want)
+        print(f"level {level} / {n_r} {bc} kappa {kappa} element arithmetic {elem}: max-rel {err:.2e}")
+        assert err <= TOL64, (elem, err)
+        c.close()
+    assert max_rel(got[0], got[1]) <= TOL64
 
 
 def test_apply_A_without_div_term(tn):
@@ -365,3 +387,25 @@ def test_argument_errors(tn):
     assert e.value.status == tn.TN_ESTATE
     tn.tn_mesh_destroy(m2)
     c.close()
+
+
+def test_operator_steps_host_rejects_bad_buffers(tn):
+    """The binding checks every host buffer before the call: device, contiguity, one dtype and the
+    layout size of its slot (the C side copies n_layout elements on trust)."""
+    c = Case(tn, 3, 9, BCS["free/free"])
+    n, npr = c.info["n_layout"], tn.tn_mesh_info(c.m, 1)["n_layout"]
+    u = [torch.zeros(n, dtype=torch.float64) for _ in range(3)]
+    p = torch.zeros(npr, dtype=torch.float64)
+    good = [torch.zeros(m, dtype=torch.float64) for m in [n, n, n, npr, n, n, n, n, n, n]]
+    tn.tn_operator_steps_host(c.m, [u], [p], [good])
+    torch.cuda.synchronize()
+    bad_cases = [
+        [good[0][:-1]] + good[1:],                                   # undersized output
+        good[:3] + [torch.zeros(n, dtype=torch.float64)] + good[4:],  # q slot with the velocity size
+        [good[0].float()] + good[1:],                                # mixed dtypes
+        [good[0].cuda()] + good[1:],                                 # device tensor as a host buffer
+        [torch.zeros(2 * n, dtype=torch.float64)[::2]] + good[1:],   # not contiguous
+    ]
+    for outs in bad_cases:
+        with pytest.raises(ValueError):
+            tn.tn_operator_steps_host(c.m, [u], [p], [outs])
