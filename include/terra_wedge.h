@@ -89,12 +89,13 @@ typedef enum { TN_BC_FREESLIP = 0, TN_BC_NOSLIP = 1 } tn_bc;
  * column of wedges (lateral wedge (d, i, j, w) over all radial cells), c = sqrt(min * max) of the
  * column, so the stored values straddle 1; used on levels with N >= 16, FP32 on coarser ones. */
 typedef enum { TN_ETA_F32 = 0, TN_ETA_BF16 = 1, TN_ETA_F16 = 2 } tn_eta_storage;
-/* Arithmetic of the FP64 viscous element op (A, its residual and smoother epilogues) on levels with
- * N >= 32, where it bounds the apply: TN_FP64_ELEM_DOUBLE_FLOAT evaluates Eq. epsq / Eq. localapply
- * in double-float (pairs of FP32 numbers, about 48 significand bits, on the FP32 pipe; every
- * operation's relative error is below 2^-45) with binary64 inputs, outputs, boundary projections,
- * interface sums and epilogues; TN_FP64_ELEM_BINARY64 in IEEE binary64 throughout.  Coarser levels,
- * B, B^T and the diagonals always use binary64. */
+/* Arithmetic of the FP64 element ops (A with its residual and smoother epilogues, B, B^T and the
+ * interior layers of diag(A)) on levels with N >= 32, where it bounds the apply:
+ * TN_FP64_ELEM_DOUBLE_FLOAT evaluates them (Eq. epsq / Eq. localapply and the one-point B) in
+ * double-float (pairs of FP32 numbers, about 48 significand bits, on the FP32 pipe; each
+ * operation's error is below 2^-44 of its operands' magnitude), with binary64 inputs, outputs, boundary projections,
+ * interface sums and epilogues; TN_FP64_ELEM_BINARY64 in IEEE binary64 throughout.  Coarser levels
+ * and the node-block diagonals always use binary64. */
 typedef enum { TN_FP64_ELEM_DOUBLE_FLOAT = 0, TN_FP64_ELEM_BINARY64 = 1 } tn_fp64_element;
 
 typedef struct tn_mesh tn_mesh;

@@ -35,6 +35,16 @@ cudaError_t upload(T*& dst, const std::vector<T>& src) {
   return cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
 }
 
+// a table as double-float pairs (hi, lo), split exactly as the kernels split binary64 values
+std::vector<float> to_df(const std::vector<double>& v) {
+  std::vector<float> out(2 * v.size());
+  for (size_t q = 0; q < v.size(); ++q) {
+    const dfl x = split(v[q]);
+    out[2 * q] = x.hi, out[2 * q + 1] = x.lo;
+  }
+  return out;
+}
+
 template <typename T>
 std::vector<float> to_f32(const std::vector<T>& v) {
   std::vector<float> out(v.size());
@@ -45,7 +55,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.laydf, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32, L.dcoef64, L.dcoef32, L.ring64};
+                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -136,19 +146,12 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
     const std::vector<double> dc = diag_factors(geo, L.n_tri, div_term);
     chk(upload(L.dcoef64, dc));
     chk(upload(L.dcoef32, to_f32(dc)));
+    chk(upload(L.dcoefdf, to_df(dc)));
     L.dcoef_div = div_term;
   }
   chk(upload(L.lay64, lay));
   chk(upload(L.lay32, to_f32(lay)));
-  {
-    // the layer table as double-float pairs, split exactly as the kernels split binary64 values
-    std::vector<float> ldf(2 * lay.size());
-    for (size_t q = 0; q < lay.size(); ++q) {
-      const dfl v = split(lay[q]);
-      ldf[2 * q] = v.hi, ldf[2 * q + 1] = v.lo;
-    }
-    chk(upload(L.laydf, ldf));
-  }
+  chk(upload(L.laydf, to_df(lay)));
   chk(upload(L.s64, s));
   chk(upload(L.s32, to_f32(s)));
   chk(upload(L.grp_ptr, gptr));

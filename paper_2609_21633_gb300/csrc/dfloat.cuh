@@ -17,7 +17,7 @@
 // Conversions from and to binary64 use integer operations only (no FP64 instruction):
 //   split: hi = the double truncated to 24 significand bits, lo = the next 23 bits (exact
 //   integer-to-float trick), then FastTwoSum to restore |lo| <= ulp(hi) / 2; relative error
-//   <= 2^-47.  Magnitudes below 2^-80 keep only hi, and values outside the FP32 exponent range
+//   below 2^-46 (both parts are truncated).  Magnitudes below 2^-80 keep only hi, and values outside the FP32 exponent range
 //   are not representable (the wedge operator's data are far inside both limits).
 //   join: hi and lo widened exactly to binary64 (bit manipulation) and added with one FP64 add,
 //   which is exact because hi + lo has at most 48 significant bits.
@@ -85,6 +85,30 @@ TN_DF_HD dfl operator*(dfl x, dfl y) {
   const float cl3 = TN_FADD(cl1, cl2);
   float zh, zl;
   fast_two_sum(ch, cl3, zh, zl);
+  return dfl(zh, zl);
+}
+
+// Sum without the second TwoSum (the "sloppy" double-word addition): absolute error about
+// 2u^2 (|x| + |y|), so it is kept for sums whose terms do not cancel; 11 operations.
+TN_DF_HD dfl add_nc(dfl x, dfl y) {
+  float sh, sl, zh, zl;
+  two_sum(x.hi, y.hi, sh, sl);
+  const float w = TN_FADD(sl, TN_FADD(x.lo, y.lo));
+  fast_two_sum(sh, w, zh, zl);
+  return dfl(zh, zl);
+}
+// x y + w in one pass: the exact product of the high parts (TwoProd), the cross terms by FMA,
+// then the sloppy addition of w; absolute error about 3u^2 (|x y| + |w|), for the same use;
+// 15 operations against 20 for a multiplication followed by an addition.
+TN_DF_HD dfl fma_nc(dfl x, dfl y, dfl w) {
+  const float ph = TN_FMUL(x.hi, y.hi);
+  float pl = TN_FFMA(x.hi, y.hi, -ph);
+  pl = TN_FFMA(x.hi, y.lo, pl);
+  pl = TN_FFMA(x.lo, y.hi, pl);
+  float sh, sl, zh, zl;
+  two_sum(ph, w.hi, sh, sl);
+  const float t = TN_FADD(sl, TN_FADD(pl, w.lo));
+  fast_two_sum(sh, t, zh, zl);
   return dfl(zh, zl);
 }
 

@@ -61,6 +61,7 @@ struct Level {
   // Per-triangle factors of the diagonal of A ([24][n_tri], see OpDiag), for div term dcoef_div.
   double* dcoef64 = nullptr;
   float* dcoef32 = nullptr;
+  float* dcoefdf = nullptr;  // the same table as double-float pairs (hi, lo)
   int dcoef_div = -1;
   // Tile-line partial sums of the FP64 halo-free tile kernels (levels with N >= 32):
   // [4 slots][3 components][n_r][10][tile-line nodes of a diamond layer].

@@ -310,6 +310,67 @@ struct OpA {
   }
 };
 
+// Double-float viscous block without hourglass control: the arithmetic of OpA with the sums
+// split by whether their terms can cancel.  The corner differences (a_xi, a_eta of nearly equal
+// nodal sums) and every node-level accumulation (combine_corners, carried and exchanged partials)
+// use the accurate double-word addition; the contractions that form the strain, the stress and
+// H = S M^-T, whose terms carry no such cancellation, use the fused multiply-add and the sum
+// without the second TwoSum (add_nc / fma_nc), about half the FP32 operations.
+template <>
+struct OpA<dfl, false> {
+  static constexpr int NIN = 3, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
+  using Col = NoCol;
+  int div_term;
+  dfl hgk;
+  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&Mi)[2][9],
+                                       const dfl (&dM)[2], const dfl* lc, const dfl (&eta)[2], dfl (&accb)[4][3],
+                                       dfl (&acct)[4][3], const Col&) const {
+    const dfl r = lc[4], vw2 = lc[5];
+    dfl X[4][3], h[2][3];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const dfl* M = Mi[w];
+      const dfl mr[3] = {r * M[6], r * M[7], r * M[8]};
+      dfl G[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dfl ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c];
+        const dfl az = add_nc(add_nc(dd[c0][c], dd[c1][c]), dd[c2][c]);
+#pragma unroll
+        for (int x = 0; x < 3; ++x) G[c][x] = fma_nc(ax, M[x], fma_nc(ay, M[3 + x], az * mr[x]));
+      }
+      const dfl ve = (vw2 * dM[w]) * eta[w];
+      const dfl ve2(ve.hi + ve.hi, ve.lo + ve.lo);  // exact doubling
+      dfl S[3][3];
+      if (div_term) {
+        const dfl vt = (ve * dfl(-2.0 / 3.0)) * add_nc(add_nc(G[0][0], G[1][1]), G[2][2]);
+        S[0][0] = fma_nc(ve2, G[0][0], vt), S[1][1] = fma_nc(ve2, G[1][1], vt), S[2][2] = fma_nc(ve2, G[2][2], vt);
+      } else {
+        S[0][0] = ve2 * G[0][0], S[1][1] = ve2 * G[1][1], S[2][2] = ve2 * G[2][2];
+      }
+      S[0][1] = S[1][0] = ve * add_nc(G[0][1], G[1][0]);
+      S[0][2] = S[2][0] = ve * add_nc(G[0][2], G[2][0]);
+      S[1][2] = S[2][1] = ve * add_nc(G[1][2], G[2][1]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dfl h0 = fma_nc(S[c][0], M[0], fma_nc(S[c][1], M[1], S[c][2] * M[2]));
+        const dfl h1 = fma_nc(S[c][0], M[3], fma_nc(S[c][1], M[4], S[c][2] * M[5]));
+        h[w][c] = fma_nc(S[c][0], mr[0], fma_nc(S[c][1], mr[1], S[c][2] * mr[2]));
+        X[c0][c] = -(h0 + h1);
+        if (w == 0) {
+          X[c1][c] = h0, X[c2][c] = h1;
+        } else {
+          X[c1][c] += h0, X[c2][c] += h1;
+        }
+      }
+    }
+    combine_corners<dfl, 3>(X, h, accb, acct);
+  }
+};
+
 // Packed FP32 pairs (sm_100+ f32x2 instructions): one instruction per pair halves the issue
 // slots of the FP32 element arithmetic, which bounds the FP32 tile kernels.
 __device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
@@ -1544,6 +1605,18 @@ template <bool HG, typename T>
 struct OpCompute<OpA<dfl, HG>, T> {
   using type = dfl;
 };
+template <typename T>
+struct OpCompute<OpDiv<dfl>, T> {
+  using type = dfl;
+};
+template <typename T>
+struct OpCompute<OpGrad<dfl>, T> {
+  using type = dfl;
+};
+template <bool HG, typename T>
+struct OpCompute<OpDiag<dfl, HG>, T> {
+  using type = dfl;
+};
 
 template <typename T, typename Op, int FLAGS, int EPI = EPI_NONE>
 cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* const* out, const EtaView<T>& eta,
@@ -2273,7 +2346,15 @@ cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, con
 template <typename T>
 cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cudaStream_t st) {
   T* out[1] = {q};
-  cudaError_t e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, EtaView<T>{}, st);
+  cudaError_t e = cudaSuccess;
+  bool done = false;
+  if constexpr (sizeof(T) == 8) {
+    if (use_df<T>(L)) {
+      e = launch_tile<T, OpDiv<dfl>, PROJ_IN>(L, bc, OpDiv<dfl>{}, u, out, EtaView<T>{}, st);
+      done = true;
+    }
+  }
+  if (!done) e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, EtaView<T>{}, st);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 1, 0, out, nullptr, st);
 }
@@ -2281,7 +2362,15 @@ cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cuda
 template <typename T>
 cudaError_t launch_grad_fine(const Level& L, BC bc, const T* p, T* const* y, cudaStream_t st) {
   const T* in[1] = {p};
-  cudaError_t e = launch_tile<T, OpGrad<T>, PROJ_OUT>(L, bc, OpGrad<T>{}, in, y, EtaView<T>{}, st);
+  cudaError_t e = cudaSuccess;
+  bool done = false;
+  if constexpr (sizeof(T) == 8) {
+    if (use_df<T>(L)) {
+      e = launch_tile<T, OpGrad<dfl>, PROJ_OUT>(L, bc, OpGrad<dfl>{}, in, y, EtaView<T>{}, st);
+      done = true;
+    }
+  }
+  if (!done) e = launch_tile<T, OpGrad<T>, PROJ_OUT>(L, bc, OpGrad<T>{}, in, y, EtaView<T>{}, st);
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 3, 0, y, nullptr, st);
 }
@@ -2298,12 +2387,22 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
     e = launch_tile<T, OpDiag2<T>, 0>(L, bc, OpDiag2<T>{div_term}, none, d, etav<T>(L), st);
   } else if constexpr (sizeof(T) == 8) {  // FP64: per-triangle factor table
     if (!L.dcoef64 || L.dcoef_div != div_term) return cudaErrorInvalidValue;  // built with the level
-    const T* coef = Tab<T>::dcoef(L);
     const int nt = (int)L.n_tri;
-    e = hg ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk, coef, nt}, none, d, etav<T>(L),
-                                               st)
-           : launch_tile<T, OpDiag<T, false>, 0>(L, bc, OpDiag<T, false>{div_term, hgk, coef, nt}, none, d,
-                                                etav<T>(L), st);
+    if (use_df<T>(L)) {  // the table's double-float copy
+      if (!L.dcoefdf) return cudaErrorInvalidValue;
+      const dfl* cdf = reinterpret_cast<const dfl*>(L.dcoefdf);
+      const dfl hk(hg_coef(L, div_term));
+      e = hg ? launch_tile<T, OpDiag<dfl, true>, 0>(L, bc, OpDiag<dfl, true>{div_term, hk, cdf, nt}, none, d,
+                                                    etav<T>(L), st)
+             : launch_tile<T, OpDiag<dfl, false>, 0>(L, bc, OpDiag<dfl, false>{div_term, hk, cdf, nt}, none, d,
+                                                     etav<T>(L), st);
+    } else {
+      const T* coef = Tab<T>::dcoef(L);
+      e = hg ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk, coef, nt}, none, d,
+                                                 etav<T>(L), st)
+             : launch_tile<T, OpDiag<T, false>, 0>(L, bc, OpDiag<T, false>{div_term, hgk, coef, nt}, none, d,
+                                                  etav<T>(L), st);
+    }
   } else {  // FP32: gradient form
     e = hg ? launch_tile<T, OpDiagG<T, true>, 0>(L, bc, OpDiagG<T, true>{div_term, hgk}, none, d, etav<T>(L), st)
            : launch_tile<T, OpDiagG<T, false>, 0>(L, bc, OpDiagG<T, false>{div_term, hgk}, none, d, etav<T>(L), st);

@@ -141,7 +141,8 @@ def test_apply_A_f32(tn):
 
 
 @pytest.mark.parametrize("level,n_r,bc,div_term", [(3, 9, "noslip/free", True), (4, 17, "free/free", True),
-                                                  (4, 9, "free/free", False)])
+                                                  (4, 9, "free/free", False), (5, 9, "free/free", True),
+                                                  (5, 9, "noslip/noslip", False)])
 def test_hourglass_control_apply_and_diag(tn, level, n_r, bc, div_term):
     """Eq. (hgstab) with kappa = 0.3: FP64 apply and diagonal at the FP64 bar, FP32 apply at the
     FP32 bar, against the oracle's explicit element matrices with Flanagan-Belytschko vectors."""
@@ -235,7 +236,7 @@ def test_apply_A_and_diag_f32_with_16bit_viscosity(tn, kind, unit):
 
 
 @pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"), (4, 27, "free/free"),
-                                          (5, 9, "free/free")])
+                                          (5, 9, "free/free"), (5, 17, "noslip/free")])
 def test_apply_B_and_BT_f64(tn, level, n_r, bc):
     c = Case(tn, level, n_r, BCS[bc])
     pm = O.pressure_mesh(c.om)
