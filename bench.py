@@ -28,16 +28,33 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 R_IN, R_OUT = 0.55, 1.0
+
+
+def measured_hbm_gbs():
+    """Copy bandwidth of the GB300s (MEASURED_PEAKS.json beside this file), else the
+    earlier measurement 6771.8 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6771.8
+
+
+HBM_GBS = measured_hbm_gbs()
 LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, contrast 1e3
 # Algorithmic FP64 work of one A apply per hexahedral cell (2 wedges, one-point rule), FMA = 2
 # flops: the differences-only gather, the factorised Jacobian, strain, stress, the stress times
 # the inverse Jacobian and the differences-only scatter of Eq. epsq / Eq. localapply, counted
 # from their structure at 240 flops per wedge.
 A_FLOPS_PER_CELL = 480.0
-# DRAM bytes per cell of the FP64 A apply measured by ncu (level 6, 65 layers, 176.8 MB for
-# 2,621,440 cells, halo-free 16 x 32 tiles), scaled to the bench size by cells; None once the
-# kernel changes.
-A_TRAFFIC_BYTES_PER_CELL = 176.77e6 / 2621440
+# ncu figures of the A tile kernel with the double-float element op (level 6, 65 layers,
+# 2,621,440 cells, one launch): DRAM bytes (125.93 MB read + 50.44 MB written) and issued warp
+# instructions (378,115,816) per cell, scaled to the bench size by cells; None once the kernel
+# changes.
+A_TRAFFIC_BYTES_PER_CELL = (125.93e6 + 50.44e6) / 2621440
+A_WARP_INST_PER_CELL = 378115816 / 2621440
+# Issue rate derived from unit counts: 152 SMs x 4 schedulers x 1 warp instruction per clock.
+ISSUE_SLOTS_PER_CLOCK = 152 * 4
 # Hourglass-control coefficient of the solves and the serving stream that use it.
 HG_KAPPA = 0.3
 # Kernel launches of one A + B + B^T + diag step: A 2 (tile, interface), B 4 (tile, interface,
@@ -535,6 +552,9 @@ def main():
         achieved = a_flops / (per_op["A"] / 1e3) / 1e12
         dfma_peak = tn.tn_probe_fma_peak(torch.float64, st)  # measured live, same clocks as the step
         ffma_peak = tn.tn_probe_fma_peak(torch.float32, st)
+        sm_hz = 1e6 * ((clk or {}).get("sm_mhz") or 2070.0)
+        issue_peak = ISSUE_SLOTS_PER_CLOCK * sm_hz / 1e12
+        issue_achieved = A_WARP_INST_PER_CELL * cells / (per_op["A"] / 1e3) / 1e12
         line = {
             "metric": "Stokes-apply GDoF/s (FP64 A+B+BT+diag step)", "value": value, "unit": "GDoF/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
@@ -544,18 +564,25 @@ def main():
                        "l2": "inputs larger than L2 (3 x %.0f MB velocity components)" % (n * 8 / 1e6)},
             "per_op_ms": per_op,
             "A_ms_binary64_element": a_binary64_ms,
-            "roofline": {"bound": "alu", "kernel": "A apply (tile kernel + interface sum)", "achieved": achieved,
-                         "peak": dfma_peak, "unit": "TFLOP/s", "frac": achieved / dfma_peak,
+            "roofline": {"bound": "alu", "kernel": "A apply, double-float element op (tile kernel + tile-line "
+                                                  "and interface passes)",
+                         "achieved": issue_achieved, "peak": issue_peak, "unit": "Twarp-inst/s (issue)",
+                         "frac": issue_achieved / issue_peak,
                          "traffic": A_TRAFFIC_BYTES_PER_CELL * cells if A_TRAFFIC_BYTES_PER_CELL else None,
-                         "flops_per_cell": A_FLOPS_PER_CELL,
-                         "peak_note": "FP64 DFMA rate measured in this run (tn_probe_fma_peak); derived "
-                                      "152 SMs x 2 DFMA/clk x 2.07 GHz = %.3f TFLOP/s" % FP64_PEAK_TFLOPS,
-                         "frac_of_derived_peak": achieved / FP64_PEAK_TFLOPS,
-                         "ffma_peak_tflops": ffma_peak,
-                         "hbm_frac_of_measured": (64.0 * cells) / (per_op["A"] / 1e3) / 6771.8e9},
+                         "warp_inst_per_cell": A_WARP_INST_PER_CELL,
+                         "peak_note": "instruction issue, 152 SMs x 4 schedulers x 1 warp instruction/clk at the "
+                                      "median SM clock under load; instructions per cell from ncu (level 6 / 65)",
+                         "fp64_equiv_tflops": achieved, "flops_per_cell": A_FLOPS_PER_CELL,
+                         "fp64_equiv_over_dfma_peak": achieved / dfma_peak, "dfma_peak_tflops": dfma_peak,
+                         "dfma_peak_derived_tflops": FP64_PEAK_TFLOPS, "ffma_peak_tflops": ffma_peak,
+                         "binary64_element": {"A_ms": a_binary64_ms,
+                                              "tflops": A_FLOPS_PER_CELL * cells / (a_binary64_ms / 1e3) / 1e12,
+                                              "frac_of_dfma_peak": A_FLOPS_PER_CELL * cells / (a_binary64_ms / 1e3)
+                                              / 1e12 / dfma_peak},
+                         "hbm_frac_of_measured": (64.0 * cells) / (per_op["A"] / 1e3) / HBM_GBS / 1e9},
             "f32_step": {"ms_per_step": ms32 / args.steps, "per_op_ms": per32,
                          "value": ndof / (ms32 / args.steps / 1e3) / 1e9, "unit": "GDoF/s",
-                         "A_hbm_frac_of_measured": (32.0 * cells) / (per32["A"] / 1e3) / 6771.8e9},
+                         "A_hbm_frac_of_measured": (32.0 * cells) / (per32["A"] / 1e3) / HBM_GBS / 1e9},
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},

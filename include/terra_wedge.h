@@ -185,7 +185,8 @@ tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* 
 
 /* q = B P u: divergence onto the pressure space of level h (node layout of level h+1).
  * B[k, (j,d)] = -sum_e V_e psi_k(q_c^e) dN_j/dx_d(q_c^e), psi_k the pressure basis
- * (nested iso-interpolation of the coarse W1 function, Sec. 3).  Stream-ordered. */
+ * (nested iso-interpolation of the coarse W1 function, Sec. 3); on level 0 with a reference state
+ * (tn_set_reference_state) the TALA divergence B_rho P u.  Stream-ordered. */
 tn_status tn_apply_B(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* q_dev, void* stream);
 
 /* q = B P u exactly as tn_apply_B (same kernels, same result), with the one intermediate that
@@ -252,8 +253,26 @@ tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int app
                       const void* const* fine_dev, void* const* coarse_dev, void* stream);
 
 /* Boussinesq buoyancy right-hand side f = P sum_e V_e Ra T(q_c) r_hat(q_c) N_j(q_c) on level 0
- * (Eq. stokes with the full temperature); f_dev[3] doubles.  Stream-ordered. */
+ * (Eq. stokes with the full temperature); f_dev[3] doubles.  With a reference state set
+ * (tn_set_reference_state) each wedge's term is weighted by rho(q_c) alpha(q_c), the TALA load
+ * Ra rho alpha T' r_hat of Eq. stokes, and T_node_dev is then the perturbation T' of Eq. tsplit.
+ * Stream-ordered. */
 tn_status tn_buoyancy(tn_mesh* mesh, const double* T_node_dev, double Ra, double* const* f_dev, void* stream);
+
+/* TALA reference state (Sec. 1, Eq. stokes and Eq. mass): the reference density rho_host[k] > 0 and
+ * thermal expansivity alpha_host[k] at the level-0 node radii r_k, k = 0 .. N_r - 1 (host arrays,
+ * copied; alpha_host NULL = 1; rho_host NULL removes the reference state: the Boussinesq system).
+ * With it the mass constraint is div(rho u) = 0, discretised by the product rule at the quadrature
+ * point: B_rho[k, (j,d)] = -sum_e V_e psi_k(q_c) (rho(q_c) dN_j/dx_d + rho'(q_c) r_hat_d(q_c) / 6),
+ * rho(q_c) = (rho_k + rho_k+1) / 2, rho' = (rho_k+1 - rho_k) / (r_k+1 - r_k), r_hat(q_c) the unit
+ * radial direction of the wedge centre; rigid rotations stay an exact null space.  tn_apply_B,
+ * tn_apply_B_static, tn_operator_steps_host and tn_stokes_solve use this B, so the saddle matrix
+ * [[P A P + I - P, P B^T], [B_rho P, 0]] is not symmetric (FGMRES needs no symmetry);
+ * tn_apply_BT, the momentum block and the preconditioner are unchanged, and tn_buoyancy weights
+ * its load by rho(q_c) alpha(q_c) (each the mean of the wedge's six nodal values).  Resets the
+ * multigrid set-up.  Synchronous.  Errors: TN_EINVAL (NULL mesh, rho <= 0 or non-finite),
+ * TN_ENOMEM, TN_ECUDA. */
+tn_status tn_set_reference_state(tn_mesh* mesh, const double* rho_host, const double* alpha_host);
 
 
 /* Measured fused multiply-add throughput of the current device in TFLOP/s (FMA = 2 flops), for

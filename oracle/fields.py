@@ -68,8 +68,20 @@ def coarsen_viscosity(fine, coarse, eta_fine):
     return acc / 8.0
 
 
-def buoyancy_rhs(mesh, T_nodes, Ra, P=None, wedges=None):
-    """Right-hand side f (3, n): sum_e V_e Ra T(q_c) r_hat(q_c) / 6, projected by P if given.
+def reference_weight(mesh, rho, alpha, wedges=None):
+    """rho(q_c) alpha(q_c) per wedge for reference profiles given at the node layers (rho[k],
+    alpha[k] at r_k): each is the mean of its six nodal values at q_c (all N_j(q_c) = 1/6), the
+    layer mean, and the buoyancy of Eq. (stokes) takes their product."""
+    ids = np.arange(mesh.n_wedges) if wedges is None else np.asarray(wedges)
+    k = ids % (mesh.n_r - 1)
+    rho, alpha = np.asarray(rho, dtype=np.float64), np.asarray(alpha, dtype=np.float64)
+    return (0.5 * (rho[k] + rho[k + 1])) * (0.5 * (alpha[k] + alpha[k + 1]))
+
+
+def buoyancy_rhs(mesh, T_nodes, Ra, P=None, wedges=None, rho=None, alpha=None):
+    """Right-hand side f (3, n): sum_e V_e Ra T(q_c) r_hat(q_c) / 6, projected by P if given;
+    with reference profiles rho, alpha (TALA, Eq. stokes: Ra rho alpha T' r_hat, T_nodes then
+    the perturbation T') each wedge's term is weighted by rho(q_c) alpha(q_c).
 
     Summed over the given wedges (all if None): complete at every node whose wedges are all in
     ``wedges``."""
@@ -77,6 +89,8 @@ def buoyancy_rhs(mesh, T_nodes, Ra, P=None, wedges=None):
     nodes = mesh.wedge_nodes(wedges)
     _, V = wedge_geometry(mesh, wedges)
     Te = wedge_temperature(mesh, T_nodes, wedges)
+    if rho is not None:
+        Te = Te * reference_weight(mesh, rho, alpha, wedges)
     xc = mesh.node_xyz(nodes.ravel()).reshape(-1, 6, 3).sum(axis=1) / 6.0
     rhat = xc / np.linalg.norm(xc, axis=1)[:, None]
     f = np.zeros((3, n))

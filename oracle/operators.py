@@ -209,17 +209,37 @@ def psi_at_centroids(mesh, Pp, wedges=None):
     return (wedge_incidence(mesh, wedges) @ Pp / 6.0).tocsr()
 
 
-def assemble_B(mesh, Pp, wedges=None):
-    """Assembled B (n_p x 3 n): B[k, (j,d)] = - sum_e V_e psi_k(q_c^e) dN_j/dx_d (q_c^e)."""
+def assemble_B(mesh, Pp, wedges=None, rho=None):
+    """Assembled B (n_p x 3 n): B[k, (j,d)] = - sum_e V_e psi_k(q_c^e) dN_j/dx_d (q_c^e).
+
+    With a reference density rho (one value per node layer, rho[k] at r_k) this is the divergence
+    of Eq. (mass), div(rho u) (TALA, Sec. 1).  Reading (the paper states the continuous equation
+    only): the product rule at the quadrature point,
+        div(rho u)(q_c) = rho(q_c) div u_h(q_c) + rho'(q_c) r_hat(q_c) . u_h(q_c),
+    with rho(q_c) = (rho_k + rho_k+1) / 2 and rho'(q_c) = (rho_k+1 - rho_k) / (r_k+1 - r_k) of the
+    radial P1 interpolant, r_hat(q_c) = x(q_c) / |x(q_c)| and u_h(q_c) the mean of the six nodal
+    values (N_j(q_c) = 1/6), so B[k, (j,d)] = - sum_e V_e psi_k(q_c) (rho_e dN_j/dx_d + rho'_e
+    r_hat_d / 6).  Rigid rotations keep div(rho u) = 0 exactly: their discrete divergence vanishes
+    per wedge and u_h(q_c) = omega x x(q_c) is orthogonal to r_hat(q_c)."""
     n = mesh.n_nodes
     ids = np.arange(mesh.n_wedges) if wedges is None else np.asarray(wedges)
     nodes = mesh.wedge_nodes(ids)
     grad, V = wedge_geometry(mesh, ids)
     Psi = psi_at_centroids(mesh, Pp, ids)                          # (m, n_p)
-    # D[e, d*n + node_j] = -V_e dN_j/dx_d
+    # D[e, d*n + node_j] = -V_e dN_j/dx_d  (times rho_e, plus the rho' r_hat term with a reference state)
     rows = np.repeat(np.arange(len(ids)), 18)
     cols = (np.arange(3)[None, None, :] * n + nodes[:, :, None]).ravel()
-    vals = (-V[:, None, None] * grad).ravel()
+    if rho is None:
+        vals = (-V[:, None, None] * grad).ravel()
+    else:
+        rho = np.asarray(rho, dtype=np.float64)
+        k = ids % (mesh.n_r - 1)
+        rho_e = 0.5 * (rho[k] + rho[k + 1])
+        drho_e = (rho[k + 1] - rho[k]) / (mesh.radii[k + 1] - mesh.radii[k])
+        xc = mesh.node_xyz(nodes.ravel()).reshape(-1, 6, 3).mean(axis=1)
+        rhat = xc / np.linalg.norm(xc, axis=1)[:, None]
+        term = rho_e[:, None, None] * grad + (drho_e[:, None] * rhat / 6.0)[:, None, :]
+        vals = (-V[:, None, None] * term).ravel()
     D = sp.csr_matrix((vals, (rows, cols)), shape=(len(ids), 3 * n))
     return (Psi.T @ D).tocsr()
 

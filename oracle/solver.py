@@ -22,19 +22,27 @@ from .multigrid import Hierarchy, rotation_basis
 
 
 class StokesSystem:
-    def __init__(self, mesh, eta, bc=(O.FREE, O.FREE), div_term=True, kappa=0.0, quad=1):
+    """With reference profiles rho, alpha (one value per node layer) the system is the TALA one of
+    Sec. 1: the momentum block and its pressure gradient P B^T are unchanged, the constraint is
+    Eq. (mass) with the density-weighted B_rho of ``oracle.operators.assemble_B``, so K is no
+    longer symmetric, and the load is Ra rho alpha T' r_hat."""
+
+    def __init__(self, mesh, eta, bc=(O.FREE, O.FREE), div_term=True, kappa=0.0, quad=1, rho=None, alpha=None):
         self.mesh, self.bc = mesh, bc
+        self.rho, self.alpha = rho, alpha
         self.pmesh = O.pressure_mesh(mesh)
         P = O.boundary_projectors(mesh, bc)
         self.P = P
         Pm = O.projector_matrix(P)
         A = O.constrain_A(O.assemble_A(mesh, eta, div_term, kappa, quad), Pm)
-        B = O.assemble_B(mesh, O.prolongation(mesh, self.pmesh)) @ Pm
+        Pp = O.prolongation(mesh, self.pmesh)
+        BT = (O.assemble_B(mesh, Pp) @ Pm).T
+        B = O.assemble_B(mesh, Pp, rho=rho) @ Pm
         self.nu, self.np_ = 3 * mesh.n_nodes, self.pmesh.n_nodes
-        self.K = sp.bmat([[A, B.T], [B, None]], format="csr")
+        self.K = sp.bmat([[A, BT], [B, None]], format="csr")
 
     def rhs(self, T, Ra):
-        f = buoyancy_rhs(self.mesh, T, Ra, self.P)
+        f = buoyancy_rhs(self.mesh, T, Ra, self.P, rho=self.rho, alpha=self.alpha)
         return np.concatenate([f.ravel(), np.zeros(self.np_)])
 
     def residual(self, b, u, p):

@@ -107,6 +107,7 @@ _SIGS = {
     "tn_prolong": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_restrict": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_buoyancy": ([P, P, ctypes.c_double, PP, P], ctypes.c_int),
+    "tn_set_reference_state": ([P, P, P], ctypes.c_int),
     "tn_mg_default_opts": ([ctypes.POINTER(tn_mg_opts)], ctypes.c_int),
     "tn_mg_setup": ([P, ctypes.c_int, ctypes.POINTER(tn_mg_opts), PP, P], ctypes.c_int),
     "tn_mg_lambda": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -301,6 +302,21 @@ def tn_restrict(mesh, level, fine, coarse, apply_bc=False, stream=None):
 def tn_buoyancy(mesh, T, Ra, f, stream=None):
     pf, _a = _ptrs(f)
     _check(lib().tn_buoyancy(mesh, _ptr(T), Ra, pf, _stream(stream)))
+
+
+def tn_set_reference_state(mesh, rho=None, alpha=None):
+    """TALA reference profiles at the level-0 node radii (host sequences of N_r values); rho=None
+    restores the Boussinesq system."""
+    import numpy as np
+    if rho is None:
+        _check(lib().tn_set_reference_state(mesh, None, None))
+        return
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    a = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+    n = tn_mesh_info(mesh, 0)["n_r"]
+    if r.size != n or (a is not None and a.size != n):
+        raise ValueError(f"reference profiles need {n} values (one per node layer)")
+    _check(lib().tn_set_reference_state(mesh, r.ctypes.data_as(P), None if a is None else a.ctypes.data_as(P)))
 
 
 def tn_mg_default_opts(**kw):

@@ -1,4 +1,5 @@
 // C ABI of the wedge Stokes library: argument checks, mesh hierarchy lifetime, dispatch.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -55,7 +56,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.laydf, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64};
+                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64, L.bw64, L.rhat64, L.rhat32, L.rhatdf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -152,6 +153,28 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
   chk(upload(L.lay64, lay));
   chk(upload(L.lay32, to_f32(lay)));
   chk(upload(L.laydf, to_df(lay)));
+  L.h_lay = lay;
+  {
+    // r_hat(q_c) = sbar / |sbar| of every lateral triangle t = ((d N + i) N + j) 2 + w
+    const int N = L.N, M = N + 1;
+    std::vector<double> rh((size_t)3 * L.n_tri);
+    for (int d = 0; d < 10; ++d)
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+          for (int w = 0; w < 2; ++w) {
+            const int ci[3] = {w ? i + 1 : i, w ? i : i + 1, w ? i + 1 : i};
+            const int cj[3] = {w ? j + 1 : j, w ? j + 1 : j, w ? j : j + 1};
+            double sb[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a)
+              for (int x = 0; x < 3; ++x) sb[x] += L.lat_xyz[(((size_t)d * M + ci[a]) * M + cj[a]) * 3 + x];
+            const double nrm = std::sqrt(sb[0] * sb[0] + sb[1] * sb[1] + sb[2] * sb[2]);
+            const int64_t t = (((int64_t)d * N + i) * N + j) * 2 + w;
+            for (int x = 0; x < 3; ++x) rh[(size_t)x * L.n_tri + t] = sb[x] / nrm;
+          }
+    chk(upload(L.rhat64, rh));
+    chk(upload(L.rhat32, to_f32(rh)));
+    chk(upload(L.rhatdf, to_df(rh)));
+  }
   chk(upload(L.s64, s));
   chk(upload(L.s32, to_f32(s)));
   chk(upload(L.grp_ptr, gptr));
@@ -612,6 +635,49 @@ tn_status tn_restrict(tn_mesh* mesh, int level, tn_prec prec, int ncomp, int app
     e = launch_restrict<float>(F, C, bc_of(mesh), ncomp, apply_bc, (const float* const*)f, (float* const*)c, S(stream));
   else return inval("tn_restrict: unknown precision");
   return e == cudaSuccess ? TN_OK : cuda_fail(e, "tn_restrict");
+}
+
+tn_status tn_set_reference_state(tn_mesh* mesh, const double* rho_host, const double* alpha_host) {
+  if (!mesh) return inval("tn_set_reference_state: NULL mesh");
+  Level& L = mesh->lv[0];
+  const int nr = L.n_r;
+  std::vector<double> rho, alpha(nr, 1.0), bw(nr - 1);
+  if (rho_host) {
+    rho.assign(rho_host, rho_host + nr);
+    if (alpha_host) alpha.assign(alpha_host, alpha_host + nr);
+    for (int k = 0; k < nr; ++k)
+      if (!(rho[k] > 0.0) || !std::isfinite(rho[k]) || !std::isfinite(alpha[k]))
+        return inval("tn_set_reference_state: rho must be positive and finite, alpha finite");
+  }
+  // layer-table slots 10, 11: rho(q_c) and rho'(q_c) / (6 w0) (zero without a reference state)
+  std::vector<double> lay = L.h_lay;
+  for (int k = 0; k + 1 < nr; ++k) {
+    double* t = &lay[(size_t)kLayerStride * k];
+    if (rho_host) {
+      const double w0 = t[0];
+      t[10] = 0.5 * (rho[k] + rho[k + 1]);
+      t[11] = (rho[k + 1] - rho[k]) / (L.radii[k + 1] - L.radii[k]) / (6.0 * w0);
+      bw[k] = (0.5 * (rho[k] + rho[k + 1])) * (0.5 * (alpha[k] + alpha[k + 1]));
+    } else {
+      t[10] = t[11] = 0.0;
+    }
+  }
+  const std::vector<float> l32 = to_f32(lay), ldf = to_df(lay);
+  cudaError_t e = cudaMemcpy(L.lay64, lay.data(), sizeof(double) * lay.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(L.lay32, l32.data(), sizeof(float) * l32.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(L.laydf, ldf.data(), sizeof(float) * ldf.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && rho_host && !L.bw64) e = cudaMalloc((void**)&L.bw64, sizeof(double) * (nr - 1));
+  if (e == cudaSuccess && rho_host)
+    e = cudaMemcpy(L.bw64, bw.data(), sizeof(double) * (nr - 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "tn_set_reference_state");
+  if (!rho_host && L.bw64) {
+    cudaFree(L.bw64);
+    L.bw64 = nullptr;
+  }
+  L.h_lay = lay;
+  L.tala = rho_host ? 1 : 0;
+  mg_invalidate(mesh);  // the Schur deflation vector of the solver depends on B
+  return TN_OK;
 }
 
 tn_status tn_buoyancy(tn_mesh* mesh, const double* T_dev, double Ra, double* const* f, void* stream) {

@@ -74,6 +74,17 @@ struct Level {
   // Weight mask over the node layout: 1 on the canonical copy of every node, 0 on other
   // copies and on padding (Euclidean inner products over unique nodes).
   uint8_t* wmask = nullptr;
+  // TALA reference state (tn_set_reference_state; level 0 only): tala = 1 when set, the layer
+  // tables then carry rho(q_c) in slot 10 and rho'(q_c) / (6 w0) in slot 11; bw64 is the buoyancy
+  // weight rho(q_c) alpha(q_c) per radial cell (n_r - 1 values, nullptr = Boussinesq).
+  int tala = 0;
+  double* bw64 = nullptr;
+  std::vector<double> h_lay;  // host copy of the layer table
+  // Unit radial direction r_hat(q_c) = sbar / |sbar| per lateral triangle, SoA [3][n_tri] (FP64,
+  // FP32 and double-float pairs): the TALA divergence's rho' term.
+  double* rhat64 = nullptr;
+  float* rhat32 = nullptr;
+  float* rhatdf = nullptr;
   double* rad64 = nullptr;  // node radii r_k
   float* rad32 = nullptr;
   double inertia[3][3] = {};  // sum over unique nodes of |x|^2 I - x x^T (rotation Gram matrix)

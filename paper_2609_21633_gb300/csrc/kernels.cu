@@ -609,15 +609,36 @@ struct OpA2 {
 
 // Fine-level divergence: each of the six nodes of a wedge gets -V tr(grad u)(q_c) / 6
 // (pressure test function psi = N_n with N_n(q_c) = 1/6); tr grad u = w0 tr G'.
-template <typename T>
+// RHO (TALA, Eq. mass): -V (rho(q_c) div u_h(q_c) + rho'(q_c) r_hat(q_c) . u_h(q_c)) / 6, the
+// product rule at the quadrature point; the layer table carries rho(q_c) in slot 10 and
+// rho'(q_c) / (6 w0) in slot 11, u_h(q_c) is the sum of the wedge's three corner sums (top + bottom)
+// over 6, so the bracket is w0 (slot 10 tr G' + slot 11 r_hat . sum_a s_a); r_hat(q_c) per lateral
+// triangle comes from the level's table.
+template <typename T, bool RHO = false>
 struct OpDiv {
   static constexpr int NIN = 3, NOUT = 1;
   static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
-  using Col = NoCol;
-  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
+  struct ColR {
+    T rh[2][3];
+  };
+  using Col = typename std::conditional<RHO, ColR, NoCol>::type;
+  const T* rhat = nullptr;  // [3][n_tri] r_hat(q_c) of every lateral triangle (RHO only)
+  int n_tri = 0;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int t0) const {
+    if constexpr (RHO) {
+      ColR c;
+#pragma unroll
+      for (int w = 0; w < 2; ++w)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) c.rh[w][x] = rhat[x * n_tri + t0 + w];
+      return c;
+    } else {
+      return Col{};
+    }
+  }
   __device__ __forceinline__ void cell(const T (&s)[4][3], const T (&dd)[4][3], const T (&Mi)[2][9],
                                        const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
-                                       T (&acct)[4][1], const Col&) const {
+                                       T (&acct)[4][1], const Col& col) const {
     const T r = lc[4], vw6 = lc[7];
     T v[2];
 #pragma unroll
@@ -631,7 +652,17 @@ struct OpDiv {
         lat = c == 0 ? ax * M[0] + ay * M[3] : lat + ax * M[c] + ay * M[3 + c];
         rad = c == 0 ? az * M[6] : rad + az * M[6 + c];
       }
-      v[w] = (vw6 * dM[w]) * (lat + r * rad);
+      T div = lat + r * rad;
+      if constexpr (RHO) {
+        T rs = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T sc = (s[c0][c] + s[c1][c]) + s[c2][c];
+          rs = c == 0 ? col.rh[w][0] * sc : rs + col.rh[w][c] * sc;
+        }
+        div = lc[10] * div + lc[11] * rs;
+      }
+      v[w] = (vw6 * dM[w]) * div;
     }
     const T v01 = v[0] + v[1];
     accb[0][0] = acct[0][0] = v[0];
@@ -1605,8 +1636,8 @@ template <bool HG, typename T>
 struct OpCompute<OpA<dfl, HG>, T> {
   using type = dfl;
 };
-template <typename T>
-struct OpCompute<OpDiv<dfl>, T> {
+template <bool RHO, typename T>
+struct OpCompute<OpDiv<dfl, RHO>, T> {
   using type = dfl;
 };
 template <typename T>
@@ -2201,9 +2232,11 @@ __global__ void k_to_f32(const double* __restrict__ a, float* b, int64_t n) {
 
 // ------------------------------------------------------------------------------------ buoyancy
 // f_j = sum_e V_e Ra T(q_c) r_hat(q_c) / 6 with r_hat(q_c) = sbar / |sbar| (x(q_c) = rho sbar).
+// With a reference state (TALA, Eq. stokes) each radial cell's term carries cellw[k] =
+// rho(q_c) alpha(q_c), and T is the perturbation T'.
 __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double* __restrict__ lay,
                            const double* __restrict__ svec, const double* __restrict__ T, double Ra, int bc_in,
-                           int bc_out, double* f0, double* f1, double* f2) {
+                           int bc_out, const double* __restrict__ cellw, double* f0, double* f1, double* f2) {
   const int N = D.N, M = N + 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (tid >= (int64_t)10 * D.n_r * M * M) return;
@@ -2231,7 +2264,8 @@ __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double*
       for (int a = 0; a < 3; ++a) s += T[b + (int64_t)pi_[a] * D.P + pj_[a]];
       for (int a = 0; a < 3; ++a) s += T[b + D.layer_stride + (int64_t)pi_[a] * D.P + pj_[a]];
       const double V = lay[kLayerStride * kk + 2] * dM;
-      const double wgt = V * Ra * (s / 6.0) / 6.0 / nrm;
+      double wgt = V * Ra * (s / 6.0) / 6.0 / nrm;
+      if (cellw) wgt *= cellw[kk];
       for (int c = 0; c < 3; ++c) f[c] += wgt * sb[c];
     }
   }
@@ -2348,13 +2382,20 @@ cudaError_t launch_div_fine(const Level& L, BC bc, const T* const* u, T* q, cuda
   T* out[1] = {q};
   cudaError_t e = cudaSuccess;
   bool done = false;
+  const int nt = (int)L.n_tri;
   if constexpr (sizeof(T) == 8) {
     if (use_df<T>(L)) {
-      e = launch_tile<T, OpDiv<dfl>, PROJ_IN>(L, bc, OpDiv<dfl>{}, u, out, EtaView<T>{}, st);
+      const dfl* rh = reinterpret_cast<const dfl*>(L.rhatdf);
+      e = L.tala ? launch_tile<T, OpDiv<dfl, true>, PROJ_IN>(L, bc, OpDiv<dfl, true>{rh, nt}, u, out, EtaView<T>{}, st)
+                 : launch_tile<T, OpDiv<dfl>, PROJ_IN>(L, bc, OpDiv<dfl>{}, u, out, EtaView<T>{}, st);
       done = true;
     }
   }
-  if (!done) e = launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, EtaView<T>{}, st);
+  if (!done) {
+    const T* rh = sizeof(T) == 8 ? (const T*)L.rhat64 : (const T*)L.rhat32;
+    e = L.tala ? launch_tile<T, OpDiv<T, true>, PROJ_IN>(L, bc, OpDiv<T, true>{rh, nt}, u, out, EtaView<T>{}, st)
+               : launch_tile<T, OpDiv<T>, PROJ_IN>(L, bc, OpDiv<T>{}, u, out, EtaView<T>{}, st);
+  }
   if (e != cudaSuccess) return e;
   return launch_interface<T>(L, bc, 1, 0, out, nullptr, st);
 }
@@ -2552,7 +2593,8 @@ cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st)
 
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st) {
   const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
-  k_buoyancy<<<nblk(n, 256), 256, 0, st>>>(dims(L), L.geo64, L.lay64, L.s64, T, Ra, bc.in, bc.out, f[0], f[1], f[2]);
+  k_buoyancy<<<nblk(n, 256), 256, 0, st>>>(dims(L), L.geo64, L.lay64, L.s64, T, Ra, bc.in, bc.out, L.bw64, f[0],
+                                           f[1], f[2]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_interface<double>(L, bc, 3, 0, f, nullptr, st);

@@ -127,3 +127,42 @@ def test_config2_solve_residual_checked_by_the_oracle(tn, shell, mode, eta_stora
         assert np.abs(r_u).max() <= RTOL * bnorm and np.abs(r_p).max() <= RTOL * bnorm
     finally:
         tn.tn_mesh_destroy(m)
+
+
+def test_vrms_matches_the_oracle_and_keeps_converging(tn):
+    """First-solve V_rms of the config-0 shell family driven by the lateral temperature perturbation
+    (viscosity from the full T): the GPU FP64 solves at levels 3, 4, 5 reproduce the oracle's stored
+    values (tests/golden/vrms_config0.txt), and level 6, beyond the oracle, continues the
+    second-order self-convergence ((V5 - V4) / (V6 - V5) near 4; Sec. 8 reports V_rms)."""
+    from tests.test_oracle_vrms import golden
+    g = golden()
+    v = {}
+    for level in (3, 4, 5, 6):
+        n_r = 2 ** level + 1
+        om = ShellMesh(level, n_r, R_IN, R_OUT)
+        m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT)
+        try:
+            info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
+            mp = LayoutMap(info, om)
+            xyz = om.node_xyz()
+            T = inputs.temperature(xyz, R_IN, R_OUT)
+            Tp = T - inputs.temperature(xyz, R_IN, R_OUT, amp=0.0)
+            tn.tn_set_temperature(m, torch.tensor(mp.to_layout(T), device="cuda"), math.log(10.0))
+            f = [torch.zeros(info["n_layout"], device="cuda", dtype=torch.float64) for _ in range(3)]
+            tn.tn_buoyancy(m, torch.tensor(mp.to_layout(Tp), device="cuda"), RA, f)
+            u = [torch.zeros_like(f[0]) for _ in range(3)]
+            p = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
+            st = tn.tn_stokes_solve(m, f, None, u, p, tn.tn_solve_default_opts(rtol=1e-10), check=False)
+            assert st["rel_residual"] <= 1e-9, st
+            uo = np.stack([mp.from_layout(t.cpu().numpy()) for t in u])
+            _, V = O.wedge_geometry(om)  # lumped one-point quadrature, as the oracle's v_rms
+            mass = np.bincount(om.wedge_nodes().ravel(), weights=np.repeat(V / 6.0, 6), minlength=om.n_nodes)
+            v[level] = float(np.sqrt(np.sum(mass * np.sum(uo ** 2, axis=0)) / mass.sum()))
+            print(f"level {level}: V_rms {v[level]:.9f} ({st['iterations']} its, residual {st['rel_residual']:.1e})")
+        finally:
+            tn.tn_mesh_destroy(m)
+        if level <= 5:
+            assert abs(v[level] / g[(level, "perturbation")] - 1) <= 1e-7, (level, v[level])
+    ratio = (v[5] - v[4]) / (v[6] - v[5])
+    print(f"(V5 - V4) / (V6 - V5) = {ratio:.3f}, order {np.log2(ratio):.2f}")
+    assert 3.0 <= ratio <= 5.3, ratio
