@@ -373,6 +373,70 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
                           double* const* u_dev, double* p_dev, tn_solve_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Energy equation (Eq. energy) in the nondimensional Boussinesq form of the spherical benchmark
+ * runs (Sec. 8): dT/dt + u . grad T = lap T, on level 0, FP64, node layout.  Space: W1 wedges with
+ * the one-point rule (Sec. 4), lumped mass m_j = sum_e V_e / 6 and the residual
+ *   R_j = sum_e V_e [grad N_j . grad T + N_j(q_c) ubar . grad T + tau_e (ubar . grad N_j)(ubar . grad T)]
+ * (diffusion, Galerkin advection, and with supg the streamline-upwind term of SUPG, Brooks and
+ * Hughes 1982), all at q_c, ubar the mean of the six nodal velocities, tau_e = h / (2 |ubar|)
+ * (coth Pe - 1 / Pe), Pe = |ubar| h / 2, h = (2 V_e)^(1/3).  Time: Heun's method,
+ * T* = T - dt M^-1 R(T), T_new = (T + T* - dt M^-1 R(T*)) / 2, on the interior node layers; the two
+ * surface layers keep their values (prescribed temperatures).  The paper's own schemes (SUPG,
+ * entropy viscosity, MMOC, Sec. 6) are named there without their discrete forms; this is the
+ * library's explicit SUPG reading.  The first energy call on a mesh allocates its workspace
+ * (five layout vectors), kept until tn_mesh_destroy.
+ * ---------------------------------------------------------------------------------------- */
+/* R = (K + C(u) + S(u)) T (u_dev NULL: the diffusion K T only; supg 0 drops S).  T_dev, R_dev: node
+ * layout of level 0, equal values on node copies; R must not alias T.  Stream-ordered. */
+tn_status tn_energy_residual(tn_mesh* mesh, const double* T_dev, const double* const* u_dev, int supg, double* R_dev,
+                             void* stream);
+/* n_steps Heun steps of size dt with the fixed velocity u_dev (NULL: diffusion only), T_dev updated
+ * in place.  Stable for dt <= tn_energy_stable_dt and an advective Courant number below ~1.
+ * Stream-ordered (the first call synchronises once to set up the workspace). */
+tn_status tn_energy_steps(tn_mesh* mesh, double* T_dev, const double* const* u_dev, double dt, int n_steps, int supg,
+                          void* stream);
+/* Diagnostics (synchronous; either output may be NULL): nu_top = the consistent diffusive heat flux
+ * through the outer surface (the residual K T summed over its nodes) divided by the same for the
+ * conductive profile T_c = r_in (r - r_out) / (r (r_in - r_out)); v_rms = sqrt(sum_j m_j |u_j|^2 /
+ * sum_j m_j) over the unique nodes. */
+tn_status tn_energy_diagnostics(tn_mesh* mesh, const double* T_dev, const double* const* u_dev, double* nu_top,
+                                double* v_rms, void* stream);
+/* Largest stable diffusion substep: 1.5 / (1.1 lambda), lambda the largest eigenvalue of M^-1 K on
+ * the interior layers from 30 power iterations (cached per mesh).  Synchronous. */
+tn_status tn_energy_stable_dt(tn_mesh* mesh, double* dt, void* stream);
+
+/* Coupled Stokes-energy time loop: n_steps steps of
+ *   viscosity exp(E (1/2 - T)) from T (tn_set_temperature), Boussinesq load Ra T r_hat (tn_buoyancy),
+ *   Stokes solve to rtol in the given mode (tn_stokes_solve) -> u, p,
+ *   diagnostics of (T, u) (tn_energy_diagnostics), then the energy update over
+ *   dt = cfl h_min / max |u| (h_min the smallest radial or lateral node spacing) in
+ *   ceil(dt / stable substep) Heun substeps; opts.dt > 0 / opts.substeps > 0 fix them instead.
+ * T_dev (in / out) must hold the surface temperatures; u_dev, p_dev receive the last solve.
+ * stats (may be NULL) gets one entry per step.  Synchronous.  Errors of the solve are returned
+ * (TN_ENOTCONVERGED stops the loop after that step's solve). */
+typedef struct {
+  double Ra;         /* Rayleigh number (1e5) */
+  double E;          /* ln(viscosity contrast) of exp(E (1/2 - T)) (ln 100) */
+  double cfl;        /* advective Courant number of a step (0.5) */
+  int supg;          /* streamline-upwind term (1) */
+  int mode;          /* tn_solve_mode of the Stokes solves (TN_SOLVE_MIXED) */
+  double rtol;       /* Stokes relative residual (1e-8) */
+  double dt;         /* > 0: fixed step instead of the CFL step (0) */
+  int substeps;      /* > 0: fixed Heun substeps per step instead of the stability bound (0) */
+} tn_convection_opts;
+typedef struct {
+  double time, dt;          /* model time after the step, step size */
+  int substeps;             /* Heun substeps of the energy update */
+  int stokes_iterations;
+  double rel_residual;      /* of the Stokes solve */
+  double nu_top, v_rms, u_max;   /* diagnostics of the step's (T, u) before the update */
+  double stokes_seconds, energy_seconds;  /* host wall time of the two halves */
+} tn_convection_step_stats;
+tn_status tn_convection_default_opts(tn_convection_opts* opts);
+tn_status tn_convection_steps(tn_mesh* mesh, double* T_dev, double* const* u_dev, double* p_dev, int n_steps,
+                              const tn_convection_opts* opts, tn_convection_step_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Serving: continuous batching of Stokes solves (the paper has no serving layer).
  * tn_server_submit queues a request and returns at once.  max_active worker threads, each
  * with its own stream, take the first queued request that fits the device-memory budget

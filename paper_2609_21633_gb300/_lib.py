@@ -71,6 +71,18 @@ class tn_server_opts(ctypes.Structure):
                 ("hg_kappa", ctypes.c_double), ("radial_quad_points", ctypes.c_int)]
 
 
+class tn_convection_opts(ctypes.Structure):
+    _fields_ = [("Ra", ctypes.c_double), ("E", ctypes.c_double), ("cfl", ctypes.c_double), ("supg", ctypes.c_int),
+                ("mode", ctypes.c_int), ("rtol", ctypes.c_double), ("dt", ctypes.c_double), ("substeps", ctypes.c_int)]
+
+
+class tn_convection_step_stats(ctypes.Structure):
+    _fields_ = [("time", ctypes.c_double), ("dt", ctypes.c_double), ("substeps", ctypes.c_int),
+                ("stokes_iterations", ctypes.c_int), ("rel_residual", ctypes.c_double), ("nu_top", ctypes.c_double),
+                ("v_rms", ctypes.c_double), ("u_max", ctypes.c_double), ("stokes_seconds", ctypes.c_double),
+                ("energy_seconds", ctypes.c_double)]
+
+
 class tn_request(ctypes.Structure):
     _fields_ = [("lateral_level", ctypes.c_int), ("radial_layers", ctypes.c_int), ("r_in", ctypes.c_double),
                 ("r_out", ctypes.c_double), ("E", ctypes.c_double), ("Ra", ctypes.c_double),
@@ -108,6 +120,14 @@ _SIGS = {
     "tn_restrict": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PP, PP, P], ctypes.c_int),
     "tn_buoyancy": ([P, P, ctypes.c_double, PP, P], ctypes.c_int),
     "tn_set_reference_state": ([P, P, P], ctypes.c_int),
+    "tn_energy_residual": ([P, P, PP, ctypes.c_int, P, P], ctypes.c_int),
+    "tn_energy_steps": ([P, P, PP, ctypes.c_double, ctypes.c_int, ctypes.c_int, P], ctypes.c_int),
+    "tn_energy_diagnostics": ([P, P, PP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), P],
+                              ctypes.c_int),
+    "tn_energy_stable_dt": ([P, ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+    "tn_convection_default_opts": ([ctypes.POINTER(tn_convection_opts)], ctypes.c_int),
+    "tn_convection_steps": ([P, P, PP, P, ctypes.c_int, ctypes.POINTER(tn_convection_opts),
+                             ctypes.POINTER(tn_convection_step_stats), P], ctypes.c_int),
     "tn_mg_default_opts": ([ctypes.POINTER(tn_mg_opts)], ctypes.c_int),
     "tn_mg_setup": ([P, ctypes.c_int, ctypes.POINTER(tn_mg_opts), PP, P], ctypes.c_int),
     "tn_mg_lambda": ([P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -317,6 +337,50 @@ def tn_set_reference_state(mesh, rho=None, alpha=None):
     if r.size != n or (a is not None and a.size != n):
         raise ValueError(f"reference profiles need {n} values (one per node layer)")
     _check(lib().tn_set_reference_state(mesh, r.ctypes.data_as(P), None if a is None else a.ctypes.data_as(P)))
+
+
+def tn_energy_residual(mesh, T, u, R, supg=True, stream=None):
+    pu, _a = _ptrs(u) if u is not None else (None, None)
+    _check(lib().tn_energy_residual(mesh, _ptr(T), pu, int(bool(supg)), _ptr(R), _stream(stream)))
+
+
+def tn_energy_steps(mesh, T, u, dt, n_steps, supg=True, stream=None):
+    pu, _a = _ptrs(u) if u is not None else (None, None)
+    _check(lib().tn_energy_steps(mesh, _ptr(T), pu, float(dt), int(n_steps), int(bool(supg)), _stream(stream)))
+
+
+def tn_energy_diagnostics(mesh, T, u, stream=None):
+    """(nu_top, v_rms)"""
+    nu, vr = ctypes.c_double(), ctypes.c_double()
+    pu, _a = _ptrs(u)
+    _check(lib().tn_energy_diagnostics(mesh, _ptr(T), pu, ctypes.byref(nu), ctypes.byref(vr), _stream(stream)))
+    return nu.value, vr.value
+
+
+def tn_energy_stable_dt(mesh, stream=None):
+    out = ctypes.c_double()
+    _check(lib().tn_energy_stable_dt(mesh, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def tn_convection_default_opts(**kw):
+    o = tn_convection_opts()
+    _check(lib().tn_convection_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def tn_convection_steps(mesh, T, u, p, n_steps, opts=None, stream=None, check=True):
+    """Returns the per-step stats as a list of dicts."""
+    o = opts if opts is not None else tn_convection_default_opts()
+    stats = (tn_convection_step_stats * max(1, n_steps))()
+    pu, _a = _ptrs(u)
+    status = lib().tn_convection_steps(mesh, _ptr(T), pu, _ptr(p), int(n_steps), ctypes.byref(o), stats,
+                                       _stream(stream))
+    if status != TN_OK and (check or status != TN_ENOTCONVERGED):
+        _check(status)
+    return [{f: getattr(stats[i], f) for f, _ in tn_convection_step_stats._fields_} for i in range(n_steps)]
 
 
 def tn_mg_default_opts(**kw):

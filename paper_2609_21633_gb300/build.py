@@ -16,7 +16,7 @@ LIBNAME = "libterra_wedge.so"
 # launchers of each quadrature rule apart)
 SOURCES = [("kernels.cu", ["-DTN_PART=1"]), ("kernels.cu", ["-DTN_PART=2"]), ("kernels.cu", ["-DTN_PART=3"]),
            ("kernels.cu", ["-DTN_PART=4"]), ("kernels.cu", ["-DTN_PART=5"]),
-           ("solver.cu", []), ("server.cu", []), ("api.cu", []), ("noalloc.cu", []), ("probe.cu", []), ("mesh.cpp", [])]
+           ("solver.cu", []), ("server.cu", []), ("api.cu", []), ("noalloc.cu", []), ("probe.cu", []), ("energy.cu", []), ("mesh.cpp", [])]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

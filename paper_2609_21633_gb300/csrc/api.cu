@@ -313,6 +313,7 @@ tn_status tn_mesh_destroy(tn_mesh* mesh) {
   mg_free(mesh->mg);
   mesh->mg = nullptr;
   free_step_buffers(mesh);
+  energy_free(mesh);
   for (auto& L : mesh->lv) free_level(L);
   delete mesh;
   return TN_OK;

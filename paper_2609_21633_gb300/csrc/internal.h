@@ -106,6 +106,17 @@ struct MGState;
 void mg_free(MGState*);
 }
 
+namespace tn {
+// Energy-equation workspace of a mesh (level 0): lumped mass, four work vectors, a reduction
+// buffer and the cached largest eigenvalue of M^-1 K (0: not computed); freed by energy_free.
+struct EnergyState {
+  double* mass = nullptr;
+  double* w[4] = {};
+  double* part = nullptr;
+  double lambda = 0;
+};
+}  // namespace tn
+
 struct tn_mesh {
   std::vector<tn::Level> lv;
   tn::MGState* mg = nullptr;
@@ -124,6 +135,7 @@ struct tn_mesh {
   // Cancel flag that tn_stokes_solve polls once per Krylov iteration (set by the server's
   // tn_server_cancel; nullptr: never cancelled).
   std::atomic<int>* cancel = nullptr;
+  tn::EnergyState en;
 };
 
 namespace tn {
@@ -136,6 +148,7 @@ void build_level_host(Level& L, int level, int n_r, double r_in, double r_out, s
                       std::string& err);
 
 void set_error(const std::string& msg);
+void energy_free(tn_mesh* mesh);
 // Tables and device arrays of one level (api.cu); destroy_level frees them.
 tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int eta_storage, int div_term);
 void destroy_level(Level& L);
@@ -204,5 +217,10 @@ int64_t ring_buffer_entries(int N, int n_r);
 // The FP32 path's viscosity from eta64: eta32, or eta16 and the column factors (see Level).
 cudaError_t launch_eta_f32_path(const Level& L, cudaStream_t st);
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st);
+// Energy equation (Eq. energy): residual R = (K + C(u) + S(u)) T (u NULL: diffusion only; supg: the
+// streamline-upwind term) and the lumped mass, FP64, with the interface sum (energy.cu drives them).
+cudaError_t launch_energy_residual(const Level& L, const double* const* u, const double* T, double* R, int supg,
+                                   cudaStream_t st);
+cudaError_t launch_lumped_mass(const Level& L, double* m, cudaStream_t st);
 
 }  // namespace tn

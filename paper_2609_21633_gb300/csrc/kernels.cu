@@ -775,6 +775,93 @@ struct OpDiag {
   }
 };
 
+// Energy residual of Eq. (energy) in the nondimensional Boussinesq form, dT/dt + u . grad T = lap T,
+// one-point rule (inputs u_x, u_y, u_z, T; one output): node j of a wedge receives
+//   grad N_j . F + V a / 6,   F = V (grad T + tau a ubar),   a = ubar . grad T,
+// the diffusion, the Galerkin advection (N_j(q_c) = 1/6) and, with supg, the streamline-upwind term
+// of SUPG (Brooks and Hughes 1982); all at q_c, ubar the mean of the six nodal velocities,
+// tau = h / (2 |ubar|) (coth Pe - 1 / Pe), Pe = |ubar| h / 2, h = (2 V)^(1/3) (the hexahedral cell's
+// volume), with the series h^2 / 12 (1 - Pe^2 / 15) for Pe < 1e-3.  grad T = w0 G with G formed from
+// the corner sums / differences as the strain of OpA, grad N_j = w0 (l_a -/+ r m2) (bottom / top).
+// adv = 0: diffusion only (the inputs' velocity slots are not used).
+template <typename T>
+struct OpEnergy {
+  static constexpr int NIN = 4, NOUT = 1;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
+  using Col = NoCol;
+  int adv, supg;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const T (&s)[4][4], const T (&dd)[4][4], const T (&Mi)[2][9],
+                                       const T (&dM)[2], const T* lc, const T (&)[2], T (&accb)[4][1],
+                                       T (&acct)[4][1], const Col&) const {
+    const T w0 = lc[0], vol = lc[2], r = lc[4];
+    T yb[2][3], yt[2][3];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const T* M = Mi[w];
+      const T ax = s[c1][3] - s[c0][3], ay = s[c2][3] - s[c0][3], az = (dd[c0][3] + dd[c1][3]) + dd[c2][3];
+      T G[3], F[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) G[x] = ax * M[x] + ay * M[3 + x] + az * (r * M[6 + x]);
+      const T V = vol * dM[w];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) F[x] = (V * w0) * G[x];
+      T q = 0;
+      if (adv) {
+        T ub[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) ub[x] = ((s[c0][x] + s[c1][x]) + s[c2][x]) * (T)(1.0 / 6.0);
+        const T a = w0 * ((ub[0] * G[0] + ub[1] * G[1]) + ub[2] * G[2]);
+        q = V * a * (T)(1.0 / 6.0);
+        if (supg) {
+          const T un = sqrt((ub[0] * ub[0] + ub[1] * ub[1]) + ub[2] * ub[2]);
+          const T h = cbrt((T)2 * V);
+          const T pe = un * h * (T)0.5;
+          const T tau = pe > (T)1e-3 ? h / ((T)2 * un) * ((T)1 / tanh(pe) - (T)1 / pe)
+                                     : h * h * (T)(1.0 / 12.0) * ((T)1 - pe * pe * (T)(1.0 / 15.0));
+          const T ta = V * tau * a;
+#pragma unroll
+          for (int x = 0; x < 3; ++x) F[x] += ta * ub[x];
+        }
+      }
+      const T p0 = (M[0] * F[0] + M[1] * F[1]) + M[2] * F[2];
+      const T p1 = (M[3] * F[0] + M[4] * F[1]) + M[5] * F[2];
+      const T p2 = r * ((M[6] * F[0] + M[7] * F[1]) + M[8] * F[2]);
+      const T lat[3] = {-(p0 + p1), p0, p1};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        yb[w][a] = w0 * (lat[a] - p2) + q;
+        yt[w][a] = w0 * (lat[a] + p2) + q;
+      }
+    }
+    // corners: 00 <- W0 node 0; 11 <- W1 node 0; 10 <- W0 node 1 + W1 node 2; 01 <- W0 node 2 + W1 node 1
+    accb[0][0] = yb[0][0], acct[0][0] = yt[0][0];
+    accb[3][0] = yb[1][0], acct[3][0] = yt[1][0];
+    accb[1][0] = yb[0][1] + yb[1][2], acct[1][0] = yt[0][1] + yt[1][2];
+    accb[2][0] = yb[0][2] + yb[1][1], acct[2][0] = yt[0][2] + yt[1][1];
+  }
+};
+
+// Lumped mass m_j = sum_e V_e / 6 (no input).
+template <typename T>
+struct OpMass {
+  static constexpr int NIN = 1, NOUT = 1;
+  static constexpr bool USES_ETA = false, LOADS = false, NEEDS_D = false;
+  using Col = NoCol;
+  __device__ __forceinline__ Col column(const T (&)[2][9], const T (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const T (&)[4][1], const T (&)[4][1], const T (&)[2][9], const T (&dM)[2],
+                                       const T* lc, const T (&)[2], T (&accb)[4][1], T (&acct)[4][1],
+                                       const Col&) const {
+    const T v0 = lc[2] * dM[0] * (T)(1.0 / 6.0), v1 = lc[2] * dM[1] * (T)(1.0 / 6.0);
+    const T v01 = v0 + v1;
+    accb[0][0] = acct[0][0] = v0;
+    accb[3][0] = acct[3][0] = v1;
+    accb[1][0] = acct[1][0] = v01;
+    accb[2][0] = acct[2][0] = v01;
+  }
+};
+
 // Diagonal in gradient form (the FP32 path, where the table loads cost more than the arithmetic
 // they save): node (a, side) of a wedge gets ve (|g|^2 + c g_d^2) with g = l_a w0 -/+ w1 m2
 // formed per cell, plus the hourglass term of OpDiag.
@@ -959,10 +1046,10 @@ __device__ __forceinline__ void epilogue(const EpiArgs<T>& E, const T* in0, cons
 // A CTA owns TI x TJ lateral node columns and computes the (TI + 1) x (TJ + 1) cells touching them.
 #define TN_TILE_PARAMS                                                                                          \
   Dims D, Op op, const T *__restrict__ in0, const T *__restrict__ in1, const T *__restrict__ in2,             \
-      T *__restrict__ out0, T *__restrict__ out1, T *__restrict__ out2, const T *__restrict__ geo,             \
+      const T *__restrict__ in3, T *__restrict__ out0, T *__restrict__ out1, T *__restrict__ out2, const T *__restrict__ geo,             \
       const T *__restrict__ lay, EtaView<T> eta, const T *__restrict__ svec, int bc_in, int bc_out, int kc,    \
       const int *__restrict__ skip, EpiArgs<T> E
-#define TN_TILE_ARGS D, op, in0, in1, in2, out0, out1, out2, geo, lay, eta, svec, bc_in, bc_out, kc, skip, E
+#define TN_TILE_ARGS D, op, in0, in1, in2, in3, out0, out1, out2, geo, lay, eta, svec, bc_in, bc_out, kc, skip, E
 // Shared memory of a tile: NS per-node values (corner sums s and, for ops that need them,
 // differences d of the input, per component) on the (TI + 2) x (TJ + 2) nodes the cells touch,
 // then corners 10, 01, 11 of every cell's output contributions.
@@ -1043,11 +1130,12 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
     v[0] = in0[o];
     if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
     if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
+    if (NIN > 3) v[NIN > 3 ? 3 : 0] = in3[o];
     if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
       T vv[3] = {v[0], v[NIN > 1 ? 1 : 0], v[NIN > 2 ? 2 : 0]};
       project_vec(vv, svec, (int64_t)lat, (int64_t)NLL, k == 0 ? bc_in : bc_out);
 #pragma unroll
-      for (int c = 0; c < NIN; ++c) v[c] = vv[c];
+      for (int c = 0; c < (NIN < 3 ? NIN : 3); ++c) v[c] = vv[c];
     }
   };
   // corner sums / differences of one node between layers k and k+1 into sd slot (i, j)
@@ -1144,6 +1232,7 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
       v[q][0] = in0[o + cdel[q]];
       if (NIN > 1) v[q][NIN > 1 ? 1 : 0] = in1[o + cdel[q]];
       if (NIN > 2) v[q][NIN > 2 ? 2 : 0] = in2[o + cdel[q]];
+      if (NIN > 3) v[q][NIN > 3 ? 3 : 0] = in3[o + cdel[q]];
     }
     if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
       const int bc = k == 0 ? bc_in : bc_out;
@@ -1152,7 +1241,7 @@ __device__ __forceinline__ void tile_body(TN_TILE_PARAMS) {
         T vv[3] = {v[q][0], v[q][NIN > 1 ? 1 : 0], v[q][NIN > 2 ? 2 : 0]};
         project_vec(vv, svec, (int64_t)(lat00 + cdel[q]), (int64_t)NLL, bc);
 #pragma unroll
-        for (int c = 0; c < NIN; ++c) v[q][c] = vv[c];
+        for (int c = 0; c < (NIN < 3 ? NIN : 3); ++c) v[q][c] = vv[c];
       }
     }
   };
@@ -1374,11 +1463,12 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     v[0] = in0[o];
     if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
     if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
+    if (NIN > 3) v[NIN > 3 ? 3 : 0] = in3[o];
     if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
       T vv[3] = {v[0], v[NIN > 1 ? 1 : 0], v[NIN > 2 ? 2 : 0]};
       project_vec(vv, svec, (int64_t)lat, (int64_t)NLL, k == 0 ? bc_in : bc_out);
 #pragma unroll
-      for (int c = 0; c < NIN; ++c) v[c] = vv[c];
+      for (int c = 0; c < (NIN < 3 ? NIN : 3); ++c) v[c] = vv[c];
     }
 #pragma unroll
     for (int c = 0; c < NIN; ++c) vc[c] = to_compute<C>(v[c]);
@@ -1675,6 +1765,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   dim3 grid(ntiles, (ncells + kc - 1) / kc, 10);
   const T* i1 = Op::NIN > 1 ? in[1] : in[0];
   const T* i2 = Op::NIN > 2 ? in[2] : in[0];
+  const T* i3 = Op::NIN > 3 ? in[3] : in[0];
   T* o1 = Op::NOUT > 1 ? out[1] : out[0];
   T* o2 = Op::NOUT > 2 ? out[2] : out[0];
   const T* sv = Tab<T>::s(L);
@@ -1684,7 +1775,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
   // from prepare_tile_kernels() when the first mesh was created
 #define TN_TILE_LAUNCH(KERNEL, TIv, TJv, EKv)                                                                   \
   KERNEL<T, Op, TIv, TJv, FLAGS, EPI, EKv><<<grid, (TIv + 1) * (TJv + 1), TileSmem<T, Op, TIv, TJv>::bytes, st>>>( \
-      D, op, in[0], i1, i2, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E)
+      D, op, in[0], i1, i2, i3, out[0], o1, o2, geo, lay, eta, sv, bc.in, bc.out, kc, skip, E)
   // 16-bit viscosity (FP32 path only): only full tiles (levels with N >= 16 store it)
   if constexpr (Op::USES_ETA && sizeof(T) == 4) {
     if (eta.kind != TN_ETA_F32) {
@@ -1705,7 +1796,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
       // the layer table in the compute type: the level's double-float copy for dfl ops
       const T* layk = kDF ? reinterpret_cast<const T*>(L.laydf) : lay;
       k_tile_hf<T, Op, TI, TJ, FLAGS, EPI, TN_ETA_F32, C><<<grid, TI * TJ, TileSmemHF<C, Op, TI, TJ>::bytes, st>>>(
-          D, op, in[0], i1, i2, out[0], o1, o2, geo, layk, eta, sv, bc.in, bc.out, kc, skip, E, (T*)L.ring64);
+          D, op, in[0], i1, i2, i3, out[0], o1, o2, geo, layk, eta, sv, bc.in, bc.out, kc, skip, E, (T*)L.ring64);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       const RingDims RD = ring_dims(L.N, TI, TJ);
@@ -2671,10 +2762,41 @@ cudaError_t set_df_attrs() {
 #if TN_PART == 0 || TN_PART == 2
 TN_INST_A(double)
 
+// Energy residual (Eq. energy) and lumped mass on level L, FP64: R = (K + C(u) + S(u)) T with the
+// element op OpEnergy (u NULL: diffusion only), plus the interface sum over diamond-edge copies.
+// Defined in this part, beside the shared-memory opt-in of its tile kernel.
+cudaError_t launch_energy_residual(const Level& L, const double* const* u, const double* T, double* R, int supg,
+                                   cudaStream_t st) {
+  const double* in[4] = {u ? u[0] : T, u ? u[1] : T, u ? u[2] : T, T};
+  double* out[1] = {R};
+  const BC bc{TN_BC_FREESLIP, TN_BC_FREESLIP};  // no projection flags: the boundary conditions do not enter R
+  cudaError_t e = launch_tile<double, OpEnergy<double>, 0>(L, bc, OpEnergy<double>{u ? 1 : 0, supg}, in, out,
+                                                           EtaView<double>{}, st);
+  if (e != cudaSuccess) return e;
+  return launch_interface<double>(L, bc, 1, 0, out, nullptr, st);
+}
+
+cudaError_t launch_lumped_mass(const Level& L, double* m, cudaStream_t st) {
+  const double* none[1] = {m};
+  double* out[1] = {m};
+  const BC bc{TN_BC_FREESLIP, TN_BC_FREESLIP};
+  cudaError_t e = launch_tile<double, OpMass<double>, 0>(L, bc, OpMass<double>{}, none, out, EtaView<double>{}, st);
+  if (e != cudaSuccess) return e;
+  return launch_interface<double>(L, bc, 1, 0, out, nullptr, st);
+}
+
+cudaError_t prepare_energy_kernels() {
+  constexpr size_t sh = TileSmemHF<double, OpEnergy<double>, TILE, 2 * TILE>::bytes;
+  if (sh > 48 * 1024)
+    return cudaFuncSetAttribute(k_tile_hf<double, OpEnergy<double>, TILE, 2 * TILE, 0, EPI_NONE, TN_ETA_F32, double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+  return cudaSuccess;
+}
+
 cudaError_t prepare_tile_kernels() {
-  const cudaError_t e[5] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
+  const cudaError_t e[6] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
                             set_df_attrs<OpA<dfl, false>>(), set_df_attrs<OpA<dfl, true>>(),
-                            prepare_tile_kernels_q2()};
+                            prepare_tile_kernels_q2(), prepare_energy_kernels()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
