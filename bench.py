@@ -83,6 +83,10 @@ def parse():
                     help="requests of the seeded serving stream measured after the solves (the full stream is 256)")
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=50,
                     help="steps of the end-to-end run through tn_operator_steps_host")
+    ap.add_argument("--convection", action="store_true",
+                    help="instead of the operator step: the coupled Stokes-energy run of the largest single-GPU "
+                         "shell (--level/--n_r, default level 8, 257 layers; --conv-steps steps)")
+    ap.add_argument("--conv-steps", dest="conv_steps", type=int, default=10)
     ap.add_argument("--largest-shell", dest="largest_shell", action="store_true",
                     help="instead of the operator step: one Stokes solve on the largest single-GPU shell "
                          "(level 8, 257 layers) and its resident device memory")
@@ -324,19 +328,22 @@ def solve_case(tn, torch, dev, level, n_r, E, Ra, mode, eta_storage=0, hg_kappa=
         tn.tn_mesh_destroy(m)
 
 
-def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1, mode=None):
+def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1, mode=None, repeated=False,
+                   max_batch=1):
     """Serving workload: seeded Stokes requests (lateral level U{3..6}, radial layers U{9,17,33,65},
     viscosity contrast log-uniform in [1, 1e4], temperature perturbation degree U{2..8}, order
     U{0..l}, amplitude U[0.01, 0.05], Ra = 7e3), solved to 1e-8 by FP64 FGMRES with the FP32
     preconditioner (mode, default TN_SOLVE_F64_PREC32), hourglass control kappa = hg_kappa,
     FP32-path viscosity storage eta_storage (1 = BF16).
     Phase 1 submits all requests at once (saturated throughput); phase 2 submits them with
-    Poisson arrivals at `load` x the saturated rate and reports latency percentiles."""
+    Poisson arrivals at `load` x the saturated rate and reports latency percentiles.
+    repeated: shapes from four only (lateral level U{4, 5}, radial layers U{17, 33}), the stream on
+    which same-shape requests meet; max_batch: the server's lockstep batch size."""
     rng = np.random.default_rng(seed)
     reqs = []
     for _ in range(n_req):
-        l = int(rng.integers(3, 7))
-        nr = int(rng.choice([9, 17, 33, 65]))
+        l = int(rng.integers(4, 6)) if repeated else int(rng.integers(3, 7))
+        nr = int(rng.choice([17, 33])) if repeated else int(rng.choice([9, 17, 33, 65]))
         contrast = 10.0 ** rng.uniform(0.0, 4.0)
         deg = int(rng.integers(2, 9))
         order = int(rng.integers(0, deg + 1))
@@ -345,7 +352,7 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1,
                          t_order=order, t_amplitude=amp))
     mode = tn.TN_SOLVE_F64_PREC32 if mode is None else mode
     srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=4, hg_kappa=hg_kappa, eta_storage=eta_storage,
-                                                        mode=mode))
+                                                        mode=mode, max_batch=max_batch))
     try:
         tickets = [tn.tn_server_submit(srv, **q) for q in reqs]
         res = [tn.tn_server_wait(srv, t) for t in tickets]
@@ -367,7 +374,10 @@ def serving_stream(tn, n_req=256, seed=0, load=0.7, hg_kappa=0.3, eta_storage=1,
         span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
         ok = sum(1 for r in res if r["status"] == tn.TN_OK)
         its = [r["iterations"] for r in res]
-        return {"requests": n_req, "stream": "first %d of the seeded 256-request stream" % n_req,
+        batched = [r["batch"] for r in res]
+        return {"requests": n_req, "stream": ("seeded %d-request stream of four shapes (level 4-5, 17 or 33 layers)"
+                                              % n_req) if repeated else "first %d of the seeded 256-request stream" % n_req,
+                "max_batch": max_batch, "mean_batch": float(np.mean([b if b > 0 else 1 for b in batched])),
                 "saturated_solves_per_s": sat, "saturated_converged": ok_sat,
                 "poisson_rate_per_s": rate, "solves_per_s": n_req / span, "p50_latency_s": float(np.percentile(lat, 50)),
                 "p99_latency_s": float(np.percentile(lat, 99)), "converged": ok,
@@ -406,10 +416,47 @@ def largest_shell(tn, torch, repeats=2):
     return out
 
 
+def convection_run(tn, torch, level, n_r, steps):
+    """Coupled run (Eq. energy with the Stokes solve each step): Ra = 1e5, viscosity contrast 1e2
+    (exp(ln 100 (1/2 - T))), free-slip, T = conductive profile + 0.01 cos(2 phi) P_3^2 perturbation,
+    surfaces held at 1 and 0; Stokes in FP32 inner solves with FP64 refinement to 1e-8, hourglass
+    control kappa = 0.3 and BF16 viscosity; energy by explicit SUPG / Heun substeps at CFL 0.5.
+    Reports every step (Nu_top, V_rms, dt, substeps, solve iterations, times) and device memory."""
+    free0, total = torch.cuda.mem_get_info()
+    t0 = time.perf_counter()
+    m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, hg_kappa=HG_KAPPA, eta_storage=tn.TN_ETA_BF16)
+    try:
+        info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
+        T = torch.tensor(layout_temperature(tn, m), device="cuda")
+        u = [torch.zeros(info["n_layout"], device="cuda", dtype=torch.float64) for _ in range(3)]
+        p = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
+        opts = tn.tn_convection_default_opts(Ra=1e5, E=math.log(100.0), mode=tn.TN_SOLVE_MIXED)
+        stats = tn.tn_convection_steps(m, T, u, p, steps, opts, check=False)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        return {"workload": f"coupled Stokes-energy run, shell l={level} (N={2 ** level}), {n_r} radial layers, "
+                            "Ra=1e5, viscosity contrast 1e2", "velocity_dofs": dof_counts(level, n_r)[0],
+                "pressure_dofs": dof_counts(level, n_r)[1], "temperature_dofs": (10 * 4 ** level + 2) * n_r,
+                "steps": stats, "seconds_total": time.perf_counter() - t0,
+                "resident_gb": (free0 - free1) / 1e9, "device_memory_gb": total / 1e9,
+                "stokes": "FP32 inner FGMRES / V-cycle, FP64 refinement to 1e-8, kappa 0.3, BF16 viscosity",
+                "energy": "one-point W1 SUPG residual, lumped mass, Heun substeps, CFL 0.5"}
+    finally:
+        tn.tn_mesh_destroy(m)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.convection:
+        import torch
+        import paper_2609_21633_gb300 as tn
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        level = args.level if args.level != 7 else 8
+        n_r = args.n_r if args.n_r != 129 else 257
+        print(json.dumps(convection_run(tn, torch, level, n_r, args.conv_steps)))
+        return 0
     if args.largest_shell:
         import torch
         import paper_2609_21633_gb300 as tn
@@ -628,6 +675,10 @@ def main():
             line["solves"] = solves
             if args.serve_requests > 0:
                 line["serving"] = serving_stream(tn, args.serve_requests, args.seed, hg_kappa=HG_KAPPA)
+                # a stream whose shapes repeat, without and with lockstep batching of same-shape requests
+                line["serving_repeated_shapes"] = {
+                    "max_batch_1": serving_stream(tn, 96, args.seed + 1, hg_kappa=HG_KAPPA, repeated=True, max_batch=1),
+                    "max_batch_4": serving_stream(tn, 96, args.seed + 1, hg_kappa=HG_KAPPA, repeated=True, max_batch=4)}
         if world == 1:
             cores = os.cpu_count() or 1
             dtp, ndp, descp = oracle_step_sample_parallel(args.level, args.n_r, 2, args.seed, cores)

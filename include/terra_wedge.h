@@ -372,6 +372,22 @@ tn_status tn_solve_default_opts(tn_solve_opts* opts);
 tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f_dev, const double* g_dev,
                           double* const* u_dev, double* p_dev, tn_solve_stats* stats, void* stream);
 
+/* n independent Stokes solves (1 <= n <= 64, n distinct meshes) advanced in lockstep on one stream:
+ * each round enqueues, for every unconverged system, its restart residual or one FGMRES iteration;
+ * the V-cycles of all iterating systems run from ONE CUDA graph launch (each system's captured
+ * V-cycle a child graph; they run concurrently), then one host synchronisation serves every system.
+ * A system leaves the rounds when it converges, breaks down, stalls or is cancelled (its mask bit
+ * clears; one combined graph is instantiated per subset of systems that iterate together).  Per
+ * system the kernels, their order and the host arithmetic are those of tn_stokes_solve, so each
+ * result is bitwise the same as solved alone.  f_dev[i][3], g_dev[i] (g_dev or g_dev[i] may be
+ * NULL), u_dev[i][3], p_dev[i], stats[i] (may be NULL) and status[i] (the system's tn_stokes_solve
+ * status) per system.  Modes TN_SOLVE_F64 and TN_SOLVE_F64_PREC32 (TN_SOLVE_MIXED: TN_EINVAL).
+ * Synchronous.  Returns TN_OK or the first non-OK system status. */
+tn_status tn_stokes_solve_batch(tn_mesh* const* meshes, int n, const tn_solve_opts* opts,
+                                const double* const* const* f_dev, const double* const* g_dev,
+                                double* const* const* u_dev, double* const* p_dev, tn_solve_stats* stats,
+                                tn_status* status, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Energy equation (Eq. energy) in the nondimensional Boussinesq form of the spherical benchmark
  * runs (Sec. 8): dT/dt + u . grad T = lap T, on level 0, FP64, node layout.  Space: W1 wedges with
@@ -460,6 +476,10 @@ typedef struct {
   int eta_storage;         /* tn_mesh_opts.eta_storage of every request's mesh (TN_ETA_F32) */
   double hg_kappa;         /* tn_mesh_opts.hg_kappa of every request's mesh (0: the plain one-point A) */
   int radial_quad_points;  /* tn_mesh_opts.radial_quad_points of every request's mesh (1) */
+  int max_batch;           /* 1..64 (1): a worker that takes a request also takes up to max_batch - 1
+                            * queued requests of the same shape (as far as the memory budget admits)
+                            * and solves them in lockstep with tn_stokes_solve_batch (modes TN_SOLVE_F64
+                            * and TN_SOLVE_F64_PREC32; TN_SOLVE_MIXED solves them one after another) */
 } tn_server_opts;
 typedef struct {
   int lateral_level, radial_layers;
@@ -475,6 +495,7 @@ typedef struct {
   int iterations, refinements;
   double rel_residual;
   double t_submit, t_start, t_end;  /* seconds since tn_server_create (host clock) */
+  int batch;               /* systems in the lockstep batch that solved it (0: solved alone) */
 } tn_result;
 
 tn_status tn_server_default_opts(tn_server_opts* opts);

@@ -68,7 +68,7 @@ TN_SOLVE_F64, TN_SOLVE_MIXED, TN_SOLVE_F64_PREC32 = 0, 1, 2
 class tn_server_opts(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("mode", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("keep_solutions", ctypes.c_int), ("eta_storage", ctypes.c_int),
-                ("hg_kappa", ctypes.c_double), ("radial_quad_points", ctypes.c_int)]
+                ("hg_kappa", ctypes.c_double), ("radial_quad_points", ctypes.c_int), ("max_batch", ctypes.c_int)]
 
 
 class tn_convection_opts(ctypes.Structure):
@@ -92,7 +92,7 @@ class tn_request(ctypes.Structure):
 class tn_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double), ("t_submit", ctypes.c_double),
-                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 _lib = None
@@ -135,6 +135,8 @@ _SIGS = {
     "tn_solve_default_opts": ([ctypes.POINTER(tn_solve_opts)], ctypes.c_int),
     "tn_stokes_solve": ([P, ctypes.POINTER(tn_solve_opts), PP, P, PP, P, ctypes.POINTER(tn_solve_stats), P],
                         ctypes.c_int),
+    "tn_stokes_solve_batch": ([PP, ctypes.c_int, ctypes.POINTER(tn_solve_opts), PP, PP, PP, PP,
+                               ctypes.POINTER(tn_solve_stats), ctypes.POINTER(ctypes.c_int), P], ctypes.c_int),
     "tn_server_default_opts": ([ctypes.POINTER(tn_server_opts)], ctypes.c_int),
     "tn_server_create": ([ctypes.POINTER(tn_server_opts), ctypes.POINTER(P)], ctypes.c_int),
     "tn_server_submit": ([P, ctypes.POINTER(tn_request), ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
@@ -432,6 +434,31 @@ def tn_stokes_solve(mesh, f, g, u, p, opts=None, stream=None, check=True):
     if status != TN_OK and (check or status != TN_ENOTCONVERGED):
         _check(status)
     return {f: getattr(st, f) for f, _ in tn_solve_stats._fields_}
+
+
+def tn_stokes_solve_batch(meshes, f, u, p, opts=None, stream=None):
+    """Lockstep solve of len(meshes) systems; f[i], u[i]: 3 tensors, p[i]: one.  Returns a list of
+    (status, stats dict) per system."""
+    n = len(meshes)
+    o = opts if opts is not None else tn_solve_default_opts()
+    st = (tn_solve_stats * n)()
+    status = (ctypes.c_int * n)()
+    keep = []
+    fa = (ctypes.c_void_p * n)()
+    ua = (ctypes.c_void_p * n)()
+    for i in range(n):
+        pf, a = _ptrs(f[i])
+        pu, b = _ptrs(u[i])
+        keep += [a, b]
+        fa[i] = ctypes.cast(pf, ctypes.c_void_p)
+        ua[i] = ctypes.cast(pu, ctypes.c_void_p)
+    ma = (ctypes.c_void_p * n)(*[ctypes.cast(m, ctypes.c_void_p) for m in meshes])
+    pa = (ctypes.c_void_p * n)(*[t.data_ptr() for t in p])
+    s = lib().tn_stokes_solve_batch(ctypes.cast(ma, PP), n, ctypes.byref(o), ctypes.cast(fa, PP), None,
+                                    ctypes.cast(ua, PP), ctypes.cast(pa, PP), st, status, _stream(stream))
+    if s == TN_EINVAL:
+        _check(s)
+    return [(status[i], {k: getattr(st[i], k) for k, _ in tn_solve_stats._fields_}) for i in range(n)]
 
 
 def _result(r):

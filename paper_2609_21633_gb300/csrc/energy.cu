@@ -40,12 +40,13 @@ __global__ void k_heun(int stage, Dims D, int64_t n, const double* __restrict__ 
   out[idx] = stage == 1 ? T[idx] - step : 0.5 * ((T[idx] + T1[idx]) - step);
 }
 
-// v_out = M^-1 K v on the interior layers, 0 on the surface layers and padding
-__global__ void k_minv(Dims D, int64_t n, const double* __restrict__ R, const double* __restrict__ m, double* out) {
+// out = scale M^-1 R on the interior layers, 0 on the surface layers and padding
+__global__ void k_minv(Dims D, int64_t n, const double* __restrict__ R, const double* __restrict__ m, double scale,
+                       double* out) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (idx >= n) return;
   const int k = layer_of(idx, D);
-  out[idx] = (k == 0 || k == D.n_r - 1 || !(m[idx] > 0.0)) ? 0.0 : R[idx] / m[idx];
+  out[idx] = (k == 0 || k == D.n_r - 1 || !(m[idx] > 0.0)) ? 0.0 : scale * R[idx] / m[idx];
 }
 
 // conductive profile T_c(r_k) = r_in (r_k - r_out) / (r_k (r_in - r_out)) at every node (padding 0)
@@ -156,7 +157,8 @@ cudaError_t ensure_energy(tn_mesh* mesh, cudaStream_t st) {
   return cudaSuccess;
 }
 
-// largest eigenvalue of M^-1 K on the interior layers (power iteration, 30 steps)
+// largest eigenvalue of M^-1 K on the interior layers: power iteration, 30 steps, the iterate
+// normalised every step (w = M^-1 K v / |v|, so |w| is the estimate and the values stay near lambda)
 cudaError_t diffusion_lambda(tn_mesh* mesh, cudaStream_t st, double* lam) {
   EnergyState& S = mesh->en;
   if (S.lambda > 0) {
@@ -174,20 +176,22 @@ cudaError_t diffusion_lambda(tn_mesh* mesh, cudaStream_t st, double* lam) {
   double nv = 0, est = 0;
   if (e == cudaSuccess) e = reduce(red, 3, L, -1, v, nullptr, nullptr, nullptr, &nv, nullptr, st);
   for (int it = 0; it < 30 && e == cudaSuccess; ++it) {
+    if (!(nv > 0) || !std::isfinite(nv)) break;
     e = launch_energy_residual(L, nullptr, v, w, 0, st);
     if (e == cudaSuccess) {
-      k_minv<<<nb(L.n_layout), 256, 0, st>>>(D, L.n_layout, w, S.mass, w);
+      k_minv<<<nb(L.n_layout), 256, 0, st>>>(D, L.n_layout, w, S.mass, 1.0 / std::sqrt(nv), w);
       e = cudaGetLastError();
     }
     double nw = 0;
     if (e == cudaSuccess) e = reduce(red, 3, L, -1, w, nullptr, nullptr, nullptr, &nw, nullptr, st);
-    if (e != cudaSuccess || !(nw > 0) || !(nv > 0)) break;
-    est = std::sqrt(nw / nv);
+    if (e != cudaSuccess || !(nw > 0) || !std::isfinite(nw)) break;
+    est = std::sqrt(nw);
     std::swap(v, w);
     nv = nw;
   }
   if (e != cudaSuccess) return e;
-  S.lambda = est > 0 ? est : 1.0;
+  if (!(est > 0) || !std::isfinite(est)) return cudaErrorUnknown;  // no usable estimate: refuse to step
+  S.lambda = est;
   *lam = S.lambda;
   return cudaSuccess;
 }
@@ -398,8 +402,14 @@ tn_status tn_convection_steps(tn_mesh* mesh, double* T_dev, double* const* u_dev
     double dt = o.dt > 0 ? o.dt : (umax > 0 ? o.cfl * h / umax : 1.5 / (1.1 * lam));
     int nsub = o.substeps > 0 ? o.substeps : std::max(1, (int)std::ceil(dt * 1.1 * lam / 1.5));
     e = heun_steps(mesh, T_dev, (const double* const*)u_dev, dt / nsub, nsub, o.supg ? 1 : 0, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    double tmax = 0;
+    if (e == cudaSuccess) e = reduce(red, 2, L, -1, T_dev, T_dev, T_dev, nullptr, &tmax, nullptr, st);
     if (e != cudaSuccess) break;
+    if (!std::isfinite(tmax)) {
+      set_error("tn_convection_steps: the temperature is no longer finite after step " + std::to_string(s));
+      status = TN_ENOTCONVERGED;
+      break;
+    }
     const auto t2 = std::chrono::steady_clock::now();
     time += dt;
     if (stats) {

@@ -167,77 +167,121 @@ int acquire_locked(tn_server* S, const Shape& s, tn_mesh** out, std::vector<tn_m
   return 1;
 }
 
-void run_job(tn_server* S, Job* J, tn_mesh* mesh, cudaStream_t st) {
-  const tn_request& R = J->req;
+// One request's device state between its set-up and its bookkeeping.
+struct JobRun {
+  Job* J = nullptr;
+  tn_mesh* mesh = nullptr;
+  double *T = nullptr, *f[3] = {nullptr, nullptr, nullptr}, *u[3] = {nullptr, nullptr, nullptr}, *p = nullptr;
   tn_status s = TN_OK;
-  if (!mesh) {
+};
+
+// Mesh (created if none is resident), vectors from the stream-ordered pool, temperature, viscosity
+// and buoyancy, all enqueued on st.
+void prepare_job(tn_server* S, JobRun& R, cudaStream_t st) {
+  const tn_request& Q = R.J->req;
+  if (!R.mesh) {
     tn_mesh_opts mo = {TN_BC_FREESLIP, TN_BC_FREESLIP, 1, 0, S->opts.eta_storage, S->opts.hg_kappa,
                        S->opts.radial_quad_points};
-    s = tn_mesh_create(R.lateral_level, R.radial_layers, R.r_in, R.r_out, &mo, &mesh);
-  }
-  J->res.status = s;
-  if (s != TN_OK) {
-    mesh = nullptr;
-  } else {
-    const Level& L0 = mesh->lv[0];
-    const Level& L1 = mesh->lv[1];
-    double *T = nullptr, *f[3] = {nullptr, nullptr, nullptr}, *u[3] = {nullptr, nullptr, nullptr}, *p = nullptr;
-    // per-request vectors come from the stream-ordered pool (no device-wide synchronisation)
-    cudaError_t e = cudaMallocAsync((void**)&T, sizeof(double) * L0.n_layout, st);
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&f[c], sizeof(double) * L0.n_layout, st);
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&u[c], sizeof(double) * L0.n_layout, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&p, sizeof(double) * L1.n_layout, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(T, 0, sizeof(double) * L0.n_layout, st);
-    for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMemsetAsync(f[c], 0, sizeof(double) * L0.n_layout, st);
-    if (e == cudaSuccess) {
-      const int64_t n = (int64_t)10 * L0.n_r * (L0.N + 1) * (L0.N + 1);
-      const double amp = R.t_amplitude / pmax_of(R.t_degree, R.t_order);
-      k_temperature<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dims(L0), L0.s64, L0.rad64, R.r_in, R.r_out,
-                                                                  R.t_degree, R.t_order, amp, T);
-      e = cudaGetLastError();
+    R.s = tn_mesh_create(Q.lateral_level, Q.radial_layers, Q.r_in, Q.r_out, &mo, &R.mesh);
+    if (R.s != TN_OK) {
+      R.mesh = nullptr;
+      return;
     }
-    if (e != cudaSuccess) {
-      s = TN_ECUDA;
-    } else {
-      tn_visc_law law{R.E, 0.0, 1.0};
-      s = tn_set_temperature(mesh, T, &law, st);
-      if (s == TN_OK) s = tn_buoyancy(mesh, T, R.Ra, f, st);
-      tn_solve_opts so;
-      tn_solve_default_opts(&so);
-      so.mode = S->opts.mode;
-      so.rtol = S->opts.rtol;
-      tn_solve_stats stats{};
-      if (s == TN_OK) {
-        mesh->cancel = &J->cancel;
-        s = tn_stokes_solve(mesh, &so, (const double* const*)f, nullptr, u, p, &stats, st);
-        mesh->cancel = nullptr;
-        J->res.iterations = stats.iterations;
-        J->res.refinements = stats.refinements;
-        J->res.rel_residual = stats.rel_residual;
-      }
-      if ((s == TN_OK || s == TN_ENOTCONVERGED) && S->opts.keep_solutions) {
-        J->u.resize((size_t)3 * L0.n_layout);
-        J->p.resize((size_t)L1.n_layout);
-        for (int c = 0; c < 3; ++c)
-          cudaMemcpyAsync(J->u.data() + (size_t)c * L0.n_layout, u[c], sizeof(double) * L0.n_layout,
-                          cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(J->p.data(), p, sizeof(double) * L1.n_layout, cudaMemcpyDeviceToHost, st);
-      }
-    }
-    for (double* q : {T, f[0], f[1], f[2], u[0], u[1], u[2], p})
-      if (q) cudaFreeAsync(q, st);
-    cudaStreamSynchronize(st);
-    J->res.status = s;
   }
+  const Level& L0 = R.mesh->lv[0];
+  const Level& L1 = R.mesh->lv[1];
+  // per-request vectors come from the stream-ordered pool (no device-wide synchronisation)
+  cudaError_t e = cudaMallocAsync((void**)&R.T, sizeof(double) * L0.n_layout, st);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&R.f[c], sizeof(double) * L0.n_layout, st);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMallocAsync((void**)&R.u[c], sizeof(double) * L0.n_layout, st);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&R.p, sizeof(double) * L1.n_layout, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(R.T, 0, sizeof(double) * L0.n_layout, st);
+  for (int c = 0; c < 3 && e == cudaSuccess; ++c) e = cudaMemsetAsync(R.f[c], 0, sizeof(double) * L0.n_layout, st);
+  if (e == cudaSuccess) {
+    const int64_t n = (int64_t)10 * L0.n_r * (L0.N + 1) * (L0.N + 1);
+    const double amp = Q.t_amplitude / pmax_of(Q.t_degree, Q.t_order);
+    k_temperature<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dims(L0), L0.s64, L0.rad64, Q.r_in, Q.r_out,
+                                                                Q.t_degree, Q.t_order, amp, R.T);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    R.s = TN_ECUDA;
+    return;
+  }
+  tn_visc_law law{Q.E, 0.0, 1.0};
+  R.s = tn_set_temperature(R.mesh, R.T, &law, st);
+  if (R.s == TN_OK) R.s = tn_buoyancy(R.mesh, R.T, Q.Ra, R.f, st);
+}
+
+// Solution copy (keep_solutions), vectors back to the pool, the mesh back to the idle pool (or its
+// reservation released), the result published.
+void finish_job(tn_server* S, JobRun& R, cudaStream_t st) {
+  Job* J = R.J;
+  const tn_request& Q = J->req;
+  if (R.mesh && (R.s == TN_OK || R.s == TN_ENOTCONVERGED) && S->opts.keep_solutions) {
+    const Level& L0 = R.mesh->lv[0];
+    const Level& L1 = R.mesh->lv[1];
+    J->u.resize((size_t)3 * L0.n_layout);
+    J->p.resize((size_t)L1.n_layout);
+    for (int c = 0; c < 3; ++c)
+      cudaMemcpyAsync(J->u.data() + (size_t)c * L0.n_layout, R.u[c], sizeof(double) * L0.n_layout,
+                      cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(J->p.data(), R.p, sizeof(double) * L1.n_layout, cudaMemcpyDeviceToHost, st);
+  }
+  for (double* q : {R.T, R.f[0], R.f[1], R.f[2], R.u[0], R.u[1], R.u[2], R.p})
+    if (q) cudaFreeAsync(q, st);
+  cudaStreamSynchronize(st);
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    if (mesh) S->idle.push_back(Pooled{mesh, Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, ++S->use_clock});
-    else S->reserved -= footprint(Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, S->opts.mode);
+    const Shape sh{Q.lateral_level, Q.radial_layers, Q.r_in, Q.r_out};
+    if (R.mesh) S->idle.push_back(Pooled{R.mesh, sh, ++S->use_clock});
+    else S->reserved -= footprint(sh, S->opts.mode);
+    J->res.status = R.s;
     J->res.t_end = S->now();
     J->res.state = 2;
     J->done = true;
     --S->running;
   }
+}
+
+// One request, or a lockstep batch of same-shape requests (tn_stokes_solve_batch), on stream st.
+void run_jobs(tn_server* S, std::vector<JobRun>& runs, cudaStream_t st) {
+  for (JobRun& R : runs) prepare_job(S, R, st);
+  tn_solve_opts so;
+  tn_solve_default_opts(&so);
+  so.mode = S->opts.mode;
+  so.rtol = S->opts.rtol;
+  std::vector<JobRun*> ready;
+  for (JobRun& R : runs)
+    if (R.s == TN_OK) ready.push_back(&R);
+  for (JobRun* R : ready) R->mesh->cancel = &R->J->cancel;
+  if (ready.size() == 1 || (!ready.empty() && so.mode == TN_SOLVE_MIXED)) {
+    for (JobRun* R : ready) {
+      tn_solve_stats ss{};
+      R->s = tn_stokes_solve(R->mesh, &so, (const double* const*)R->f, nullptr, R->u, R->p, &ss, st);
+      R->J->res.iterations = ss.iterations, R->J->res.refinements = ss.refinements;
+      R->J->res.rel_residual = ss.rel_residual;
+    }
+  } else if (!ready.empty()) {
+    const size_t n = ready.size();
+    std::vector<tn_mesh*> ms(n);
+    std::vector<const double* const*> fs(n);
+    std::vector<double* const*> us(n);
+    std::vector<double*> ps(n);
+    std::vector<tn_solve_stats> ss(n);
+    std::vector<tn_status> st_(n);
+    for (size_t i = 0; i < n; ++i)
+      ms[i] = ready[i]->mesh, fs[i] = ready[i]->f, us[i] = ready[i]->u, ps[i] = ready[i]->p;
+    tn_stokes_solve_batch(ms.data(), (int)n, &so, fs.data(), nullptr, us.data(), ps.data(), ss.data(), st_.data(), st);
+    for (size_t i = 0; i < n; ++i) {
+      ready[i]->s = st_[i];
+      ready[i]->J->res.iterations = ss[i].iterations, ready[i]->J->res.refinements = ss[i].refinements;
+      ready[i]->J->res.rel_residual = ss[i].rel_residual;
+      ready[i]->J->res.batch = (int)n;
+    }
+  }
+  for (JobRun* R : ready) R->mesh->cancel = nullptr;
+  for (JobRun& R : runs) finish_job(S, R, st);
   S->cv_done.notify_all();
   S->cv_work.notify_all();
 }
@@ -247,8 +291,7 @@ void worker(tn_server* S) {
   cudaStream_t st;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   while (true) {
-    Job* J = nullptr;
-    tn_mesh* mesh = nullptr;
+    std::vector<JobRun> runs;
     std::vector<tn_mesh*> to_free;
     {
       std::unique_lock<std::mutex> lk(S->mu);
@@ -256,22 +299,39 @@ void worker(tn_server* S) {
         if (S->stop && S->queue.empty()) break;
         for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
           const tn_request& R = (*it)->req;
+          tn_mesh* mesh = nullptr;
           if (acquire_locked(S, Shape{R.lateral_level, R.radial_layers, R.r_in, R.r_out}, &mesh, to_free)) {
-            J = *it;
+            runs.push_back(JobRun{*it, mesh});
             S->queue.erase(it);
             break;
           }
         }
-        if (J) break;
+        if (!runs.empty()) break;
         S->cv_work.wait(lk);
       }
-      if (!J) break;
-      ++S->running;
-      J->res.state = 1;
-      J->res.t_start = S->now();
+      if (runs.empty()) break;
+      // lockstep batch: further queued requests of the same shape, as long as they fit the budget
+      const tn_request& R0 = runs[0].J->req;
+      const Shape s0{R0.lateral_level, R0.radial_layers, R0.r_in, R0.r_out};
+      for (auto it = S->queue.begin(); it != S->queue.end() && (int)runs.size() < S->opts.max_batch;) {
+        const tn_request& R = (*it)->req;
+        const Shape sh{R.lateral_level, R.radial_layers, R.r_in, R.r_out};
+        tn_mesh* mesh = nullptr;
+        if (!(sh < s0) && !(s0 < sh) && acquire_locked(S, sh, &mesh, to_free)) {
+          runs.push_back(JobRun{*it, mesh});
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+      for (JobRun& r : runs) {
+        ++S->running;
+        r.J->res.state = 1;
+        r.J->res.t_start = S->now();
+      }
     }
     for (tn_mesh* m : to_free) tn_mesh_destroy(m);
-    run_job(S, J, mesh, st);
+    run_jobs(S, runs, st);
   }
   cudaStreamDestroy(st);
 }
@@ -293,6 +353,7 @@ tn_status tn_server_default_opts(tn_server_opts* o) {
   o->eta_storage = TN_ETA_F32;
   o->hg_kappa = 0.0;
   o->radial_quad_points = 1;
+  o->max_batch = 1;
   return TN_OK;
 }
 
@@ -303,7 +364,8 @@ tn_status tn_server_create(const tn_server_opts* opts, tn_server** out) {
   if (opts) o = *opts;
   if (o.max_active < 1 || o.max_active > 64 || !(o.memory_fraction > 0.0) || o.memory_fraction > 1.0 ||
       !(o.rtol > 0.0) || o.eta_storage < TN_ETA_F32 || o.eta_storage > TN_ETA_F16 || !(o.hg_kappa >= 0.0) ||
-      o.radial_quad_points < 0 || o.radial_quad_points > 2 || (o.radial_quad_points == 2 && o.hg_kappa > 0.0)) {
+      o.radial_quad_points < 0 || o.radial_quad_points > 2 || (o.radial_quad_points == 2 && o.hg_kappa > 0.0) ||
+      o.max_batch < 1 || o.max_batch > 64) {
     set_error("tn_server_create: invalid options");
     return TN_EINVAL;
   }

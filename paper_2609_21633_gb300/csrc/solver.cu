@@ -509,6 +509,7 @@ struct PrecState {
   KVec<T> w, tmp;                     // work vectors
   KVec<T> ir_r, ir_c;                 // FP32 iterative refinement: inner rhs and correction
   cudaGraphExec_t vgraph = nullptr;   // the V-cycle (level-0 b -> level-0 x) captured after set-up
+  cudaGraph_t vtemplate = nullptr;    // its graph, kept for composing several systems' V-cycles
   T* tu[3] = {nullptr, nullptr, nullptr};  // velocity scratch (level 0)
 };
 
@@ -867,6 +868,10 @@ void capture_vcycle(MGState* m, const tn_mesh* mesh) {
     cudaGraphExecDestroy(P.vgraph);
     P.vgraph = nullptr;
   }
+  if (P.vtemplate) {
+    cudaGraphDestroy(P.vtemplate);
+    P.vtemplate = nullptr;
+  }
   if (!m->cap) ck(cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking));
   if (g_err != cudaSuccess) return;
   cudaGraph_t g = nullptr;
@@ -876,7 +881,8 @@ void capture_vcycle(MGState* m, const tn_mesh* mesh) {
   if (e == cudaSuccess && g_err == cudaSuccess) {
     if (cudaGraphInstantiate(&P.vgraph, g, 0) != cudaSuccess) P.vgraph = nullptr;
   }
-  if (g) cudaGraphDestroy(g);
+  if (P.vgraph) P.vtemplate = g;
+  else if (g) cudaGraphDestroy(g);
   cudaGetLastError();
 }
 
@@ -1071,9 +1077,10 @@ void apply_K(MGState* m, tn_mesh* mesh, const KVec<T>& x, KVec<T>& y, cudaStream
   ck(launch_restrict<T>(L0, L1, bc, 1, 0, fin, cout, st));
 }
 
-// z = P^-1 r: z_p = -r_p / diag(M_1/eta), z_u = V(r_u - B^T z_p)
+// z = P^-1 r: z_p = -r_p / diag(M_1/eta), z_u = V(r_u - B^T z_p).  Split around the V-cycle for
+// the lockstep solver: prec_pre (z_p and the V-cycle's right-hand side), the V-cycle, prec_post.
 template <typename T>
-void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStream_t st) {
+void prec_pre(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStream_t st) {
   PrecState<T>& P = ps<T>(m);
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
@@ -1100,15 +1107,28 @@ void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStr
   k_axpby<T><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, 3, -1.0, P4<T>((const T* const*)P.tu, 3), 1.0,
                                              M4<T>(G.b.mm(), 3));
   ckl();
-  run_vcycle<T>(m, mesh, st);
+}
+
+template <typename T>
+void prec_post(MGState* m, tn_mesh* mesh, KVec<T>& z, cudaStream_t st) {
+  PrecState<T>& P = ps<T>(m);
+  const Level& L0 = mesh->lv[0];
+  MGLevelT<T>& G = P.L[0];
   for (int c = 0; c < 3; ++c)
     ck(cudaMemcpyAsync(z.u[c], G.x().c[c], sizeof(T) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
+}
+
+template <typename T>
+void apply_prec(MGState* m, tn_mesh* mesh, const KVec<T>& r, KVec<T>& z, cudaStream_t st) {
+  prec_pre<T>(m, mesh, r, z, st);
+  run_vcycle<T>(m, mesh, st);
+  prec_post<T>(m, mesh, z, st);
 }
 
 
 // FP64 Krylov vector -> FP32 preconditioner -> FP64 (mode TN_SOLVE_F64_PREC32): the vector is
 // unit-norm, so FP32 holds it without scaling.
-void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<double>& z, cudaStream_t st) {
+void prec_f32_pre(MGState* m, tn_mesh* mesh, const KVec<double>& r, cudaStream_t st) {
   PrecState<float>& F = m->p32;
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
@@ -1118,13 +1138,26 @@ void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<doubl
   }
   k_convert<double, float><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, r.p, F.ir_r.p, 1.0);
   ckl();
-  apply_prec<float>(m, mesh, F.ir_r, F.ir_c, st);
+  prec_pre<float>(m, mesh, F.ir_r, F.ir_c, st);
+}
+
+void prec_f32_post(MGState* m, tn_mesh* mesh, KVec<double>& z, cudaStream_t st) {
+  PrecState<float>& F = m->p32;
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  prec_post<float>(m, mesh, F.ir_c, st);
   for (int c = 0; c < 3; ++c) {
     k_convert<float, double><<<nb(L0.n_layout), EB, 0, st>>>(L0.n_layout, F.ir_c.u[c], z.u[c], 1.0);
     ckl();
   }
   k_convert<float, double><<<nb(L1.n_layout), EB, 0, st>>>(L1.n_layout, F.ir_c.p, z.p, 1.0);
   ckl();
+}
+
+void apply_prec_f32(MGState* m, tn_mesh* mesh, const KVec<double>& r, KVec<double>& z, cudaStream_t st) {
+  prec_f32_pre(m, mesh, r, st);
+  run_vcycle<float>(m, mesh, st);
+  prec_f32_post(m, mesh, z, st);
 }
 
 // Restarted FGMRES(m) with right preconditioning and CGS2 orthogonalisation (Saad 1993).
@@ -1248,6 +1281,191 @@ const char* breakdown_text(int why) {
   }
 }
 
+// ---------------------------------------------------------------- lockstep FGMRES (serving batches)
+// Several systems advance in lockstep on one stream: each round enqueues, for every system, either
+// its restart residual or one FGMRES iteration, launches the V-cycles of all iterating systems
+// together as one CUDA graph (each system's captured V-cycle a child graph, run concurrently),
+// synchronises once and does every system's host part.  Per system the enqueued kernels, their
+// order and the host arithmetic are those of fgmres<double>, so each result is bitwise the one of
+// a solve alone.
+struct LockSys {
+  tn_mesh* mesh = nullptr;
+  MGState* m = nullptr;
+  KVec<double> b, x;
+  double abstol = 0, beta = 0, beta_best = 0;
+  int its = 0, j = 0, stall = 0, why = FGMRES_OK, phase = 0;  // phase 0 restart, 1 iterating, 2 done
+  std::vector<double> H, cs, sn, g, y;
+  double* hs = nullptr;  // pinned host copy of the system's device scalars
+};
+
+cudaGraph_t sys_vtemplate(MGState* m, bool prec32) { return prec32 ? m->p32.vtemplate : m->p64.vtemplate; }
+
+// The combined V-cycle graph of a subset of systems (bit mask), instantiated once and cached.
+struct VcycleBatch {
+  std::vector<std::pair<uint64_t, cudaGraphExec_t>> cache;
+  ~VcycleBatch() {
+    for (auto& c : cache) cudaGraphExecDestroy(c.second);
+  }
+  cudaGraphExec_t get(uint64_t mask, std::vector<LockSys>& sys, bool prec32) {
+    for (auto& c : cache)
+      if (c.first == mask) return c.second;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return nullptr;
+    bool ok = true;
+    for (size_t i = 0; i < sys.size() && ok; ++i) {
+      if (!(mask >> i & 1)) continue;
+      cudaGraph_t child = sys_vtemplate(sys[i].m, prec32);
+      cudaGraphNode_t node;
+      ok = child && cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child) == cudaSuccess;
+    }
+    if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (ex) cache.emplace_back(mask, ex);
+    return ex;
+  }
+};
+
+void lock_update_x(LockSys& q, int cols, int rs, cudaStream_t st) {
+  PrecState<double>& P = q.m->p64;
+  for (int i = cols - 1; i >= 0; --i) {
+    double v = q.g[i];
+    for (int k = i + 1; k < cols; ++k) v -= q.H[k * (rs + 1) + i] * q.y[k];
+    q.y[i] = v / q.H[i * (rs + 1) + i];
+  }
+  ck(cudaMemcpyAsync(q.m->S + S_Y, q.y.data(), sizeof(double) * cols, cudaMemcpyHostToDevice, st));
+  std::vector<const KVec<double>*> zb(cols);
+  for (int i = 0; i < cols; ++i) zb[i] = &P.Z[i];
+  if (cols > 0) kaxpy<double>(q.mesh, cols, zb.data(), q.m->S + S_Y, 1.0, q.x, st);
+}
+
+void fgmres_lockstep(std::vector<LockSys>& sys, int restart, int max_iters, bool prec32, cudaStream_t st) {
+  VcycleBatch vb;
+  for (auto& q : sys) {
+    q.H.assign((restart + 1) * restart, 0.0);
+    q.cs.assign(restart, 0.0), q.sn.assign(restart, 0.0), q.g.assign(restart + 1, 0.0), q.y.assign(restart, 0.0);
+  }
+  while (g_err == cudaSuccess) {
+    bool any = false;
+    uint64_t mask = 0;
+    // enqueue: restart residuals, and the first half of an iteration up to the V-cycle
+    for (size_t i = 0; i < sys.size(); ++i) {
+      LockSys& q = sys[i];
+      PrecState<double>& P = q.m->p64;
+      if (q.phase == 2) continue;
+      any = true;
+      if (q.phase == 0) {
+        apply_K<double>(q.m, q.mesh, q.x, P.w, st);
+        kaxpby<double>(q.mesh, 1.0, q.b, 0.0, P.V[0], st);
+        kaxpby<double>(q.mesh, -1.0, P.w, 1.0, P.V[0], st);
+        const KVec<double>* v0[1] = {&P.V[0]};
+        kdots<double>(q.m, q.mesh, 1, v0, P.V[0], q.m->S + S_NRM, st);
+        ck(cudaMemcpyAsync(q.hs, q.m->S, sizeof(double) * S_MAX, cudaMemcpyDeviceToHost, st));
+      } else {
+        if (prec32) prec_f32_pre(q.m, q.mesh, P.V[q.j], st);
+        else prec_pre<double>(q.m, q.mesh, P.V[q.j], P.Z[q.j], st);
+        mask |= (uint64_t)1 << i;
+      }
+    }
+    if (!any) break;
+    if (mask) {
+      cudaGraphExec_t ex = (mask & (mask - 1)) ? vb.get(mask, sys, prec32) : nullptr;
+      if (ex) {
+        ck(cudaGraphLaunch(ex, st));
+      } else {
+        for (size_t i = 0; i < sys.size(); ++i)
+          if (mask >> i & 1) {
+            if (prec32) run_vcycle<float>(sys[i].m, sys[i].mesh, st);
+            else run_vcycle<double>(sys[i].m, sys[i].mesh, st);
+          }
+      }
+    }
+    // second half of the iterations: preconditioned vector, operator, CGS2
+    for (size_t i = 0; i < sys.size(); ++i) {
+      if (!(mask >> i & 1)) continue;
+      LockSys& q = sys[i];
+      PrecState<double>& P = q.m->p64;
+      const int j = q.j;
+      if (prec32) prec_f32_post(q.m, q.mesh, P.Z[j], st);
+      else prec_post<double>(q.m, q.mesh, P.Z[j], st);
+      apply_K<double>(q.m, q.mesh, P.Z[j], P.w, st);
+      std::vector<const KVec<double>*> vbs(j + 1);
+      for (int k = 0; k <= j; ++k) vbs[k] = &P.V[k];
+      kdots<double>(q.m, q.mesh, j + 1, vbs.data(), P.w, q.m->S + S_H, st);
+      kaxpy<double>(q.mesh, j + 1, vbs.data(), q.m->S + S_H, -1.0, P.w, st);
+      kdots<double>(q.m, q.mesh, j + 1, vbs.data(), P.w, q.m->S + S_H2, st);
+      kaxpy<double>(q.mesh, j + 1, vbs.data(), q.m->S + S_H2, -1.0, P.w, st);
+      const KVec<double>* wv[1] = {&P.w};
+      kdots<double>(q.m, q.mesh, 1, wv, P.w, q.m->S + S_NRM, st);
+      ck(cudaMemcpyAsync(q.hs, q.m->S, sizeof(double) * S_MAX, cudaMemcpyDeviceToHost, st));
+    }
+    ck(cudaStreamSynchronize(st));
+    if (g_err != cudaSuccess) break;
+    // host part of every system, in order
+    for (size_t i = 0; i < sys.size(); ++i) {
+      LockSys& q = sys[i];
+      PrecState<double>& P = q.m->p64;
+      if (q.phase == 0) {
+        q.beta = std::sqrt(q.hs[S_NRM]);
+        if (!std::isfinite(q.beta)) q.why = FGMRES_NONFINITE;
+        else if (q.its > 0 && !(q.beta < 0.999 * q.beta_best)) ++q.stall;
+        else q.stall = 0;
+        if (q.stall >= kStallRestarts) q.why = FGMRES_STALL;
+        if (cancelled(q.mesh)) q.why = FGMRES_CANCELLED;
+        if (q.its == 0 || q.beta < q.beta_best) q.beta_best = q.beta;
+        if (q.why != FGMRES_OK || q.beta <= q.abstol || q.its >= max_iters) {
+          q.phase = 2;
+          continue;
+        }
+        kaxpby<double>(q.mesh, 0.0, P.V[0], 1.0 / q.beta, P.V[0], st);
+        std::fill(q.g.begin(), q.g.end(), 0.0);
+        q.g[0] = q.beta;
+        q.j = 0;
+        q.phase = 1;
+        continue;
+      }
+      if (q.phase != 1) continue;
+      const int j = q.j;
+      double* col = &q.H[j * (restart + 1)];
+      bool finite = std::isfinite(q.hs[S_NRM]);
+      for (int k = 0; k <= j; ++k) {
+        col[k] = q.hs[S_H + k] + q.hs[S_H2 + k];
+        finite = finite && std::isfinite(col[k]);
+      }
+      if (!finite) {  // update x with the previous columns and stop
+        q.why = FGMRES_NONFINITE;
+        lock_update_x(q, j, restart, st);
+        q.phase = 2;
+        continue;
+      }
+      const double hn = std::sqrt(q.hs[S_NRM]);
+      col[j + 1] = hn;
+      if (hn > 0) kaxpby<double>(q.mesh, 1.0 / hn, P.w, 0.0, P.V[j + 1], st);
+      for (int k = 0; k < j; ++k) {
+        const double t0 = q.cs[k] * col[k] + q.sn[k] * col[k + 1];
+        col[k + 1] = -q.sn[k] * col[k] + q.cs[k] * col[k + 1];
+        col[k] = t0;
+      }
+      const double den = std::sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+      q.cs[j] = den > 0 ? col[j] / den : 1.0;
+      q.sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      q.g[j + 1] = -q.sn[j] * q.g[j];
+      q.g[j] = q.cs[j] * q.g[j];
+      ++q.its;
+      const bool stop = std::fabs(q.g[j + 1]) <= q.abstol || hn == 0.0 || cancelled(q.mesh);
+      if (stop || j + 1 >= restart || q.its >= max_iters) {  // end of the cycle: x += Z y, then restart
+        lock_update_x(q, j + 1, restart, st);
+        q.phase = 0;
+      } else {
+        q.j = j + 1;
+      }
+    }
+  }
+}
+
 template <typename T>
 KVec<T> wrap(T* const* u, T* p) {
   KVec<T> v;
@@ -1300,6 +1518,8 @@ void mg_free(MGState* m) {
   }
   if (m->p64.vgraph) cudaGraphExecDestroy(m->p64.vgraph);
   if (m->p32.vgraph) cudaGraphExecDestroy(m->p32.vgraph);
+  if (m->p64.vtemplate) cudaGraphDestroy(m->p64.vtemplate);
+  if (m->p32.vtemplate) cudaGraphDestroy(m->p32.vtemplate);
   if (m->cap) cudaStreamDestroy(m->cap);
   if (m->S) cudaFree(m->S);
   if (m->flag) cudaFree(m->flag);
@@ -1459,39 +1679,46 @@ tn_status tn_solve_default_opts(tn_solve_opts* o) {
   return TN_OK;
 }
 
-tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f, const double* g,
-                          double* const* u, double* p, tn_solve_stats* stats, void* stream) {
-  if (!mesh || !f || !u || !p) return TN_EINVAL;
+}  // extern "C"
+
+namespace {
+
+// Checks shared by the single and the batched solve.
+tn_status solve_check(const char* who, tn_mesh* mesh, const tn_solve_opts& o, const double* const* f,
+                      double* const* u, double* p) {
+  if (!mesh || !f || !u || !p) {
+    set_error(std::string(who) + ": NULL argument");
+    return TN_EINVAL;
+  }
   for (int c = 0; c < 3; ++c)
     if (!f[c] || !u[c]) {
-      set_error("tn_stokes_solve: NULL vector");
+      set_error(std::string(who) + ": NULL vector");
       return TN_EINVAL;
     }
   if (mesh->lv.size() < 2) {
-    set_error("tn_stokes_solve: the mesh hierarchy has a single level");
+    set_error(std::string(who) + ": the mesh hierarchy has a single level");
     return TN_EINVAL;
   }
-  tn_solve_opts o;
-  tn_solve_default_opts(&o);
-  if (opts) o = *opts;
   if (o.restart < 1 || o.restart > MAX_RESTART || !(o.rtol > 0) || o.max_iters < 1 ||
       (o.mode != TN_SOLVE_F64 && o.mode != TN_SOLVE_MIXED && o.mode != TN_SOLVE_F64_PREC32)) {
-    set_error("tn_stokes_solve: invalid options (restart must be in [1, 30])");
+    set_error(std::string(who) + ": invalid options (restart must be in [1, 30])");
     return TN_EINVAL;
   }
-  cudaStream_t st = (cudaStream_t)stream;
-  auto t0 = std::chrono::steady_clock::now();
-  const bool mixed = o.mode == TN_SOLVE_MIXED;
-  tn_status s;
+  return TN_OK;
+}
+
+// Multigrid set-up when needed, workspaces, b = (f, g) in the FP64 temporary, x = (u, p) = 0 and
+// ||b|| (one host synchronisation).
+tn_status solve_begin(tn_mesh* mesh, const tn_solve_opts& o, const double* const* f, const double* g, double* const* u,
+                      double* p, cudaStream_t st, void* stream, KVec<double>& b, KVec<double>& x, double& bnorm) {
+  const bool mixed = o.mode == TN_SOLVE_MIXED, prec32 = o.mode == TN_SOLVE_F64_PREC32;
   // the mixed modes need only the FP32 multigrid; the refinement mode keeps only the residual
   // work vectors in FP64, the FP32-preconditioner mode the FP64 Krylov basis
-  const bool prec32 = o.mode == TN_SOLVE_F64_PREC32;
   const bool mg32 = mixed || prec32;
   if (!mesh->mg || !(mg32 ? mesh->mg->p32.ready : mesh->mg->p64.ready)) {
-    s = tn_mg_setup(mesh, mg32 ? TN_F32 : TN_F64, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
+    const tn_status s = tn_mg_setup(mesh, mg32 ? TN_F32 : TN_F64, mesh->mg ? &mesh->mg->opts : nullptr, nullptr, stream);
     if (s != TN_OK) return s;
   }
-  g_err = cudaSuccess;
   MGState* m = mesh->mg;
   const Level& L0 = mesh->lv[0];
   const Level& L1 = mesh->lv[1];
@@ -1502,18 +1729,83 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
     set_error("tn_stokes_solve: workspace allocation failed");
     return TN_ENOMEM;
   }
-  // b = (f, g) in the FP64 temporary; x = (u, p) = 0
-  PrecState<double>& D = m->p64;
-  KVec<double> b = D.tmp;
+  b = m->p64.tmp;
   for (int c = 0; c < 3; ++c) ck(cudaMemcpyAsync(b.u[c], f[c], sizeof(double) * L0.n_layout, cudaMemcpyDeviceToDevice, st));
   if (g) ck(cudaMemcpyAsync(b.p, g, sizeof(double) * L1.n_layout, cudaMemcpyDeviceToDevice, st));
   else ck(cudaMemsetAsync(b.p, 0, sizeof(double) * L1.n_layout, st));
-  KVec<double> x = wrap<double>(u, p);
+  x = wrap<double>(u, p);
   for (int c = 0; c < 3; ++c) ck(cudaMemsetAsync(u[c], 0, sizeof(double) * L0.n_layout, st));
   ck(cudaMemsetAsync(p, 0, sizeof(double) * L1.n_layout, st));
   const KVec<double>* bb[1] = {&b};
   kdots<double>(m, mesh, 1, bb, b, m->S + S_NRM, st);
-  const double bnorm = std::sqrt(host_scalar(m, S_NRM, st));
+  bnorm = std::sqrt(host_scalar(m, S_NRM, st));
+  return TN_OK;
+}
+
+// Rigid rotations out of the returned velocity (free-slip on both surfaces), the true residual
+// ||b - K x|| (one host synchronisation).
+double solve_true_residual(tn_mesh* mesh, const KVec<double>& b, KVec<double>& x, cudaStream_t st) {
+  MGState* m = mesh->mg;
+  PrecState<double>& D = m->p64;
+  if (rotations_singular(mesh)) project_rotations<double>(m, mesh->lv[0], x.u, st);
+  KVec<double>& r = D.V[0];
+  apply_K<double>(m, mesh, x, D.w, st);
+  kaxpby<double>(mesh, 1.0, b, 0.0, r, st);
+  kaxpby<double>(mesh, -1.0, D.w, 1.0, r, st);
+  const KVec<double>* rv[1] = {&r};
+  kdots<double>(m, mesh, 1, rv, r, m->S + S_NRM, st);
+  return std::sqrt(host_scalar(m, S_NRM, st));
+}
+
+tn_status solve_status(const char* who, const tn_solve_opts& o, int its, int refs, int why, double res, double bnorm,
+                       double seconds, tn_solve_stats* stats) {
+  const double rel = bnorm > 0 ? res / bnorm : 0.0;
+  if (stats) {
+    stats->iterations = its;
+    stats->refinements = refs;
+    stats->rel_residual = rel;
+    stats->seconds = seconds;
+    stats->converged = why == FGMRES_OK && rel <= o.rtol;
+  }
+  if (g_err != cudaSuccess) {
+    set_error(std::string(who) + ": " + cudaGetErrorString(g_err));
+    return TN_ECUDA;
+  }
+  if (why == FGMRES_CANCELLED) {
+    set_error(std::string(who) + ": cancelled");
+    return TN_ECANCELED;
+  }
+  if (why != FGMRES_OK || !(rel <= o.rtol)) {  // !(<=): a NaN residual is not convergence
+    set_error(std::string(who) + ": " + breakdown_text(why));
+    return TN_ENOTCONVERGED;
+  }
+  return TN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double* const* f, const double* g,
+                          double* const* u, double* p, tn_solve_stats* stats, void* stream) {
+  tn_solve_opts o;
+  tn_solve_default_opts(&o);
+  if (opts) o = *opts;
+  tn_status s = solve_check("tn_stokes_solve", mesh, o, f, u, p);
+  if (s != TN_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto t0 = std::chrono::steady_clock::now();
+  const bool mixed = o.mode == TN_SOLVE_MIXED;
+  const bool prec32 = o.mode == TN_SOLVE_F64_PREC32;
+  g_err = cudaSuccess;
+  KVec<double> b, x;
+  double bnorm = 0;
+  s = solve_begin(mesh, o, f, g, u, p, st, stream, b, x, bnorm);
+  if (s != TN_OK) return s;
+  MGState* m = mesh->mg;
+  const Level& L0 = mesh->lv[0];
+  const Level& L1 = mesh->lv[1];
+  PrecState<double>& D = m->p64;
   int its = 0, refs = 0, why = FGMRES_OK;
   double res = bnorm;
   if (!std::isfinite(bnorm)) why = FGMRES_NONFINITE;  // NaN / Inf in f or g: nothing to solve
@@ -1561,39 +1853,76 @@ tn_status tn_stokes_solve(tn_mesh* mesh, const tn_solve_opts* opts, const double
         ++refs;
       }
     }
-    if (rotations_singular(mesh)) project_rotations<double>(m, L0, x.u, st);
-    // true residual of the returned solution
-    KVec<double>& r = D.V[0];
-    apply_K<double>(m, mesh, x, D.w, st);
-    kaxpby<double>(mesh, 1.0, b, 0.0, r, st);
-    kaxpby<double>(mesh, -1.0, D.w, 1.0, r, st);
-    const KVec<double>* rv[1] = {&r};
-    kdots<double>(m, mesh, 1, rv, r, m->S + S_NRM, st);
-    res = std::sqrt(host_scalar(m, S_NRM, st));
+    res = solve_true_residual(mesh, b, x, st);
   }
   ck(cudaStreamSynchronize(st));
-  auto t1 = std::chrono::steady_clock::now();
-  const double rel = bnorm > 0 ? res / bnorm : 0.0;
-  if (stats) {
-    stats->iterations = its;
-    stats->refinements = refs;
-    stats->rel_residual = rel;
-    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
-    stats->converged = why == FGMRES_OK && rel <= o.rtol;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return solve_status("tn_stokes_solve", o, its, refs, why, res, bnorm, secs, stats);
+}
+
+tn_status tn_stokes_solve_batch(tn_mesh* const* meshes, int n, const tn_solve_opts* opts, const double* const* const* f,
+                                const double* const* g, double* const* const* u, double* const* p,
+                                tn_solve_stats* stats, tn_status* status, void* stream) {
+  if (!meshes || n < 1 || n > 64 || !f || !u || !p || !status) {
+    set_error("tn_stokes_solve_batch: bad arguments (1 <= n <= 64)");
+    return TN_EINVAL;
   }
-  if (g_err != cudaSuccess) {
-    set_error(std::string("tn_stokes_solve: ") + cudaGetErrorString(g_err));
-    return TN_ECUDA;
+  tn_solve_opts o;
+  tn_solve_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.mode == TN_SOLVE_MIXED) {
+    set_error("tn_stokes_solve_batch: modes TN_SOLVE_F64 and TN_SOLVE_F64_PREC32 only");
+    return TN_EINVAL;
   }
-  if (why == FGMRES_CANCELLED) {
-    set_error("tn_stokes_solve: cancelled");
-    return TN_ECANCELED;
+  for (int i = 0; i < n; ++i) {
+    const tn_status s = solve_check("tn_stokes_solve_batch", meshes[i], o, f[i], u[i], p[i]);
+    if (s != TN_OK) return s;
+    for (int k = 0; k < i; ++k)
+      if (meshes[k] == meshes[i]) {
+        set_error("tn_stokes_solve_batch: a mesh appears twice");
+        return TN_EINVAL;
+      }
   }
-  if (why != FGMRES_OK || !(rel <= o.rtol)) {  // !(<=): a NaN residual is not convergence
-    set_error(std::string("tn_stokes_solve: ") + breakdown_text(why));
-    return TN_ENOTCONVERGED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool prec32 = o.mode == TN_SOLVE_F64_PREC32;
+  auto t0 = std::chrono::steady_clock::now();
+  g_err = cudaSuccess;
+  std::vector<LockSys> sys(n);
+  std::vector<double> bnorm(n, 0.0), res(n, 0.0);
+  std::vector<int> why(n, FGMRES_OK);
+  std::vector<KVec<double>> bs(n);
+  tn_status first = TN_OK;
+  for (int i = 0; i < n; ++i) status[i] = TN_OK;
+  for (int i = 0; i < n; ++i) {
+    status[i] = solve_begin(meshes[i], o, f[i], g ? g[i] : nullptr, u[i], p[i], st, stream, bs[i], sys[i].x, bnorm[i]);
+    LockSys& q = sys[i];
+    q.mesh = meshes[i];
+    q.m = meshes[i]->mg;
+    q.b = bs[i];
+    q.abstol = o.rtol * bnorm[i];
+    res[i] = bnorm[i];
+    if (status[i] != TN_OK || !std::isfinite(bnorm[i]) || !(bnorm[i] > 0)) q.phase = 2;
+    if (status[i] == TN_OK && !std::isfinite(bnorm[i])) why[i] = FGMRES_NONFINITE;
+    if (status[i] == TN_OK && cudaMallocHost((void**)&q.hs, sizeof(double) * S_MAX) != cudaSuccess) {
+      status[i] = TN_ENOMEM;
+      q.phase = 2;
+    }
   }
-  return TN_OK;
+  fgmres_lockstep(sys, o.restart, o.max_iters, prec32, st);
+  for (int i = 0; i < n; ++i) {
+    LockSys& q = sys[i];
+    if (status[i] == TN_OK) {
+      if (why[i] == FGMRES_OK) why[i] = q.why;
+      if (bnorm[i] > 0 && std::isfinite(bnorm[i])) res[i] = solve_true_residual(q.mesh, q.b, q.x, st);
+      ck(cudaStreamSynchronize(st));
+      const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      status[i] = solve_status("tn_stokes_solve_batch", o, q.its, 0, why[i], res[i], bnorm[i], secs,
+                               stats ? &stats[i] : nullptr);
+    }
+    if (q.hs) cudaFreeHost(q.hs);
+    if (first == TN_OK && status[i] != TN_OK) first = status[i];
+  }
+  return first;
 }
 
 }  // extern "C"

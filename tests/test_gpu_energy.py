@@ -130,3 +130,19 @@ def test_convection_loop_matches_the_oracle(tn):
         assert np.abs(T - T0).max() > 1e-4                    # the field evolved
     finally:
         s.close()
+
+
+def test_stable_substep_scales_with_the_mesh(tn):
+    """The diffusion bound dt ~ h^2: from level 3 / 9 to 5 / 33 to 7 / 129 layers the spacing halves
+    twice per pair, so the stable substep shrinks by about 16 each time (the largest eigenvalue of
+    M^-1 K reaches ~1e6 at level 7, where an unnormalised power iteration would overflow)."""
+    dts = []
+    for level, n_r in ((3, 9), (5, 33), (7, 129)):
+        m = tn.tn_mesh_create(level, n_r, R_IN, R_OUT, max_levels=2)
+        try:
+            dts.append(tn.tn_energy_stable_dt(m))
+        finally:
+            tn.tn_mesh_destroy(m)
+    ratios = [dts[0] / dts[1], dts[1] / dts[2]]
+    print("stable substeps", dts, "ratios", ratios)
+    assert all(8.0 <= q <= 32.0 for q in ratios), (dts, ratios)

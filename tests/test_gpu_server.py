@@ -87,3 +87,32 @@ def test_admission_and_invalid_requests(tn):
             tn.tn_server_submit(srv, 3, 9, 0.0, 7e3, 2, 3, 0.01)  # order > degree
     finally:
         tn.tn_server_destroy(srv)
+
+
+def test_same_shape_requests_batched_in_lockstep(tn):
+    """max_batch = 4: queued requests of one shape are solved in lockstep (tn_stokes_solve_batch, their
+    V-cycles from one graph launch).  A request's solution is bitwise the same alone and inside such
+    a batch, and batches do form."""
+    srv = tn.tn_server_create(tn.tn_server_default_opts(max_active=1, keep_solutions=1, max_batch=4, hg_kappa=0.3,
+                                                        eta_storage=1, mode=tn.TN_SOLVE_F64_PREC32))
+    try:
+        ref = dict(lateral_level=3, radial_layers=9, E=math.log(100.0), Ra=7e3, t_degree=3, t_order=2,
+                   t_amplitude=0.03)
+        t0 = tn.tn_server_submit(srv, **ref)
+        r0 = tn.tn_server_wait(srv, t0)
+        assert r0["status"] == tn.TN_OK and r0["batch"] == 0
+        u0, p0 = tn.tn_server_solution(srv, t0, *layouts(3, 9))
+        # one worker: while it solves the first request, the others queue up and the next take batches
+        mix = [dict(ref, E=math.log(1e3)), ref, dict(ref, t_degree=5, t_order=3), dict(ref, E=0.0), ref,
+               dict(ref, t_amplitude=0.05), dict(ref, lateral_level=4, radial_layers=9)]
+        tickets = [tn.tn_server_submit(srv, **q) for q in mix]
+        results = [tn.tn_server_wait(srv, t) for t in tickets]
+        for q, r in zip(mix, results):
+            assert r["status"] == tn.TN_OK and r["rel_residual"] <= 1e-8, (q, r)
+        assert max(r["batch"] for r in results) >= 2, [r["batch"] for r in results]
+        v, pv = valid_mask(3, 9), valid_mask(2, 5)
+        for t in (tickets[1], tickets[4]):
+            u1, p1 = tn.tn_server_solution(srv, t, *layouts(3, 9))
+            assert np.array_equal(u1[:, v], u0[:, v]) and np.array_equal(p1[pv], p0[pv])
+    finally:
+        tn.tn_server_destroy(srv)

@@ -1,4 +1,6 @@
 """GPU multigrid and Stokes solve against the CPU FP64 oracle (through the C ABI)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -133,3 +135,54 @@ def test_stokes_solution_matches_direct_solve(tn):
     # both solutions meet a 1e-8 relative residual; the difference is that residual amplified
     # by the conditioning of the saddle system (observed about 2e-6 for u at level 3)
     assert err_u < 2e-5 and err_p < 2e-5
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_lockstep_batch_is_bitwise_the_solo_solve(tn, mode):
+    """tn_stokes_solve_batch: four same-shape systems (different temperature fields and viscosity
+    contrasts, so they converge after different iteration counts; the fourth with a NaN load) give,
+    per system, bitwise the velocity and pressure of tn_stokes_solve, the same iteration counts and
+    statuses."""
+    level, n_r = 3, 9
+    om = ShellMesh(level, n_r, 0.55, 1.0)
+    specs = [(math.log(10.0), 0.01, 3, 2), (math.log(1e3), 0.03, 4, 1), (math.log(100.0), 0.02, 2, 0),
+             (math.log(10.0), float("nan"), 3, 2)]
+
+    def make(E, amp, deg, order):
+        m = tn.tn_mesh_create(level, n_r, 0.55, 1.0, hg_kappa=0.3)
+        info, pinfo = tn.tn_mesh_info(m, 0), tn.tn_mesh_info(m, 1)
+        mp = LayoutMap(info, om)
+        T = inputs.temperature(om.node_xyz(), 0.55, 1.0, amp=0.01 if amp != amp else amp, l=deg, m=order)
+        Td = torch.tensor(mp.to_layout(T), device="cuda")
+        tn.tn_set_temperature(m, Td, E)
+        f = [torch.zeros(info["n_layout"], device="cuda", dtype=torch.float64) for _ in range(3)]
+        tn.tn_buoyancy(m, Td, 7e3, f)
+        if amp != amp:
+            f[0][5] = float("nan")
+        u = [torch.zeros_like(f[0]) for _ in range(3)]
+        p = torch.zeros(pinfo["n_layout"], device="cuda", dtype=torch.float64)
+        return m, f, u, p
+
+    opts = tn.tn_solve_default_opts(mode=mode)
+    solo, batch = [], []
+    try:
+        for spec in specs:
+            m, f, u, p = make(*spec)
+            st = tn.tn_stokes_solve(m, f, None, u, p, opts, check=False)
+            solo.append((m, st, [t.clone() for t in u], p.clone()))
+        sys = [make(*spec) for spec in specs]
+        batch = [s[0] for s in sys]
+        res = tn.tn_stokes_solve_batch(batch, [s[1] for s in sys], [s[2] for s in sys], [s[3] for s in sys], opts)
+        for i, ((status, st), (_, st0, u0, p0), s) in enumerate(zip(res, solo, sys)):
+            print(f"system {i}: status {status}, {st['iterations']} its (solo {st0['iterations']}), "
+                  f"residual {st['rel_residual']:.2e}")
+            assert st["iterations"] == st0["iterations"] and st["converged"] == st0["converged"]
+            if i < 3:
+                assert status == tn.TN_OK and st["rel_residual"] <= 1e-8
+                assert all(torch.equal(a, b) for a, b in zip(s[2], u0)) and torch.equal(s[3], p0)
+            else:
+                assert status == tn.TN_ENOTCONVERGED
+        assert len({st["iterations"] for _, st in res[:3]}) > 1  # the systems left the rounds at different times
+    finally:
+        for m in [s[0] for s in solo] + batch:
+            tn.tn_mesh_destroy(m)
