@@ -184,4 +184,72 @@ TN_DF_HD double widen(float f) {
 // double-float -> binary64: one exact FP64 addition
 TN_DF_HD double join(dfl a) { return widen(a.hi) + widen(a.lo); }
 
+#if defined(__CUDACC__)
+// Packed double-float: two independent values in the lanes of f32x2 registers (hi.x + lo.x,
+// hi.y + lo.y), every operation the scalar one lane-wise with the packed FP32 instructions (one
+// issue slot per pair).  Lanes never mix inside an operation and every packed instruction rounds
+// each lane to nearest, so a lane follows the scalar formula step for step.  A kernel written with
+// df2 may still group its sums differently from its scalar version: the two then agree to the
+// double-float rounding level (about 2^-46 relative), not bitwise.
+struct df2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 p2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ df2 pack(dfl a, dfl b) { return df2{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ dfl lane_x(const df2& a) { return dfl(a.hi.x, a.lo.x); }
+__device__ __forceinline__ dfl lane_y(const df2& a) { return dfl(a.hi.y, a.lo.y); }
+
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = p2add(a, b);
+  const float2 bb = p2sub(s, a);
+  e = p2add(p2sub(a, p2sub(s, bb)), p2sub(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = p2add(a, b);
+  e = p2sub(b, p2sub(s, a));
+}
+// AccurateDWPlusDW, lane-wise
+__device__ __forceinline__ df2 add2(const df2& x, const df2& y) {
+  float2 sh, sl, th, tl, vh, vl, zh, zl;
+  two_sum2(x.hi, y.hi, sh, sl);
+  two_sum2(x.lo, y.lo, th, tl);
+  fast_two_sum2(sh, p2add(sl, th), vh, vl);
+  fast_two_sum2(vh, p2add(tl, vl), zh, zl);
+  return df2{zh, zl};
+}
+__device__ __forceinline__ df2 sub2(const df2& x, const df2& y) { return add2(x, df2{p2neg(y.hi), p2neg(y.lo)}); }
+// DWTimesDW3, lane-wise
+__device__ __forceinline__ df2 mul2(const df2& x, const df2& y) {
+  const float2 ch = p2mul(x.hi, y.hi);
+  const float2 cl1 = p2fma(x.hi, y.hi, p2neg(ch));
+  const float2 tl1 = p2fma(x.hi, y.lo, p2mul(x.lo, y.lo));
+  const float2 cl2 = p2fma(x.lo, y.hi, tl1);
+  float2 zh, zl;
+  fast_two_sum2(ch, p2add(cl1, cl2), zh, zl);
+  return df2{zh, zl};
+}
+// add_nc / fma_nc, lane-wise
+__device__ __forceinline__ df2 add_nc2(const df2& x, const df2& y) {
+  float2 sh, sl, zh, zl;
+  two_sum2(x.hi, y.hi, sh, sl);
+  fast_two_sum2(sh, p2add(sl, p2add(x.lo, y.lo)), zh, zl);
+  return df2{zh, zl};
+}
+__device__ __forceinline__ df2 fma_nc2(const df2& x, const df2& y, const df2& w) {
+  const float2 ph = p2mul(x.hi, y.hi);
+  float2 pl = p2fma(x.hi, y.hi, p2neg(ph));
+  pl = p2fma(x.hi, y.lo, pl);
+  pl = p2fma(x.lo, y.hi, pl);
+  float2 sh, sl, zh, zl;
+  two_sum2(ph, w.hi, sh, sl);
+  fast_two_sum2(sh, p2add(sl, p2add(pl, w.lo)), zh, zl);
+  return df2{zh, zl};
+}
+#endif
+
 }  // namespace tn

@@ -312,62 +312,75 @@ struct OpA {
 
 // Double-float viscous block without hourglass control: the arithmetic of OpA with the sums
 // split by whether their terms can cancel.  The corner differences (a_xi, a_eta of nearly equal
-// nodal sums) and every node-level accumulation (combine_corners, carried and exchanged partials)
-// use the accurate double-word addition; the contractions that form the strain, the stress and
-// H = S M^-T, whose terms carry no such cancellation, use the fused multiply-add and the sum
-// without the second TwoSum (add_nc / fma_nc), about half the FP32 operations.
+// nodal sums) and every node-level accumulation (corner combinations, carried and exchanged
+// partials) use the accurate double-word addition; the contractions that form the strain, the
+// stress and H = S M^-T, whose terms carry no such cancellation, use the fused multiply-add and the
+// sum without the second TwoSum (add_nc / fma_nc).  The two wedges of the cell are the two lanes of
+// packed f32x2 double-floats (x = W0, y = W1; lane pairs of corners (00, 11), (10, 01), (01, 10),
+// as in OpA<float, false>), one issue slot per pair; lanes meet only where corners 10 and 01 and
+// the top-minus-bottom parts combine.
 template <>
 struct OpA<dfl, false> {
   static constexpr int NIN = 3, NOUT = 3;
   static constexpr bool USES_ETA = true, LOADS = true, NEEDS_D = true;
-  using Col = NoCol;
+  struct Col {
+    df2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
+  };
   int div_term;
   dfl hgk;
-  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
-  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&Mi)[2][9],
-                                       const dfl (&dM)[2], const dfl* lc, const dfl (&eta)[2], dfl (&accb)[4][3],
-                                       dfl (&acct)[4][3], const Col&) const {
-    const dfl r = lc[4], vw2 = lc[5];
-    dfl X[4][3], h[2][3];
+  __device__ __forceinline__ Col column(const dfl (&Mi)[2][9], const dfl (&dM)[2], int) const {
+    Col c;
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
-      const dfl* M = Mi[w];
-      const dfl mr[3] = {r * M[6], r * M[7], r * M[8]};
-      dfl G[3][3];
+    for (int q = 0; q < 9; ++q) c.M[q] = pack(Mi[0][q], Mi[1][q]);
+    c.dM = pack(dM[0], dM[1]);
+    return c;
+  }
+  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&)[2][9],
+                                       const dfl (&)[2], const dfl* lc, const dfl (&eta)[2], dfl (&accb)[4][3],
+                                       dfl (&acct)[4][3], const Col& col) const {
+    const df2 r = pack(lc[4], lc[4]), vw2 = pack(lc[5], lc[5]);
+    const df2* M = col.M;
+    const df2 mr[3] = {mul2(r, M[6]), mul2(r, M[7]), mul2(r, M[8])};
+    df2 G[3][3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const dfl ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c];
-        const dfl az = add_nc(add_nc(dd[c0][c], dd[c1][c]), dd[c2][c]);
+    for (int c = 0; c < 3; ++c) {
+      const df2 s0 = pack(s[0][c], s[3][c]), s1 = pack(s[1][c], s[2][c]), s2 = pack(s[2][c], s[1][c]);
+      const df2 ax = sub2(s1, s0), ay = sub2(s2, s0);
+      const df2 az = add_nc2(add_nc2(pack(dd[0][c], dd[3][c]), pack(dd[1][c], dd[2][c])), pack(dd[2][c], dd[1][c]));
 #pragma unroll
-        for (int x = 0; x < 3; ++x) G[c][x] = fma_nc(ax, M[x], fma_nc(ay, M[3 + x], az * mr[x]));
-      }
-      const dfl ve = (vw2 * dM[w]) * eta[w];
-      const dfl ve2(ve.hi + ve.hi, ve.lo + ve.lo);  // exact doubling
-      dfl S[3][3];
-      if (div_term) {
-        const dfl vt = (ve * dfl(-2.0 / 3.0)) * add_nc(add_nc(G[0][0], G[1][1]), G[2][2]);
-        S[0][0] = fma_nc(ve2, G[0][0], vt), S[1][1] = fma_nc(ve2, G[1][1], vt), S[2][2] = fma_nc(ve2, G[2][2], vt);
-      } else {
-        S[0][0] = ve2 * G[0][0], S[1][1] = ve2 * G[1][1], S[2][2] = ve2 * G[2][2];
-      }
-      S[0][1] = S[1][0] = ve * add_nc(G[0][1], G[1][0]);
-      S[0][2] = S[2][0] = ve * add_nc(G[0][2], G[2][0]);
-      S[1][2] = S[2][1] = ve * add_nc(G[1][2], G[2][1]);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const dfl h0 = fma_nc(S[c][0], M[0], fma_nc(S[c][1], M[1], S[c][2] * M[2]));
-        const dfl h1 = fma_nc(S[c][0], M[3], fma_nc(S[c][1], M[4], S[c][2] * M[5]));
-        h[w][c] = fma_nc(S[c][0], mr[0], fma_nc(S[c][1], mr[1], S[c][2] * mr[2]));
-        X[c0][c] = -(h0 + h1);
-        if (w == 0) {
-          X[c1][c] = h0, X[c2][c] = h1;
-        } else {
-          X[c1][c] += h0, X[c2][c] += h1;
-        }
-      }
+      for (int x = 0; x < 3; ++x) G[c][x] = fma_nc2(ax, M[x], fma_nc2(ay, M[3 + x], mul2(az, mr[x])));
     }
-    combine_corners<dfl, 3>(X, h, accb, acct);
+    const df2 ve = mul2(mul2(vw2, col.dM), pack(eta[0], eta[1]));
+    const df2 ve2{p2add(ve.hi, ve.hi), p2add(ve.lo, ve.lo)};  // exact doubling
+    df2 S[3][3];
+    if (div_term) {
+      const dfl m23(-2.0 / 3.0);
+      const df2 vt = mul2(mul2(ve, pack(m23, m23)), add_nc2(add_nc2(G[0][0], G[1][1]), G[2][2]));
+      S[0][0] = fma_nc2(ve2, G[0][0], vt), S[1][1] = fma_nc2(ve2, G[1][1], vt), S[2][2] = fma_nc2(ve2, G[2][2], vt);
+    } else {
+      S[0][0] = mul2(ve2, G[0][0]), S[1][1] = mul2(ve2, G[1][1]), S[2][2] = mul2(ve2, G[2][2]);
+    }
+    S[0][1] = S[1][0] = mul2(ve, add_nc2(G[0][1], G[1][0]));
+    S[0][2] = S[2][0] = mul2(ve, add_nc2(G[0][2], G[2][0]));
+    S[1][2] = S[2][1] = mul2(ve, add_nc2(G[1][2], G[2][1]));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const df2 h0 = fma_nc2(S[c][0], M[0], fma_nc2(S[c][1], M[1], mul2(S[c][2], M[2])));
+      const df2 h1 = fma_nc2(S[c][0], M[3], fma_nc2(S[c][1], M[4], mul2(S[c][2], M[5])));
+      const df2 h2 = fma_nc2(S[c][0], mr[0], fma_nc2(S[c][1], mr[1], mul2(S[c][2], mr[2])));
+      // X at corners (00, 11) = -(h0 + h1) per lane; at (10, 01) = (h0.x + h1.y, h1.x + h0.y)
+      const df2 x03 = add2(h0, h1);
+      const df2 x12 = add2(pack(lane_x(h0), lane_x(h1)), pack(lane_y(h1), lane_y(h0)));
+      // top-minus-bottom part: h2 at (00, 11), h2.x + h2.y at (10, 01)
+      const dfl hs = lane_x(h2) + lane_y(h2);
+      const df2 h12 = pack(hs, hs);
+      const df2 b03 = add2(x03, h2), t03 = sub2(h2, x03);  // bottom -(x03 + h2), top h2 - x03
+      const df2 b12 = sub2(x12, h12), t12 = add2(x12, h12);
+      accb[0][c] = -lane_x(b03), acct[0][c] = lane_x(t03);
+      accb[3][c] = -lane_y(b03), acct[3][c] = lane_y(t03);
+      accb[1][c] = lane_x(b12), acct[1][c] = lane_x(t12);
+      accb[2][c] = lane_y(b12), acct[2][c] = lane_y(t12);
+    }
   }
 };
 
@@ -672,6 +685,44 @@ struct OpDiv {
   }
 };
 
+// Double-float divergence without the TALA term: the arithmetic of OpDiv with the corner
+// differences and the corner combination of the two wedges accurate, the contraction with M^-1 by
+// fused multiply-adds (add_nc / fma_nc).
+template <>
+struct OpDiv<dfl, false> {
+  static constexpr int NIN = 3, NOUT = 1;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
+  using Col = NoCol;
+  const dfl* rhat = nullptr;
+  int n_tri = 0;
+  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&Mi)[2][9],
+                                       const dfl (&dM)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][1],
+                                       dfl (&acct)[4][1], const Col&) const {
+    const dfl r = lc[4], vw6 = lc[7];
+    dfl v[2];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const dfl* M = Mi[w];
+      dfl lat(0.0), rad(0.0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dfl ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c];
+        const dfl az = add_nc(add_nc(dd[c0][c], dd[c1][c]), dd[c2][c]);
+        lat = c == 0 ? fma_nc(ax, M[0], ay * M[3]) : fma_nc(ax, M[c], fma_nc(ay, M[3 + c], lat));
+        rad = c == 0 ? az * M[6] : fma_nc(az, M[6 + c], rad);
+      }
+      v[w] = (vw6 * dM[w]) * fma_nc(r, rad, lat);
+    }
+    const dfl v01 = v[0] + v[1];
+    accb[0][0] = acct[0][0] = v[0];
+    accb[3][0] = acct[3][0] = v[1];
+    accb[1][0] = acct[1][0] = v01;
+    accb[2][0] = acct[2][0] = v01;
+  }
+};
+
 // Fine-level gradient (transpose of OpDiv): y_j += -V p(q_c) grad N_j(q_c), p(q_c) the mean of
 // the six nodal values; H[:, m] = f M^-1[m, :] (times r for m = 2), f = -vol w0 |det M| p(q_c).
 template <typename T>
@@ -705,6 +756,41 @@ struct OpGrad {
       }
     }
     combine_corners<T, 3>(X, h, accb, acct);
+  }
+};
+
+// Double-float gradient: the pressure sum at q_c (no cancellation) and the products by M^-1 with the
+// sum without the second TwoSum; the corner combination accurate.
+template <>
+struct OpGrad<dfl> {
+  static constexpr int NIN = 1, NOUT = 3;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = false;
+  using Col = NoCol;
+  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
+  __device__ __forceinline__ void cell(const dfl (&sn)[4][1], const dfl (&)[4][1], const dfl (&Mi)[2][9],
+                                       const dfl (&dM)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][3],
+                                       dfl (&acct)[4][3], const Col&) const {
+    const dfl r = lc[4], vw6 = lc[7];
+    dfl X[4][3], h[2][3];
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
+      const dfl* M = Mi[w];
+      const dfl f = (vw6 * dM[w]) * add_nc(add_nc(sn[c0][0], sn[c1][0]), sn[c2][0]);
+      const dfl fr = f * r;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const dfl h0 = f * M[c], h1 = f * M[3 + c];
+        h[w][c] = fr * M[6 + c];
+        X[c0][c] = -(h0 + h1);
+        if (w == 0) {
+          X[c1][c] = h0, X[c2][c] = h1;
+        } else {
+          X[c1][c] += h0, X[c2][c] += h1;
+        }
+      }
+    }
+    combine_corners<dfl, 3>(X, h, accb, acct);
   }
 };
 
@@ -859,6 +945,50 @@ struct OpMass {
     accb[3][0] = acct[3][0] = v1;
     accb[1][0] = acct[1][0] = v01;
     accb[2][0] = acct[2][0] = v01;
+  }
+};
+
+// Double-float diagonal (one-point, no hourglass control): sums of positive terms, so every
+// addition but the accumulation over the two wedges uses add_nc / fma_nc.
+template <>
+struct OpDiag<dfl, false> {
+  static constexpr int NIN = 1, NOUT = 3;
+  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false;
+  struct Col {
+    int t0;
+  };
+  int div_term;
+  dfl hgk;
+  const dfl* coef;  // [kDiagCoef][n_tri]
+  int n_tri;
+  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int t0) const { return Col{t0}; }
+  __device__ __forceinline__ void cell(const dfl (&)[4][1], const dfl (&)[4][1], const dfl (&)[2][9], const dfl (&dM)[2],
+                                       const dfl* lc, const dfl (&eta)[2], dfl (&accb)[4][3], dfl (&acct)[4][3],
+                                       const Col& col) const {
+    const dfl r = lc[4], vw2 = lc[5];
+    const dfl r2 = r * r, rr(r.hi + r.hi, r.lo + r.lo);  // exact doubling
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const dfl* cf = coef + col.t0 + w;
+      const dfl A = (vw2 * dM[w]) * eta[w];
+      const dfl Ar2 = A * r2, A2r = A * rr;
+      dfl AQ[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) AQ[d] = Ar2 * cf[(18 + d) * n_tri];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = kCorner[w][a];
+        const bool first = w == 0 || q == 3;  // corner 11 belongs to W1 only
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const dfl inner = fma_nc(A, cf[(3 * a + d) * n_tri], AQ[d]);
+          const dfl cr = A2r * cf[(9 + 3 * a + d) * n_tri];
+          const dfl vb = add_nc(inner, -cr), vt = add_nc(inner, cr);
+          accb[q][d] = first ? vb : add_nc(accb[q][d], vb);
+          acct[q][d] = first ? vt : add_nc(acct[q][d], vt);
+        }
+      }
+    }
   }
 };
 
