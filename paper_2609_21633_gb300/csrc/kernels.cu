@@ -90,6 +90,14 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 #ifndef TN_PREFETCH
 #define TN_PREFETCH 0
 #endif
+// FP32 A apply on paired-cell tiles (pair32.cuh) where N >= 32 (0: the square tiles), and its CTA
+// target: radial chunks halve until the grid has this many CTAs (two resident per SM)
+#ifndef TN_PAIR32
+#define TN_PAIR32 1
+#endif
+#ifndef TN_PAIR_CTA_TARGET
+#define TN_PAIR_CTA_TARGET (8 * 152)
+#endif
 template <typename T>
 struct MinBlocks {
   static constexpr int value = sizeof(T) == 8 ? TN_MINB_F64 : TN_MINB_F32;
@@ -388,7 +396,16 @@ struct OpA<dfl, false> {
 // slots of the FP32 element arithmetic, which bounds the FP32 tile kernels.
 __device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// a - b lane-wise, rounded to nearest: the packed subtraction of PTX (no intrinsic exists)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra, rb, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
@@ -1781,11 +1798,9 @@ __global__ void k_ring_fix(Dims D, RingDims RD, const T* __restrict__ ring, cons
                            int bc_out, const int* __restrict__ skip, EpiArgs<T> E) {
   if (skip && *skip) return;
   const int N = D.N, n_r = D.n_r;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int rid = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y, d = blockIdx.z;  // grid: RC x n_r x 10
+  if (rid >= RD.RC) return;
   const int64_t per_k = (int64_t)10 * RD.RC;
-  if (tid >= per_k * n_r) return;
-  const int k = (int)(tid / per_k);
-  const int d = (int)((tid % per_k) / RD.RC), rid = (int)(tid % RD.RC);
   int i, j;
   if (rid < RD.H) {
     i = (rid / (N + 1)) * RD.TI, j = rid % (N + 1);
@@ -1832,6 +1847,8 @@ __global__ void k_ring_fix(Dims D, RingDims RD, const T* __restrict__ ring, cons
   if (NOUT > 1) out1[idx] = v[NOUT > 1 ? 1 : 0];
   if (NOUT > 2) out2[idx] = v[NOUT > 2 ? 2 : 0];
 }
+
+#include "pair32.cuh"
 
 // Square tiles: MinBlocks CTAs per SM through the register cap of the launch bounds.
 template <typename T, typename Op, int TI, int TJ, int FLAGS, int EPI = EPI_NONE, int EK = TN_ETA_F32>
@@ -1930,8 +1947,7 @@ cudaError_t launch_tile(const Level& L, BC bc, Op op, const T* const* in, T* con
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       const RingDims RD = ring_dims(L.N, TI, TJ);
-      const int64_t nr = (int64_t)10 * RD.RC * L.n_r;
-      k_ring_fix<T, Op::NOUT, FLAGS, EPI><<<nblk(nr, 256), 256, 0, st>>>(D, RD, (const T*)L.ring64, in[0], i1, i2,
+      k_ring_fix<T, Op::NOUT, FLAGS, EPI><<<dim3(nblk(RD.RC, 256), L.n_r, 10), 256, 0, st>>>(D, RD, (const T*)L.ring64, in[0], i1, i2,
                                                                         out[0], o1, o2, sv, bc.in, bc.out, skip, E);
       return cudaGetLastError();
     }
@@ -1964,9 +1980,8 @@ __global__ void k_interface(Dims D, int n_groups, const int* __restrict__ gptr, 
                             const T* __restrict__ u0, const T* __restrict__ u1, const T* __restrict__ u2,
                             int bc_in, int bc_out, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= (int64_t)n_groups * D.n_r) return;
-  const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;  // grid: groups x layers
+  if (g >= n_groups) return;
   T* y[3] = {y0, y1, y2};
   const T* u[3] = {u0, u1, u2};
   const int b = gptr[g], e = gptr[g + 1];
@@ -2004,9 +2019,8 @@ __global__ void k_interface_epi(Dims D, int n_groups, const int* __restrict__ gp
                                 const T* __restrict__ x2, int bc_in, int bc_out, const int* __restrict__ skip,
                                 EpiArgs<T> E) {
   if (skip && *skip) return;
-  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (gid >= (int64_t)n_groups * D.n_r) return;
-  const int g = (int)(gid % n_groups), k = (int)(gid / n_groups);
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;  // grid: groups x layers
+  if (g >= n_groups) return;
   const T* y[3] = {t0, t1, t2};
   const T* u[3] = {x0, x1, x2};
   const int b = gptr[g], e = gptr[g + 1];
@@ -2515,10 +2529,53 @@ inline bool use_df(const Level& L) {
   return sizeof(T) == 8 && L.df && TN_WIDE_TILES && TN_HALO_FREE && L.N >= 2 * TILE;
 }
 
+// The FP32 A apply on paired-cell tiles (pair32.cuh) serves levels with N >= 32 whose three input
+// arrays start on 16-byte boundaries; the others take the square tiles.
+inline bool pair32_ok(const Level& L, const float* const* in) {
+  auto al = [](const float* p) { return ((uintptr_t)p & 15) == 0; };
+  return TN_PAIR32 && L.N >= 2 * TILE && L.ring64 && L.n_layout < (int64_t)INT32_MAX &&
+         L.n_wedges < (int64_t)INT32_MAX && al(in[0]) && al(in[1]) && al(in[2]);
+}
+
+template <bool HG, int EPI>
+cudaError_t launch_pair32(const Level& L, BC bc, const OpA<float, HG>& op, const float* const* in, float* const* out,
+                          cudaStream_t st, const int* skip, const EpiArgs<float>* epi) {
+  constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  EpiArgs<float> E{};
+  if (epi) E = *epi;
+  const Dims D = dims(L);
+  const int ntiles = (L.N / kPTI) * (L.N / kPTJ), ncells = L.n_r - 1;
+  int kc = ncells;
+  while (kc > kPMaxKc || (kc > TN_KC_MIN && (int64_t)ntiles * 10 * ((ncells + kc - 1) / kc) < TN_PAIR_CTA_TARGET))
+    kc = (kc + 1) / 2;
+  const dim3 grid(ntiles, (ncells + kc - 1) / kc, 10);
+  const EtaView<float> ev = etav<float>(L);
+  float4* const ring = reinterpret_cast<float4*>(L.ring64);  // 16 floats per 12 doubles of the FP64 layout
+#define TN_PAIR_LAUNCH(EKv)                                                                                    \
+  k_pair32<HG, F, EPI, EKv><<<grid, kPThreads, kPSmemBytes, st>>>(D, op, in[0], in[1], in[2], out[0], out[1],   \
+                                                                 out[2], L.geo32, L.lay32, ev, L.s32, bc.in,     \
+                                                                 bc.out, kc, skip, E, ring)
+  if (ev.kind == TN_ETA_BF16) TN_PAIR_LAUNCH(TN_ETA_BF16);
+  else if (ev.kind == TN_ETA_F16) TN_PAIR_LAUNCH(TN_ETA_F16);
+  else TN_PAIR_LAUNCH(TN_ETA_F32);
+#undef TN_PAIR_LAUNCH
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const RingDims RD = ring_dims(L.N, kPTI, kPTJ);
+  k_ring4_fix<F, EPI><<<dim3(nblk(RD.RC, 256), L.n_r, 10), 256, 0, st>>>(D, RD, ring, in[0], in[1], in[2], out[0], out[1], out[2], L.s32,
+                                                      bc.in, bc.out, skip, E);
+  return cudaGetLastError();
+}
+
 template <typename T, bool HG>
 cudaError_t apply_A_hg(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                        const int* skip) {
   constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
+  if constexpr (sizeof(T) == 4) {
+    if (pair32_ok(L, u))
+      return launch_pair32<HG, EPI_NONE>(L, bc, OpA<float, HG>{div_term, (float)hg_coef(L, div_term)}, u, y, st, skip,
+                                         nullptr);
+  }
   if constexpr (sizeof(T) == 8) {
     if (use_df<T>(L)) {
       OpA<dfl, HG> op{div_term, dfl(hg_coef(L, div_term))};
@@ -2539,6 +2596,8 @@ cudaError_t apply_A_q2_epi(const Level& L, BC bc, int div_term, int epi, const T
                            T* const* t, cudaStream_t st, const int* skip);
 // Shared-memory opt-ins of the OpA2 tile kernels (see prepare_tile_kernels).
 cudaError_t prepare_tile_kernels_q2();
+// Shared-memory opt-ins of the FP32 paired-cell A kernels (defined with their launchers).
+cudaError_t prepare_tile_kernels_f32();
 
 template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
@@ -2566,6 +2625,17 @@ cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T
       }
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    if (pair32_ok(L, in)) {
+      const OpA<float, HG> o32{div_term, (float)hg_coef(L, div_term)};
+      switch (epi) {
+        case EPI_RESID: return launch_pair32<HG, EPI_RESID>(L, bc, o32, in, t, st, skip, &E);
+        case EPI_CHEB1: return launch_pair32<HG, EPI_CHEB1>(L, bc, o32, in, t, st, skip, &E);
+        case EPI_CHEB2: return launch_pair32<HG, EPI_CHEB2>(L, bc, o32, in, t, st, skip, &E);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
   OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
   using Op = OpA<T, HG>;
   switch (epi) {
@@ -2585,7 +2655,7 @@ cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, con
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)L.n_groups * L.n_r;
   if (n == 0) return cudaSuccess;
-  const unsigned nb = nblk(n, 128);
+  const dim3 nb(nblk(L.n_groups, 128), L.n_r);
   const Dims D = dims(L);
 #define TN_IEPI(EP)                                                                                             \
   k_interface_epi<T, EP><<<nb, 128, 0, st>>>(D, L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), t[0], t[1], t[2], \
@@ -2719,7 +2789,8 @@ cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* cons
   const T* u0 = u ? u[0] : nullptr;
   const T* u1 = u ? u[1] : nullptr;
   const T* u2 = u ? u[2] : nullptr;
-  k_interface<T><<<nblk(n, 128), 128, 0, st>>>(dims(L), L.n_groups, L.grp_ptr, L.grp_off, Tab<T>::gs(L), ncomp, mode,
+  k_interface<T><<<dim3(nblk(L.n_groups, 128), L.n_r), 128, 0, st>>>(dims(L), L.n_groups, L.grp_ptr, L.grp_off,
+                                                                   Tab<T>::gs(L), ncomp, mode,
                                                y[0], y1, y2, u0, u1, u2, bc.in, bc.out, skip);
   return cudaGetLastError();
 }
@@ -2924,7 +2995,7 @@ cudaError_t prepare_energy_kernels() {
 }
 
 cudaError_t prepare_tile_kernels() {
-  const cudaError_t e[6] = {set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
+  const cudaError_t e[7] = {prepare_tile_kernels_f32(), set_wide_attrs<OpA<double, false>>(), set_wide_attrs<OpA<double, true>>(),
                             set_df_attrs<OpA<dfl, false>>(), set_df_attrs<OpA<dfl, true>>(),
                             prepare_tile_kernels_q2(), prepare_energy_kernels()};
   for (cudaError_t x : e)
@@ -2934,6 +3005,28 @@ cudaError_t prepare_tile_kernels() {
 #endif
 #if TN_PART == 0 || TN_PART == 3
 TN_INST_A(float)
+template <bool HG, int EPI, int EK>
+cudaError_t set_pair32_attr() {
+  return cudaFuncSetAttribute(k_pair32<HG, PROJ_IN | PROJ_OUT | ADD_ID, EPI, EK>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmemBytes);
+}
+template <bool HG, int EPI>
+cudaError_t set_pair32_attrs() {
+  const cudaError_t e[3] = {set_pair32_attr<HG, EPI, TN_ETA_F32>(), set_pair32_attr<HG, EPI, TN_ETA_BF16>(),
+                            set_pair32_attr<HG, EPI, TN_ETA_F16>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+cudaError_t prepare_tile_kernels_f32() {
+  const cudaError_t e[8] = {set_pair32_attrs<false, EPI_NONE>(), set_pair32_attrs<false, EPI_RESID>(),
+                            set_pair32_attrs<false, EPI_CHEB1>(), set_pair32_attrs<false, EPI_CHEB2>(),
+                            set_pair32_attrs<true, EPI_NONE>(),  set_pair32_attrs<true, EPI_RESID>(),
+                            set_pair32_attrs<true, EPI_CHEB1>(),  set_pair32_attrs<true, EPI_CHEB2>()};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
 #endif
 #undef TN_INST_A
 

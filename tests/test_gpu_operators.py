@@ -235,6 +235,41 @@ def test_apply_A_and_diag_f32_with_16bit_viscosity(tn, kind, unit):
     c.close()
 
 
+@pytest.mark.parametrize("level,n_r,bc,kappa,div_term,kind", [
+    (5, 17, "free/free", 0.0, True, 0), (5, 27, "noslip/free", 0.0, True, 0), (6, 9, "noslip/noslip", 0.0, False, 0),
+    (5, 17, "free/free", 0.3, True, 0), (6, 11, "noslip/free", 0.3, False, 0), (5, 9, "free/free", 0.0, True, 1),
+    (5, 19, "noslip/free", 0.3, True, 2)])
+def test_apply_A_f32_paired_tiles(tn, level, n_r, bc, kappa, div_term, kind):
+    """FP32 A on levels with N >= 32 (two cells per thread, tile lines through the ring buffer,
+    radial chunks with a ragged last one when n_r - 1 is not a multiple of the chunk) against the
+    oracle; inputs moved off the 16-byte boundary take the square tiles, which agree to FP32
+    rounding."""
+    c = Case(tn, level, n_r, BCS[bc], div_term=div_term, eta_storage=kind, hg_kappa=kappa)
+    N = 2 ** level
+    eta = c.eta if kind == 0 else c.map.wedges_from_layout(
+        stored_viscosity(c.map.wedges_to_layout(c.eta), N, n_r, kind))
+    u = c.vec(31)
+    want = O.apply_A_constrained(c.om, eta, u, c.P, div_term=div_term, kappa=kappa)
+    ud = [c.dev(u[i], torch.float32) for i in range(3)]
+    y = c.zeros(dtype=torch.float32)
+    tn.tn_apply_A(c.m, 0, ud, y)
+    got = np.stack([c.host(t) for t in y])
+    err = max_rel(got, want)
+    # the same input one element past a 16-byte boundary
+    n = c.info["n_layout"]
+    buf = [torch.zeros(n + 4, device="cuda", dtype=torch.float32) for _ in range(3)]
+    for b, x in zip(buf, ud):
+        b[1:n + 1] = x
+    y2 = c.zeros(dtype=torch.float32)
+    tn.tn_apply_A(c.m, 0, [b[1:n + 1] for b in buf], y2)
+    got2 = np.stack([c.host(t) for t in y2])
+    print(f"level {level} / {n_r} kappa {kappa} kind {kind}: paired {err:.2e}, square tiles {max_rel(got2, want):.2e}")
+    assert err <= TOL32
+    assert max_rel(got2, want) <= TOL32
+    assert max_rel(got, got2) <= TOL32
+    c.close()
+
+
 @pytest.mark.parametrize("level,n_r,bc", [(2, 5, "free/free"), (3, 9, "noslip/free"), (4, 27, "free/free"),
                                           (5, 9, "free/free"), (5, 17, "noslip/free")])
 def test_apply_B_and_BT_f64(tn, level, n_r, bc):
