@@ -56,7 +56,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.laydf, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64, L.bw64, L.rhat64, L.rhat32, L.rhatdf};
+                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64, L.grp_dij, L.bw64, L.rhat64, L.rhat32, L.rhatdf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -193,7 +193,15 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
   }
   {
     const int64_t nring = ring_buffer_entries(L.N, L.n_r);
-    if (nring > 0) chk(cudaMalloc((void**)&L.ring64, sizeof(double) * nring));
+    if (nring > 0) {
+      chk(cudaMalloc((void**)&L.ring64, sizeof(double) * nring));
+      std::vector<int4> dij(goff.size());
+      for (size_t q = 0; q < goff.size(); ++q) {
+        const int64_t d = goff[q] / L.diamond_stride, r = goff[q] % L.diamond_stride;
+        dij[q] = make_int4((int)d, (int)(r / L.P), (int)(r % L.P), 0);
+      }
+      chk(upload(L.grp_dij, dij));
+    }
   }
   chk(cudaMalloc((void**)&L.scr64, sizeof(double) * L.n_layout));
   chk(cudaMalloc((void**)&L.scr32, sizeof(float) * L.n_layout));

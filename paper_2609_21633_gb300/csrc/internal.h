@@ -64,8 +64,11 @@ struct Level {
   float* dcoefdf = nullptr;  // the same table as double-float pairs (hi, lo)
   int dcoef_div = -1;
   // Tile-line partial sums of the FP64 halo-free tile kernels (levels with N >= 32):
-  // [4 slots][3 components][n_r][10][tile-line nodes of a diamond layer].
+  // [4 slots][3 components][n_r][10][tile-line nodes of a diamond layer]; the FP32 paired-cell
+  // tiles use the same allocation as float4 entries [4 slots][n_r][10][tile-line nodes].
   double* ring64 = nullptr;
+  // (diamond, i, j, 0) of every interface copy (grp_off order), levels with a ring buffer.
+  int4* grp_dij = nullptr;
   uint16_t* eta16 = nullptr;
   float* eta_cs = nullptr;
   // Scratch scalar field in this level's node layout (B / B^T intermediate).

@@ -96,7 +96,7 @@ inline unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); 
 #define TN_PAIR32 1
 #endif
 #ifndef TN_PAIR_CTA_TARGET
-#define TN_PAIR_CTA_TARGET (8 * 152)
+#define TN_PAIR_CTA_TARGET (16 * 152)
 #endif
 template <typename T>
 struct MinBlocks {
@@ -2533,7 +2533,7 @@ inline bool use_df(const Level& L) {
 // arrays start on 16-byte boundaries; the others take the square tiles.
 inline bool pair32_ok(const Level& L, const float* const* in) {
   auto al = [](const float* p) { return ((uintptr_t)p & 15) == 0; };
-  return TN_PAIR32 && L.N >= 2 * TILE && L.ring64 && L.n_layout < (int64_t)INT32_MAX &&
+  return TN_PAIR32 && L.quad == 1 && L.N >= 2 * TILE && L.ring64 && L.grp_dij && L.n_layout < (int64_t)INT32_MAX &&
          L.n_wedges < (int64_t)INT32_MAX && al(in[0]) && al(in[1]) && al(in[2]);
 }
 
@@ -2562,8 +2562,13 @@ cudaError_t launch_pair32(const Level& L, BC bc, const OpA<float, HG>& op, const
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const RingDims RD = ring_dims(L.N, kPTI, kPTJ);
-  k_ring4_fix<F, EPI><<<dim3(nblk(RD.RC, 256), L.n_r, 10), 256, 0, st>>>(D, RD, ring, in[0], in[1], in[2], out[0], out[1], out[2], L.s32,
-                                                      bc.in, bc.out, skip, E);
+  k_ring4_fix<F, EPI><<<dim3(nblk(RD.RC, 256), L.n_r, 10), 256, 0, st>>>(D, RD, ring, in[0], in[1], in[2], out[0],
+                                                                        out[1], out[2], L.s32, bc.in, bc.out, skip, E);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || L.n_groups == 0) return e;
+  k_ring4_edges<EPI><<<dim3(nblk(L.n_groups, 128), L.n_r), 128, 0, st>>>(
+      D, RD, L.n_groups, L.grp_ptr, L.grp_off, L.grp_dij, L.grp_s32, ring, in[0], in[1], in[2], out[0], out[1], out[2],
+      bc.in, bc.out, skip, E);
   return cudaGetLastError();
 }
 
@@ -2571,11 +2576,6 @@ template <typename T, bool HG>
 cudaError_t apply_A_hg(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                        const int* skip) {
   constexpr int F = PROJ_IN | PROJ_OUT | ADD_ID;
-  if constexpr (sizeof(T) == 4) {
-    if (pair32_ok(L, u))
-      return launch_pair32<HG, EPI_NONE>(L, bc, OpA<float, HG>{div_term, (float)hg_coef(L, div_term)}, u, y, st, skip,
-                                         nullptr);
-  }
   if constexpr (sizeof(T) == 8) {
     if (use_df<T>(L)) {
       OpA<dfl, HG> op{div_term, dfl(hg_coef(L, div_term))};
@@ -2599,9 +2599,28 @@ cudaError_t prepare_tile_kernels_q2();
 // Shared-memory opt-ins of the FP32 paired-cell A kernels (defined with their launchers).
 cudaError_t prepare_tile_kernels_f32();
 
+// The FP32 A apply on paired-cell tiles, interface sums included (pair32.cuh).
+template <bool HG>
+cudaError_t pair32_apply(const Level& L, BC bc, int div_term, int epi, const float* const* in, float* const* out,
+                         cudaStream_t st, const int* skip, const EpiArgs<float>* E) {
+  const OpA<float, HG> op{div_term, (float)hg_coef(L, div_term)};
+  switch (epi) {
+    case EPI_NONE: return launch_pair32<HG, EPI_NONE>(L, bc, op, in, out, st, skip, nullptr);
+    case EPI_RESID: return launch_pair32<HG, EPI_RESID>(L, bc, op, in, out, st, skip, E);
+    case EPI_CHEB1: return launch_pair32<HG, EPI_CHEB1>(L, bc, op, in, out, st, skip, E);
+    case EPI_CHEB2: return launch_pair32<HG, EPI_CHEB2>(L, bc, op, in, out, st, skip, E);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_apply_A(const Level& L, BC bc, int div_term, const T* const* u, T* const* y, cudaStream_t st,
                            const int* skip) {
+  if constexpr (sizeof(T) == 4) {
+    if (pair32_ok(L, u))
+      return L.hg_kappa > 0 ? pair32_apply<true>(L, bc, div_term, EPI_NONE, u, y, st, skip, nullptr)
+                            : pair32_apply<false>(L, bc, div_term, EPI_NONE, u, y, st, skip, nullptr);
+  }
   cudaError_t e = L.quad == 2      ? apply_A_q2<T>(L, bc, div_term, u, y, st, skip)
                   : L.hg_kappa > 0 ? apply_A_hg<T, true>(L, bc, div_term, u, y, st, skip)
                                    : apply_A_hg<T, false>(L, bc, div_term, u, y, st, skip);
@@ -2625,17 +2644,6 @@ cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T
       }
     }
   }
-  if constexpr (sizeof(T) == 4) {
-    if (pair32_ok(L, in)) {
-      const OpA<float, HG> o32{div_term, (float)hg_coef(L, div_term)};
-      switch (epi) {
-        case EPI_RESID: return launch_pair32<HG, EPI_RESID>(L, bc, o32, in, t, st, skip, &E);
-        case EPI_CHEB1: return launch_pair32<HG, EPI_CHEB1>(L, bc, o32, in, t, st, skip, &E);
-        case EPI_CHEB2: return launch_pair32<HG, EPI_CHEB2>(L, bc, o32, in, t, st, skip, &E);
-        default: return cudaErrorInvalidValue;
-      }
-    }
-  }
   OpA<T, HG> op{div_term, (T)hg_coef(L, div_term)};
   using Op = OpA<T, HG>;
   switch (epi) {
@@ -2649,6 +2657,13 @@ cudaError_t apply_A_epi_hg(const Level& L, BC bc, int div_term, int epi, const T
 template <typename T>
 cudaError_t launch_apply_A_epi(const Level& L, BC bc, int div_term, int epi, const T* const* in, const EpiArgs<T>& E,
                                T* const* t, cudaStream_t st, const int* skip) {
+  if constexpr (sizeof(T) == 4) {
+    if (pair32_ok(L, in)) {
+      if (epi != EPI_RESID && epi != EPI_CHEB1 && epi != EPI_CHEB2) return cudaErrorInvalidValue;
+      return L.hg_kappa > 0 ? pair32_apply<true>(L, bc, div_term, epi, in, t, st, skip, &E)
+                            : pair32_apply<false>(L, bc, div_term, epi, in, t, st, skip, &E);
+    }
+  }
   cudaError_t e = L.quad == 2      ? apply_A_q2_epi<T>(L, bc, div_term, epi, in, E, t, st, skip)
                   : L.hg_kappa > 0 ? apply_A_epi_hg<T, true>(L, bc, div_term, epi, in, E, t, st, skip)
                                    : apply_A_epi_hg<T, false>(L, bc, div_term, epi, in, E, t, st, skip);

@@ -92,9 +92,11 @@ __device__ __forceinline__ void pair_cell(const float2 (&tp)[4][3], const float2
 #pragma unroll
       for (int x = 0; x < 3; ++x) G[c][x] = fma2(ax, M[x], fma2(ay, M[3 + x], mul2(az, mr[x])));
       if constexpr (HG) {
-        const float2 k9 = p2(lc.z, lc.z), a3 = mul2(az, p2(1.f / 3.f, 1.f / 3.f));
-        al1[c] = sub2(sub2(D1[HG ? w : 0][c], a3), mul2(k9, sub2(add2(ax, ax), ay)));
-        al2[c] = sub2(sub2(D2[HG ? w : 0][c], a3), mul2(k9, sub2(add2(ay, ay), ax)));
+        // alpha_1 = (d_1 - a_zeta / 3) - k9 (2 a_xi - a_eta), alpha_2 = (d_2 - a_zeta / 3) - k9 (2 a_eta - a_xi)
+        const float2 nk9 = p2(-lc.z, -lc.z), a3 = mul2(az, p2(1.f / 3.f, 1.f / 3.f));
+        const float2 dl = sub2(ax, ay);
+        al1[c] = fma2(nk9, add2(ax, dl), sub2(D1[HG ? w : 0][c], a3));
+        al2[c] = fma2(nk9, sub2(ay, dl), sub2(D2[HG ? w : 0][c], a3));
       }
     }
     const float2 ve = mul2(mul2(vw2, gc[(12 * w + 9) * kPThreads]), eta[w]);
@@ -109,11 +111,11 @@ __device__ __forceinline__ void pair_cell(const float2 (&tp)[4][3], const float2
     S[0][1] = S[1][0] = mul2(ve, add2(G[0][1], G[1][0]));
     S[0][2] = S[2][0] = mul2(ve, add2(G[0][2], G[2][0]));
     S[1][2] = S[2][1] = mul2(ve, add2(G[1][2], G[2][1]));
-    float2 ek = p2(0.f, 0.f), e3 = p2(0.f, 0.f);
+    float2 nek = p2(0.f, 0.f), e3 = p2(0.f, 0.f);  // -eps k9, eps / 3
     if constexpr (HG) {
       const float2 eps = mul2(mul2(p2(hgk, hgk), eta[w]),
                               fma2(vw2, gc[(12 * w + 10) * kPThreads], mul2(p2(lc.w, lc.w), gc[(12 * w + 11) * kPThreads])));
-      ek = mul2(eps, p2(lc.z, lc.z)), e3 = mul2(eps, p2(1.f / 3.f, 1.f / 3.f));
+      nek = mul2(eps, p2(-lc.z, -lc.z)), e3 = mul2(eps, p2(1.f / 3.f, 1.f / 3.f));
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -121,10 +123,11 @@ __device__ __forceinline__ void pair_cell(const float2 (&tp)[4][3], const float2
       float2 h1 = fma2(S[c][0], M[3], fma2(S[c][1], M[4], mul2(S[c][2], M[5])));
       const float2 h2 = fma2(S[c][0], mr[0], fma2(S[c][1], mr[1], mul2(S[c][2], mr[2])));
       if constexpr (HG) {
+        // b_1 = 2 alpha_1 - alpha_2, b_2 = 2 alpha_2 - alpha_1 (b_1 + b_2 = alpha_1 + alpha_2)
         const float2 b1 = sub2(add2(al1[c], al1[c]), al2[c]), b2 = sub2(add2(al2[c], al2[c]), al1[c]);
-        h0 = sub2(h0, mul2(ek, b1)), h1 = sub2(h1, mul2(ek, b2));
-        const float2 v1 = mul2(e3, b1), v2 = mul2(e3, b2);
-        Y[w][0][c] = sub2(h2, add2(v1, v2)), Y[w][HG ? 1 : 0][c] = add2(h2, v1), Y[w][HG ? 2 : 0][c] = add2(h2, v2);
+        h0 = fma2(nek, b1, h0), h1 = fma2(nek, b2, h1);
+        Y[w][0][c] = sub2(h2, mul2(e3, add2(al1[c], al2[c])));
+        Y[w][HG ? 1 : 0][c] = fma2(e3, b1, h2), Y[w][HG ? 2 : 0][c] = fma2(e3, b2, h2);
       } else {
         Y[w][0][c] = h2;
       }
@@ -327,6 +330,10 @@ __global__ void __launch_bounds__(kPThreads, 2)
     }
     out0[idx] = v[0], out1[idx] = v[1], out2[idx] = v[2];
   };
+  auto store4 = [&](int k, int idx, const float4& v4) {
+    float v[3] = {v4.x, v4.y, v4.z};
+    store_node(k, idx, v);
+  };
   auto ring_put = [&](int k, int slot, int rid, const float4& v) { ring[ring4_at(RD, n_r, slot, k, d, rid)] = v; };
   // node layer kn from the corner totals of this thread's two cells (all radial contributions in):
   // sum the four cells around every node, store the nodes inside the tile, ring the tile lines
@@ -362,12 +369,8 @@ __global__ void __launch_bounds__(kPThreads, 2)
     }
     const int ok = on0 + kn * LS;
     if (lane > 0) {
-      if (w > 0) {
-        float v[3] = {own0.x, own0.y, own0.z};
-        store_node(kn, ok, v);
-      }
-      float v[3] = {own1.x, own1.y, own1.z};
-      store_node(kn, ok + P, v);
+      if (w > 0) store4(kn, ok, own0);
+      store4(kn, ok + P, own1);
     } else {  // column j0
       if (w > 0) ring_put(kn, 1, rcol0, own0);
       ring_put(kn, 1, rcol0 + 1, own1);
@@ -430,8 +433,71 @@ __global__ void __launch_bounds__(kPThreads, 2)
   cp_async_wait<0>();
 }
 
-// Sums the ring partials of k_pair32 and finishes the tile-line nodes (as k_ring_fix does for the
-// FP64 halo-free tiles).
+// Sum of the ring partials of k_pair32 at tile-line node (i, j) of diamond d, node layer k: one
+// partial per tile that has the node on its edge (slot 2 bi + bj; no tile beyond the diamond).
+__device__ __forceinline__ void ring4_sum(const RingDims& RD, int N, int n_r, const float4* __restrict__ ring, int k,
+                                          int d, int i, int j, float (&v)[3]) {
+  const int rid = ring_index(RD, N, i, j);
+  const bool on_h = i % RD.TI == 0, on_v = j % RD.TJ == 0;
+  for (int bi = 0; bi < 2; ++bi) {
+    if (bi == 1 && !on_h) break;
+    if (on_h && ((bi == 0 && i == 0) || (bi == 1 && i == N))) continue;
+    for (int bj = 0; bj < 2; ++bj) {
+      if (bj == 1 && !on_v) break;
+      if (on_v && ((bj == 0 && j == 0) || (bj == 1 && j == N))) continue;
+      const float4 x = ring[ring4_at(RD, n_r, 2 * bi + bj, k, d, rid)];
+      v[0] += x.x, v[1] += x.y, v[2] += x.z;
+    }
+  }
+}
+
+// Diamond-edge nodes of the paired-cell tiles, one thread per interface group g (the copies of one
+// lattice point) and node layer k: the ring partials of every copy summed, the boundary rows
+// projected and (I - P) u added once, then the value -- or the fused vector update -- at every
+// copy (what k_ring_fix and k_interface do in two passes for the other tiles).
+template <int EPI>
+__global__ void k_ring4_edges(Dims D, RingDims RD, int n_groups, const int* __restrict__ gptr,
+                              const int64_t* __restrict__ goff, const int4* __restrict__ gdij,
+                              const float* __restrict__ gs, const float4* __restrict__ ring,
+                              const float* __restrict__ in0, const float* __restrict__ in1,
+                              const float* __restrict__ in2, float* __restrict__ out0, float* __restrict__ out1,
+                              float* __restrict__ out2, int bc_in, int bc_out, const int* __restrict__ skip,
+                              EpiArgs<float> E) {
+  if (skip && *skip) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;  // grid: groups x layers
+  if (g >= n_groups) return;
+  const int N = D.N, n_r = D.n_r;
+  const int b = gptr[g], e = gptr[g + 1];
+  float v[3] = {0.f, 0.f, 0.f};
+  for (int q = b; q < e; ++q) {
+    const int4 c = gdij[q];
+    ring4_sum(RD, N, n_r, ring, k, c.x, c.y, c.z, v);
+  }
+  const int lo = k * (int)D.layer_stride;
+  if (k == 0 || k == n_r - 1) {
+    const int bc = k == 0 ? bc_in : bc_out;
+    const int o = (int)goff[b] + lo;
+    const float w[3] = {in0[o], in1[o], in2[o]};
+    if (bc == TN_BC_NOSLIP) {
+      for (int c = 0; c < 3; ++c) v[c] = w[c];
+    } else {
+      const float s[3] = {gs[g], gs[n_groups + g], gs[2 * n_groups + g]};
+      const float dv = v[0] * s[0] + v[1] * s[1] + v[2] * s[2], dw = w[0] * s[0] + w[1] * s[1] + w[2] * s[2];
+      for (int c = 0; c < 3; ++c) v[c] += (dw - dv) * s[c];
+    }
+  }
+  for (int q = b; q < e; ++q) {
+    const int o = (int)goff[q] + lo;
+    if (EPI != EPI_NONE) {
+      epilogue<float, EPI>(E, in0, in1, in2, o, v);
+    } else {
+      out0[o] = v[0], out1[o] = v[1], out2[o] = v[2];
+    }
+  }
+}
+
+// Sums the ring partials of k_pair32 and finishes the tile-line nodes inside the diamond (as
+// k_ring_fix does for the FP64 halo-free tiles); the diamond-edge nodes are k_ring4_edges'.
 template <int FLAGS, int EPI>
 __global__ void k_ring4_fix(Dims D, RingDims RD, const float4* __restrict__ ring, const float* __restrict__ in0,
                             const float* __restrict__ in1, const float* __restrict__ in2, float* __restrict__ out0,
@@ -450,33 +516,23 @@ __global__ void k_ring4_fix(Dims D, RingDims RD, const float4* __restrict__ ring
     j = (r2 / per) * RD.TJ;
     i = (t / (RD.TI - 1)) * RD.TI + 1 + t % (RD.TI - 1);
   }
-  const bool on_h = i % RD.TI == 0, on_v = j % RD.TJ == 0;
+  if (i == 0 || i == N || j == 0 || j == N) return;  // diamond edge
   float v[3] = {0.f, 0.f, 0.f};
-  for (int bi = 0; bi < 2; ++bi) {
-    if (bi == 1 && !on_h) break;
-    if (on_h && ((bi == 0 && i == 0) || (bi == 1 && i == N))) continue;  // no tile there
-    for (int bj = 0; bj < 2; ++bj) {
-      if (bj == 1 && !on_v) break;
-      if (on_v && ((bj == 0 && j == 0) || (bj == 1 && j == N))) continue;
-      const float4 x = ring[ring4_at(RD, n_r, 2 * bi + bj, k, d, rid)];
-      v[0] += x.x, v[1] += x.y, v[2] += x.z;
-    }
-  }
+  ring4_sum(RD, N, n_r, ring, k, d, i, j, v);
   const int M = N + 1;
   const int idx = (int)(d * D.diamond_stride) + k * (int)D.layer_stride + i * D.P + j;
   const int64_t so = ((int64_t)d * M + i) * D.P + j;
-  const bool shared = i == 0 || i == N || j == 0 || j == N;
   if ((FLAGS & PROJ_OUT) && (k == 0 || k == n_r - 1)) {
     const int bc = k == 0 ? bc_in : bc_out;
     project_vec(v, svec, so, D.n_lat_layout, bc);
-    if ((FLAGS & ADD_ID) && !shared) {
+    if (FLAGS & ADD_ID) {
       float uu[3] = {in0[idx], in1[idx], in2[idx]};
       float pu[3] = {uu[0], uu[1], uu[2]};
       project_vec(pu, svec, so, D.n_lat_layout, bc);
       for (int c = 0; c < 3; ++c) v[c] += uu[c] - pu[c];
     }
   }
-  if (EPI != EPI_NONE && !shared) {
+  if (EPI != EPI_NONE) {
     epilogue<float, EPI>(E, in0, in1, in2, idx, v);
     return;
   }
