@@ -56,7 +56,7 @@ std::vector<float> to_f32(const std::vector<T>& v) {
 void free_level(Level& L) {
   void* ptrs[] = {L.geo64, L.geo32, L.lay64, L.lay32, L.laydf, L.s64,   L.s32,   L.grp_ptr, L.grp_off, L.grp_s64,
                   L.grp_s32, L.owned, L.eta64, L.eta32, L.eta16, L.eta_cs, L.scr64, L.scr32, L.wmask, L.rad64,
-                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.ring64, L.grp_dij, L.bw64, L.rhat64, L.rhat32, L.rhatdf};
+                  L.rad32, L.dcoef64, L.dcoef32, L.dcoefdf, L.dcoefdf2, L.ring64, L.grp_dij, L.bw64, L.rhat64, L.rhat32, L.rhatdf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = Level();
@@ -147,7 +147,18 @@ tn_status create_level(Level& L, int l, int nr, double r_in, double r_out, int e
     const std::vector<double> dc = diag_factors(geo, L.n_tri, div_term);
     chk(upload(L.dcoef64, dc));
     chk(upload(L.dcoef32, to_f32(dc)));
-    chk(upload(L.dcoefdf, to_df(dc)));
+    const std::vector<float> dcf = to_df(dc);
+    chk(upload(L.dcoefdf, dcf));
+    {
+      const int64_t nt = L.n_tri, np = nt / 2;
+      std::vector<float4> d2((size_t)kDiagCoef * np);
+      for (int q = 0; q < kDiagCoef; ++q)
+        for (int64_t pp = 0; pp < np; ++pp) {
+          const size_t a = 2 * (size_t)(q * nt + 2 * pp), b = a + 2;
+          d2[(size_t)q * np + pp] = make_float4(dcf[a], dcf[b], dcf[a + 1], dcf[b + 1]);
+        }
+      chk(upload(L.dcoefdf2, d2));
+    }
     L.dcoef_div = div_term;
   }
   chk(upload(L.lay64, lay));

@@ -62,6 +62,9 @@ struct Level {
   double* dcoef64 = nullptr;
   float* dcoef32 = nullptr;
   float* dcoefdf = nullptr;  // the same table as double-float pairs (hi, lo)
+  // ... and per cell (the two triangles t = 2 p, 2 p + 1 of a lateral cell): [q][n_tri / 2] float4
+  // (hi of t, hi of t + 1, lo of t, lo of t + 1), the lanes of the packed double-float diagonal
+  float4* dcoefdf2 = nullptr;
   int dcoef_div = -1;
   // Tile-line partial sums of the FP64 halo-free tile kernels (levels with N >= 32):
   // [4 slots][3 components][n_r][10][tile-line nodes of a diamond layer]; the FP32 paired-cell

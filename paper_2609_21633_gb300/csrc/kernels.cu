@@ -704,37 +704,44 @@ struct OpDiv {
 
 // Double-float divergence without the TALA term: the arithmetic of OpDiv with the corner
 // differences and the corner combination of the two wedges accurate, the contraction with M^-1 by
-// fused multiply-adds (add_nc / fma_nc).
+// fused multiply-adds (add_nc / fma_nc), the two wedges in the lanes of packed double-floats.
 template <>
 struct OpDiv<dfl, false> {
   static constexpr int NIN = 3, NOUT = 1;
   static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
-  using Col = NoCol;
+  struct Col {
+    df2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
+  };
   const dfl* rhat = nullptr;
   int n_tri = 0;
-  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
-  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&Mi)[2][9],
-                                       const dfl (&dM)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][1],
-                                       dfl (&acct)[4][1], const Col&) const {
-    const dfl r = lc[4], vw6 = lc[7];
-    dfl v[2];
+  __device__ __forceinline__ Col column(const dfl (&Mi)[2][9], const dfl (&dM)[2], int) const {
+    Col c;
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
-      const dfl* M = Mi[w];
-      dfl lat(0.0), rad(0.0);
+    for (int q = 0; q < 9; ++q) c.M[q] = pack(Mi[0][q], Mi[1][q]);
+    c.dM = pack(dM[0], dM[1]);
+    return c;
+  }
+  // the two wedges in the lanes of packed double-floats (x = W0, y = W1), corner pairs as in
+  // OpA<dfl, false>: a_xi = s_10 - s_00 | s_01 - s_11, a_eta = s_01 - s_00 | s_10 - s_11
+  __device__ __forceinline__ void cell(const dfl (&s)[4][3], const dfl (&dd)[4][3], const dfl (&)[2][9],
+                                       const dfl (&)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][1],
+                                       dfl (&acct)[4][1], const Col& col) const {
+    const df2 r = pack(lc[4], lc[4]), vw6 = pack(lc[7], lc[7]);
+    const df2* M = col.M;
+    df2 lat, rad;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const dfl ax = s[c1][c] - s[c0][c], ay = s[c2][c] - s[c0][c];
-        const dfl az = add_nc(add_nc(dd[c0][c], dd[c1][c]), dd[c2][c]);
-        lat = c == 0 ? fma_nc(ax, M[0], ay * M[3]) : fma_nc(ax, M[c], fma_nc(ay, M[3 + c], lat));
-        rad = c == 0 ? az * M[6] : fma_nc(az, M[6 + c], rad);
-      }
-      v[w] = (vw6 * dM[w]) * fma_nc(r, rad, lat);
+    for (int c = 0; c < 3; ++c) {
+      const df2 s0 = pack(s[0][c], s[3][c]), s1 = pack(s[1][c], s[2][c]), s2 = pack(s[2][c], s[1][c]);
+      const df2 ax = sub2(s1, s0), ay = sub2(s2, s0);
+      const dfl d12 = add_nc(dd[1][c], dd[2][c]);
+      const df2 az = add_nc2(pack(dd[0][c], dd[3][c]), pack(d12, d12));
+      lat = c == 0 ? fma_nc2(ax, M[0], mul2(ay, M[3])) : fma_nc2(ax, M[c], fma_nc2(ay, M[3 + c], lat));
+      rad = c == 0 ? mul2(az, M[6]) : fma_nc2(az, M[6 + c], rad);
     }
-    const dfl v01 = v[0] + v[1];
-    accb[0][0] = acct[0][0] = v[0];
-    accb[3][0] = acct[3][0] = v[1];
+    const df2 v = mul2(mul2(vw6, col.dM), fma_nc2(r, rad, lat));
+    const dfl v01 = lane_x(v) + lane_y(v);
+    accb[0][0] = acct[0][0] = lane_x(v);
+    accb[3][0] = acct[3][0] = lane_y(v);
     accb[1][0] = acct[1][0] = v01;
     accb[2][0] = acct[2][0] = v01;
   }
@@ -777,37 +784,45 @@ struct OpGrad {
 };
 
 // Double-float gradient: the pressure sum at q_c (no cancellation) and the products by M^-1 with the
-// sum without the second TwoSum; the corner combination accurate.
+// sum without the second TwoSum; the corner combination accurate; the two wedges in the lanes of
+// packed double-floats.
 template <>
 struct OpGrad<dfl> {
   static constexpr int NIN = 1, NOUT = 3;
   static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = false;
-  using Col = NoCol;
-  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int) const { return Col{}; }
-  __device__ __forceinline__ void cell(const dfl (&sn)[4][1], const dfl (&)[4][1], const dfl (&Mi)[2][9],
-                                       const dfl (&dM)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][3],
-                                       dfl (&acct)[4][3], const Col&) const {
-    const dfl r = lc[4], vw6 = lc[7];
-    dfl X[4][3], h[2][3];
+  struct Col {
+    df2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
+  };
+  __device__ __forceinline__ Col column(const dfl (&Mi)[2][9], const dfl (&dM)[2], int) const {
+    Col c;
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const int c0 = kCorner[w][0], c1 = kCorner[w][1], c2 = kCorner[w][2];
-      const dfl* M = Mi[w];
-      const dfl f = (vw6 * dM[w]) * add_nc(add_nc(sn[c0][0], sn[c1][0]), sn[c2][0]);
-      const dfl fr = f * r;
+    for (int q = 0; q < 9; ++q) c.M[q] = pack(Mi[0][q], Mi[1][q]);
+    c.dM = pack(dM[0], dM[1]);
+    return c;
+  }
+  // the two wedges in the lanes of packed double-floats (x = W0, y = W1); corners as in OpA<dfl, false>
+  __device__ __forceinline__ void cell(const dfl (&sn)[4][1], const dfl (&)[4][1], const dfl (&)[2][9],
+                                       const dfl (&)[2], const dfl* lc, const dfl (&)[2], dfl (&accb)[4][3],
+                                       dfl (&acct)[4][3], const Col& col) const {
+    const df2 r = pack(lc[4], lc[4]), vw6 = pack(lc[7], lc[7]);
+    const df2* M = col.M;
+    const dfl s12 = add_nc(sn[1][0], sn[2][0]);  // corners 10 and 01 belong to both wedges
+    const df2 f = mul2(mul2(vw6, col.dM), add_nc2(pack(sn[0][0], sn[3][0]), pack(s12, s12)));
+    const df2 fr = mul2(f, r);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const dfl h0 = f * M[c], h1 = f * M[3 + c];
-        h[w][c] = fr * M[6 + c];
-        X[c0][c] = -(h0 + h1);
-        if (w == 0) {
-          X[c1][c] = h0, X[c2][c] = h1;
-        } else {
-          X[c1][c] += h0, X[c2][c] += h1;
-        }
-      }
+    for (int c = 0; c < 3; ++c) {
+      const df2 h0 = mul2(f, M[c]), h1 = mul2(f, M[3 + c]), h2 = mul2(fr, M[6 + c]);
+      const df2 x03 = add2(h0, h1);
+      const df2 x12 = add2(pack(lane_x(h0), lane_x(h1)), pack(lane_y(h1), lane_y(h0)));
+      const dfl hs = lane_x(h2) + lane_y(h2);
+      const df2 h12 = pack(hs, hs);
+      const df2 b03 = add2(x03, h2), t03 = sub2(h2, x03);  // bottom -(x03 + h2), top h2 - x03
+      const df2 b12 = sub2(x12, h12), t12 = add2(x12, h12);
+      accb[0][c] = -lane_x(b03), acct[0][c] = lane_x(t03);
+      accb[3][c] = -lane_y(b03), acct[3][c] = lane_y(t03);
+      accb[1][c] = lane_x(b12), acct[1][c] = lane_x(t12);
+      accb[2][c] = lane_y(b12), acct[2][c] = lane_y(t12);
     }
-    combine_corners<dfl, 3>(X, h, accb, acct);
   }
 };
 
@@ -967,44 +982,57 @@ struct OpMass {
 
 // Double-float diagonal (one-point, no hourglass control): sums of positive terms, so every
 // addition but the accumulation over the two wedges uses add_nc / fma_nc.
+// Double-float diagonal without hourglass control, the two wedges of the cell in the lanes of
+// packed df2 values (x = W0, y = W1) as in OpA<dfl, false>; the factor table comes per cell
+// (Level::dcoefdf2), one 16-byte load per factor for both wedges.  Every contribution is a sum of
+// squares, so the node sums of the tile kernel (POSITIVE) and the corner sums here use the
+// double-word addition without the second TwoSum, which is accurate for operands of one sign.
 template <>
 struct OpDiag<dfl, false> {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false;
+  static constexpr bool USES_ETA = true, LOADS = false, NEEDS_D = false, POSITIVE = true;
   struct Col {
-    int t0;
+    int p0;  // the cell's entry of the per-cell table
   };
   int div_term;
   dfl hgk;
-  const dfl* coef;  // [kDiagCoef][n_tri]
-  int n_tri;
-  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int t0) const { return Col{t0}; }
+  const float4* coef;  // [kDiagCoef][n_tri / 2]
+  int n_pair;
+  __device__ __forceinline__ Col column(const dfl (&)[2][9], const dfl (&)[2], int t0) const { return Col{t0 >> 1}; }
   __device__ __forceinline__ void cell(const dfl (&)[4][1], const dfl (&)[4][1], const dfl (&)[2][9], const dfl (&dM)[2],
                                        const dfl* lc, const dfl (&eta)[2], dfl (&accb)[4][3], dfl (&acct)[4][3],
                                        const Col& col) const {
-    const dfl r = lc[4], vw2 = lc[5];
-    const dfl r2 = r * r, rr(r.hi + r.hi, r.lo + r.lo);  // exact doubling
+    const df2 r = pack(lc[4], lc[4]), vw2 = pack(lc[5], lc[5]);
+    const df2 r2 = mul2(r, r), rr{p2add(r.hi, r.hi), p2add(r.lo, r.lo)};  // exact doubling
+    const df2 A = mul2(mul2(vw2, pack(dM[0], dM[1])), pack(eta[0], eta[1]));
+    const df2 Ar2 = mul2(A, r2), A2r = mul2(A, rr);
+    const float4* const cf = coef + col.p0;
+    auto C = [&](int q) {
+      const float4 v = cf[(int64_t)q * n_pair];
+      return df2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    };
+    df2 AQ[3];
 #pragma unroll
-    for (int w = 0; w < 2; ++w) {
-      const dfl* cf = coef + col.t0 + w;
-      const dfl A = (vw2 * dM[w]) * eta[w];
-      const dfl Ar2 = A * r2, A2r = A * rr;
-      dfl AQ[3];
+    for (int d = 0; d < 3; ++d) AQ[d] = mul2(Ar2, C(18 + d));
+    df2 vb[3][3], vt[3][3];  // local node a, component d; lanes (W0, W1)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) AQ[d] = Ar2 * cf[(18 + d) * n_tri];
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int q = kCorner[w][a];
-        const bool first = w == 0 || q == 3;  // corner 11 belongs to W1 only
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const dfl inner = fma_nc(A, cf[(3 * a + d) * n_tri], AQ[d]);
-          const dfl cr = A2r * cf[(9 + 3 * a + d) * n_tri];
-          const dfl vb = add_nc(inner, -cr), vt = add_nc(inner, cr);
-          accb[q][d] = first ? vb : add_nc(accb[q][d], vb);
-          acct[q][d] = first ? vt : add_nc(acct[q][d], vt);
-        }
+      for (int d = 0; d < 3; ++d) {
+        const df2 inner = fma_nc2(A, C(3 * a + d), AQ[d]);
+        const df2 cr = mul2(A2r, C(9 + 3 * a + d));
+        vb[a][d] = add_nc2(inner, df2{p2neg(cr.hi), p2neg(cr.lo)});
+        vt[a][d] = add_nc2(inner, cr);
       }
+    // corners: 00 = W0 node 0, 11 = W1 node 0, 10 = W0 node 1 + W1 node 2, 01 = W0 node 2 + W1 node 1
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      accb[0][d] = lane_x(vb[0][d]), acct[0][d] = lane_x(vt[0][d]);
+      accb[3][d] = lane_y(vb[0][d]), acct[3][d] = lane_y(vt[0][d]);
+      const df2 b12 = add_nc2(pack(lane_x(vb[1][d]), lane_x(vb[2][d])), pack(lane_y(vb[2][d]), lane_y(vb[1][d])));
+      const df2 t12 = add_nc2(pack(lane_x(vt[1][d]), lane_x(vt[2][d])), pack(lane_y(vt[2][d]), lane_y(vt[1][d])));
+      accb[1][d] = lane_x(b12), accb[2][d] = lane_y(b12);
+      acct[1][d] = lane_x(t12), acct[2][d] = lane_y(t12);
     }
   }
 };
@@ -1540,6 +1568,18 @@ struct TileSmemHF {
   static constexpr size_t bytes = sizeof(C) * (size_t)(SD + SM);
 };
 
+// Ops whose contributions all have one sign (POSITIVE = true) let the tile kernel sum nodes with
+// the double-word addition without the second TwoSum; the others use the accurate one.
+template <typename Op, typename = void>
+struct IsPositive : std::false_type {};
+template <typename Op>
+struct IsPositive<Op, std::void_t<decltype(Op::POSITIVE)>> : std::integral_constant<bool, Op::POSITIVE> {};
+template <typename Op, typename C>
+__device__ __forceinline__ C node_add(const C& a, const C& b) {
+  if constexpr (std::is_same<C, dfl>::value && IsPositive<Op>::value) return add_nc(a, b);
+  else return a + b;
+}
+
 // storage <-> compute conversions: identities, or binary64 <-> double-float
 template <typename C>
 __device__ __forceinline__ C to_compute(double x) {
@@ -1673,9 +1713,9 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) {
         C a = acc[0][c];
-        if (ti >= 1) a += SM(0, c, ti - 1, tj);
-        if (tj >= 1) a += SM(1, c, ti, tj - 1);
-        if (ti >= 1 && tj >= 1) a += SM(2, c, ti - 1, tj - 1);
+        if (ti >= 1) a = node_add<Op>(a, SM(0, c, ti - 1, tj));
+        if (tj >= 1) a = node_add<Op>(a, SM(1, c, ti, tj - 1));
+        if (ti >= 1 && tj >= 1) a = node_add<Op>(a, SM(2, c, ti - 1, tj - 1));
         v[c] = a;
       }
       if (interior) store_node(k, c00 + k * LS, lat00, v);
@@ -1690,9 +1730,9 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
       for (int c = 0; c < NOUT; ++c) {
         C a = C(0.0);
-        if (si >= 1 && sj < TJ) a += SM(0, c, si - 1, sj);
-        if (sj >= 1 && si < TI) a += SM(1, c, si, sj - 1);
-        if (si >= 1 && sj >= 1) a += SM(2, c, si - 1, sj - 1);
+        if (si >= 1 && sj < TJ) a = node_add<Op>(a, SM(0, c, si - 1, sj));
+        if (sj >= 1 && si < TI) a = node_add<Op>(a, SM(1, c, si, sj - 1));
+        if (si >= 1 && sj >= 1) a = node_add<Op>(a, SM(2, c, si - 1, sj - 1));
         v[c] = a;
       }
       ring_store(k, i0 + si, j0 + sj, 2 * (si == 0) + (sj == 0), v);
@@ -1766,7 +1806,7 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int c = 0; c < NOUT; ++c) accb[q][c] += carry[q][c];
+        for (int c = 0; c < NOUT; ++c) accb[q][c] = node_add<Op>(accb[q][c], carry[q][c]);
       exchange_write(k, accb);
     }
     if (NS == 0 || k < kc0) __syncthreads();
@@ -2739,10 +2779,11 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
       if (!L.dcoefdf) return cudaErrorInvalidValue;
       const dfl* cdf = reinterpret_cast<const dfl*>(L.dcoefdf);
       const dfl hk(hg_coef(L, div_term));
+      if (!hg && !L.dcoefdf2) return cudaErrorInvalidValue;
       e = hg ? launch_tile<T, OpDiag<dfl, true>, 0>(L, bc, OpDiag<dfl, true>{div_term, hk, cdf, nt}, none, d,
                                                     etav<T>(L), st)
-             : launch_tile<T, OpDiag<dfl, false>, 0>(L, bc, OpDiag<dfl, false>{div_term, hk, cdf, nt}, none, d,
-                                                     etav<T>(L), st);
+             : launch_tile<T, OpDiag<dfl, false>, 0>(L, bc, OpDiag<dfl, false>{div_term, hk, L.dcoefdf2, nt / 2},
+                                                     none, d, etav<T>(L), st);
     } else {
       const T* coef = Tab<T>::dcoef(L);
       e = hg ? launch_tile<T, OpDiag<T, true>, 0>(L, bc, OpDiag<T, true>{div_term, hgk, coef, nt}, none, d,
