@@ -708,7 +708,7 @@ struct OpDiv {
 template <>
 struct OpDiv<dfl, false> {
   static constexpr int NIN = 3, NOUT = 1;
-  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = true, PREFETCH = true;
   struct Col {
     df2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
   };
@@ -789,7 +789,7 @@ struct OpGrad {
 template <>
 struct OpGrad<dfl> {
   static constexpr int NIN = 1, NOUT = 3;
-  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = false;
+  static constexpr bool USES_ETA = false, LOADS = true, NEEDS_D = false, PREFETCH = true;
   struct Col {
     df2 M[9], dM;  // M^-1 entries and |det M| of (W0, W1)
   };
@@ -1574,6 +1574,10 @@ template <typename Op, typename = void>
 struct IsPositive : std::false_type {};
 template <typename Op>
 struct IsPositive<Op, std::void_t<decltype(Op::POSITIVE)>> : std::integral_constant<bool, Op::POSITIVE> {};
+template <typename Op, typename = void>
+struct IsPrefetch : std::false_type {};
+template <typename Op>
+struct IsPrefetch<Op, std::void_t<decltype(Op::PREFETCH)>> : std::integral_constant<bool, Op::PREFETCH> {};
 template <typename Op, typename C>
 __device__ __forceinline__ C node_add(const C& a, const C& b) {
   if constexpr (std::is_same<C, dfl>::value && IsPositive<Op>::value) return add_nc(a, b);
@@ -1644,13 +1648,16 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     si = e <= TJ ? TI : e - TJ - 1;
     sj = e <= TJ ? e : TJ;
   };
-  auto load_node = [&](int off, int lat, int k, C (&vc)[NIN]) {
+  // a node's input values at layer k: load_raw issues the loads, finish_node projects them on the
+  // boundary layers and converts them to the compute type (load_node does both at once)
+  auto load_raw = [&](int off, int k, T (&v)[NIN]) {
     const int o = off + k * LS;
-    T v[NIN];
     v[0] = in0[o];
     if (NIN > 1) v[NIN > 1 ? 1 : 0] = in1[o];
     if (NIN > 2) v[NIN > 2 ? 2 : 0] = in2[o];
     if (NIN > 3) v[NIN > 3 ? 3 : 0] = in3[o];
+  };
+  auto finish_node = [&](int lat, int k, T (&v)[NIN], C (&vc)[NIN]) {
     if ((FLAGS & PROJ_IN) && (k == 0 || k == n_r - 1)) {
       T vv[3] = {v[0], v[NIN > 1 ? 1 : 0], v[NIN > 2 ? 2 : 0]};
       project_vec(vv, svec, (int64_t)lat, (int64_t)NLL, k == 0 ? bc_in : bc_out);
@@ -1659,6 +1666,11 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
     }
 #pragma unroll
     for (int c = 0; c < NIN; ++c) vc[c] = to_compute<C>(v[c]);
+  };
+  auto load_node = [&](int off, int lat, int k, C (&vc)[NIN]) {
+    T v[NIN];
+    load_raw(off, k, v);
+    finish_node(lat, k, v, vc);
   };
   auto put_node = [&](int i, int j, const C (&b)[NIN], const C (&t)[NIN], C (&sv)[NIN], C (&dv)[NIN]) {
 #pragma unroll
@@ -1746,27 +1758,61 @@ __device__ __forceinline__ void tile_body_hf(TN_TILE_PARAMS, T* __restrict__ rin
 #pragma unroll
     for (int c = 0; c < NOUT; ++c) carry[q][c] = C(0.0);
   const int kstart = kc0 > 0 ? kc0 - 1 : 0;
+  // PREFETCH ops (light element work, held by load latency): the raw input of node layer k + 2 is
+  // loaded while cell layer k is computed, and the extra node (one per thread < NX) keeps its
+  // bottom values from the previous layer instead of loading them again
+  constexpr bool PF = IsPrefetch<Op>::value && NS > 0;
+  T rawn[PF ? NIN : 1], rawx[PF ? NIN : 1];
+  C xbot[PF ? NIN : 1];
+  int xoff = 0, xlat = 0, xsi = 0, xsj = 0;
+  const bool hasx = (int)threadIdx.x < NX;  // blockDim.x = TI TJ > NX
+  if (hasx) {
+    extra_node((int)threadIdx.x, xsi, xsj);
+    const int ni = i0 + xsi, nj = j0 + xsj;  // <= N
+    xoff = (int)(d * D.diamond_stride) + ni * P + nj;
+    xlat = d * (N + 1) * P + ni * P + nj;
+  }
   if (NS > 0) load_node(c00, lat00, kstart, ub);
+  if constexpr (PF) {
+    load_raw(c00, kstart + 1, rawn);
+    if (hasx) {
+      load_node(xoff, xlat, kstart, xbot);
+      load_raw(xoff, kstart + 1, rawx);
+    }
+  }
   for (int k = kstart; k < kc1; ++k) {
     C s[4][NIN], dd[4][NIN];
-    if (NS > 0) {
+    if constexpr (PF) {
+      C ut[NIN];
+      finish_node(lat00, k + 1, rawn, ut);
+      if (k + 2 <= kc1) load_raw(c00, k + 2, rawn);
+      put_node(ti, tj, ub, ut, s[0], dd[0]);
+#pragma unroll
+      for (int c = 0; c < NIN; ++c) ub[c] = ut[c];
+      if (hasx) {
+        C xt[NIN], xs[NIN], xd[NIN];
+        finish_node(xlat, k + 1, rawx, xt);
+        if (k + 2 <= kc1) load_raw(xoff, k + 2, rawx);
+        put_node(xsi, xsj, xbot, xt, xs, xd);
+#pragma unroll
+        for (int c = 0; c < NIN; ++c) xbot[c] = xt[c];
+      }
+      __syncthreads();
+    } else if (NS > 0) {
       C ut[NIN];
       load_node(c00, lat00, k + 1, ut);
       put_node(ti, tj, ub, ut, s[0], dd[0]);
 #pragma unroll
       for (int c = 0; c < NIN; ++c) ub[c] = ut[c];
-      for (int e = (int)threadIdx.x; e < NX; e += (int)blockDim.x) {
-        int si, sj;
-        extra_node(e, si, sj);
-        const int ni = i0 + si, nj = j0 + sj;  // <= N
-        const int off = (int)(d * D.diamond_stride) + ni * P + nj;
-        const int lat = d * (N + 1) * P + ni * P + nj;
+      if (hasx) {
         C xb[NIN], xt[NIN], xs[NIN], xd[NIN];
-        load_node(off, lat, k, xb);
-        load_node(off, lat, k + 1, xt);
-        put_node(si, sj, xb, xt, xs, xd);
+        load_node(xoff, xlat, k, xb);
+        load_node(xoff, xlat, k + 1, xt);
+        put_node(xsi, xsj, xb, xt, xs, xd);
       }
       __syncthreads();
+    }
+    if (NS > 0) {
       const int qi[3] = {ti + 1, ti, ti + 1}, qj[3] = {tj, tj + 1, tj + 1};
 #pragma unroll
       for (int q = 1; q < 4; ++q)
