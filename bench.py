@@ -48,11 +48,11 @@ LAW = dict(E=math.log(1e3), jump_r=0.9, jump_factor=30.0)  # x30 below r = 0.9, 
 # from their structure at 240 flops per wedge.
 A_FLOPS_PER_CELL = 480.0
 # ncu figures of the A tile kernel with the packed double-float element op (level 6, 65 layers,
-# 2,621,440 cells, one launch): DRAM bytes (126.06 MB read + 50.31 MB written) and issued warp
-# instructions (264,957,752) per cell, scaled to the bench size by cells; None once the kernel
+# 2,621,440 cells, one launch): DRAM bytes (126.14 MB read + 49.46 MB written) and issued warp
+# instructions (262,034,000) per cell, scaled to the bench size by cells; None once the kernel
 # changes.
-A_TRAFFIC_BYTES_PER_CELL = (126.06e6 + 50.31e6) / 2621440
-A_WARP_INST_PER_CELL = 264957752 / 2621440
+A_TRAFFIC_BYTES_PER_CELL = (126.14e6 + 49.46e6) / 2621440
+A_WARP_INST_PER_CELL = 262034000 / 2621440
 # Issue rate derived from unit counts: 152 SMs x 4 schedulers x 1 warp instruction per clock.
 ISSUE_SLOTS_PER_CLOCK = 152 * 4
 # Hourglass-control coefficient of the solves and the serving stream that use it.
