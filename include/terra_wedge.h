@@ -179,7 +179,11 @@ tn_status tn_get_viscosity(const tn_mesh* mesh, int level, double* eta_dev, void
 /* y = (P A P + (I - P)) u on level h (Eq. matfree with Eq. elemmat; the one-point rule, or the
  * mesh's tn_mesh_opts.hg_kappa / radial_quad_points variant of Sec. 4).
  * u_dev[3], y_dev[3]: node layout of level h, type double (TN_F64) or float (TN_F32);
- * y must not alias u.  Stream-ordered. */
+ * y must not alias u.  Stream-ordered.  On levels with N >= 32 the applies use the level's
+ * preallocated tile-line buffer (FP64 and FP32), so applies on one mesh must not overlap on the
+ * GPU: issue them on one stream, or order their streams with events.  FP32 inputs that start on a
+ * 16-byte boundary take the paired-cell kernel, others the square tiles (same result to FP32
+ * rounding). */
 tn_status tn_apply_A(tn_mesh* mesh, int level, tn_prec prec, const void* const* u_dev, void* const* y_dev,
                      void* stream);
 
