@@ -2168,11 +2168,9 @@ __global__ void k_diag_A(Dims D, const T* __restrict__ geo, const T* __restrict_
                          const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, int nq, T* d0,
                          T* d1, T* d2) {
   const int N = D.N, M = N + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)10 * 2 * M * M;
-  if (tid >= total) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), side_ = (int)((tid / ((int64_t)M * M)) % 2),
-            d = (int)(tid / ((int64_t)M * M * 2));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: lattice points x 2 layers x 10 diamonds
+  if (t >= M * M) return;
+  const int i = t / M, j = t - i * M, side_ = blockIdx.y, d = blockIdx.z;
   const int k = side_ == 0 ? 0 : D.n_r - 1;
   // (cell di, cell dj, wedge, local lateral node) of the six triangles around lattice node (i, j)
   const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
@@ -2246,11 +2244,9 @@ __global__ void k_block_A(Dims D, const T* __restrict__ geo, const T* __restrict
                           const T* __restrict__ svec, int bc_in, int bc_out, int div_term, T hgk, int nq, T* b0,
                           T* b1, T* b2, T* b3, T* b4, T* b5) {
   const int N = D.N, M = N + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)10 * D.n_r * M * M;
-  if (tid >= total) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
-            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: lattice points x n_r x 10 diamonds
+  if (t >= M * M) return;
+  const int i = t / M, j = t - i * M, k = blockIdx.y, d = blockIdx.z;
   const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
   const T gxi[3] = {-1, 1, 0}, geta[3] = {-1, 0, 1};
   const T third = div_term ? (T)(1.0 / 3.0) : (T)1;
@@ -2369,10 +2365,9 @@ __global__ void k_prolong(Dims F, Dims C, int lf, int rf, int ncomp, int apply_b
                           const T* __restrict__ c1, const T* __restrict__ c2, T* f0, T* f1, T* f2,
                           const T* __restrict__ svec, int bc_in, int bc_out) {
   const int N = F.N, M = N + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)10 * F.n_r * M * M) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % F.n_r),
-            d = (int)(tid / ((int64_t)M * M * F.n_r));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: fine lattice points x F.n_r x 10
+  if (t >= M * M) return;
+  const int i = t / M, j = t - i * M, k = blockIdx.y, d = blockIdx.z;
   int li[2], lj[2], nl;
   if (lf == 1 || (!(i & 1) && !(j & 1))) {
     li[0] = lf == 1 ? i : i / 2, lj[0] = lf == 1 ? j : j / 2, nl = 1;
@@ -2415,10 +2410,9 @@ __global__ void k_restrict(Dims F, Dims C, int lf, int rf, int ncomp, const uint
                            const T* __restrict__ f0, const T* __restrict__ f1, const T* __restrict__ f2, T* c0, T* c1,
                            T* c2) {
   const int NC = C.N, MC = NC + 1, NF = F.N, MF = NF + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
-  const int J = (int)(tid % MC), I = (int)((tid / MC) % MC), K = (int)((tid / ((int64_t)MC * MC)) % C.n_r),
-            d = (int)(tid / ((int64_t)MC * MC * C.n_r));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: coarse lattice points x C.n_r x 10
+  if (t >= MC * MC) return;
+  const int I = t / MC, J = t - I * MC, K = blockIdx.y, d = blockIdx.z;
   const int nb[7][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, -1}, {-1, 1}};
   const T* fs[3] = {f0, f1, f2};
   T* cs[3] = {c0, c1, c2};
@@ -2447,10 +2441,9 @@ __global__ void k_restrict(Dims F, Dims C, int lf, int rf, int ncomp, const uint
 template <typename T>
 __global__ void k_project_bdry(Dims D, T* y0, T* y1, T* y2, const T* __restrict__ svec, int bc_in, int bc_out) {
   const int M = D.N + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)10 * 2 * M * M) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), side = (int)((tid / ((int64_t)M * M)) % 2),
-            d = (int)(tid / ((int64_t)M * M * 2));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: lattice points x 2 layers x 10 diamonds
+  if (t >= M * M) return;
+  const int i = t / M, j = t - i * M, side = blockIdx.y, d = blockIdx.z;
   const int k = side == 0 ? 0 : D.n_r - 1;
   const int64_t idx = (int64_t)d * D.diamond_stride + (int64_t)k * D.layer_stride + (int64_t)i * D.P + j;
   T v[3] = {y0[idx], y1[idx], y2[idx]};
@@ -2468,10 +2461,9 @@ template <typename T>
 __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T* __restrict__ layF,
                              EtaView<T> etaF, T* m) {
   const int NC = C.N, MC = NC + 1, NF = F.N;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)10 * C.n_r * MC * MC) return;
-  const int J = (int)(tid % MC), I = (int)((tid / MC) % MC), K = (int)((tid / ((int64_t)MC * MC)) % C.n_r),
-            d = (int)(tid / ((int64_t)MC * MC * C.n_r));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: coarse lattice points x C.n_r x 10
+  if (t >= MC * MC) return;
+  const int I = t / MC, J = t - I * MC, K = blockIdx.y, d = blockIdx.z;
   const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
   // children of coarse W0 / W1: (fine di, fine dj, fine wedge), barycentric weight of local node a
   const int kid[2][4][3] = {{{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}}};
@@ -2508,11 +2500,10 @@ __global__ void k_diag_pmass(Dims F, Dims C, const T* __restrict__ geoF, const T
 __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, double jump_r, double jump_f,
                              const double* __restrict__ lay, double* eta) {
   const int N = D.N;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nw = (int64_t)10 * (D.n_r - 1) * N * N * 2;
-  if (tid >= nw) return;
-  const int w = (int)(tid % 2), j = (int)((tid / 2) % N), i = (int)((tid / (2 * N)) % N),
-            k = (int)((tid / (2 * (int64_t)N * N)) % (D.n_r - 1)), d = (int)(tid / (2 * (int64_t)N * N * (D.n_r - 1)));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: lateral wedges x (n_r - 1) x 10 diamonds
+  if (t >= 2 * N * N) return;
+  const int i = t / (2 * N), r = t - i * 2 * N, j = r >> 1, w = r & 1, k = blockIdx.y, d = blockIdx.z;
+  const int64_t tid = (((int64_t)d * (D.n_r - 1) + k) * N * N + (int64_t)i * N + j) * 2 + w;  // wedge index
   int pi_[3], pj_[3];
   if (w == 0) pi_[0] = i, pj_[0] = j, pi_[1] = i + 1, pj_[1] = j, pi_[2] = i, pj_[2] = j + 1;
   else pi_[0] = i + 1, pj_[0] = j + 1, pi_[1] = i, pj_[1] = j + 1, pi_[2] = i + 1, pj_[2] = j;
@@ -2528,12 +2519,10 @@ __global__ void k_eta_from_T(Dims D, const double* __restrict__ T, double E, dou
 
 __global__ void k_eta_coarsen(Dims F, Dims C, int lf, int rf, const double* __restrict__ ef, double* ec) {
   const int NC = C.N, NF = F.N;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t nw = (int64_t)10 * (C.n_r - 1) * NC * NC * 2;
-  if (tid >= nw) return;
-  const int w = (int)(tid % 2), J = (int)((tid / 2) % NC), I = (int)((tid / (2 * NC)) % NC),
-            K = (int)((tid / (2 * (int64_t)NC * NC)) % (C.n_r - 1)),
-            d = (int)(tid / (2 * (int64_t)NC * NC * (C.n_r - 1)));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: coarse lateral wedges x (C.n_r - 1) x 10
+  if (t >= 2 * NC * NC) return;
+  const int I = t / (2 * NC), r = t - I * 2 * NC, J = r >> 1, w = r & 1, K = blockIdx.y, d = blockIdx.z;
+  const int64_t tid = (((int64_t)d * (C.n_r - 1) + K) * NC * NC + (int64_t)I * NC + J) * 2 + w;  // wedge index
   const int kid[2][4][3] = {{{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}}};
   double s = 0;
   const int nlat = lf == 2 ? 4 : 1;
@@ -2559,10 +2548,9 @@ __global__ void k_buoyancy(Dims D, const double* __restrict__ geo, const double*
                            const double* __restrict__ svec, const double* __restrict__ T, double Ra, int bc_in,
                            int bc_out, const double* __restrict__ cellw, double* f0, double* f1, double* f2) {
   const int N = D.N, M = N + 1;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)10 * D.n_r * M * M) return;
-  const int j = (int)(tid % M), i = (int)((tid / M) % M), k = (int)((tid / ((int64_t)M * M)) % D.n_r),
-            d = (int)(tid / ((int64_t)M * M * D.n_r));
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // grid: lattice points x n_r x 10 diamonds
+  if (t >= M * M) return;
+  const int i = t / M, j = t - i * M, k = blockIdx.y, d = blockIdx.z;
   const int tri[6][4] = {{0, 0, 0, 0}, {-1, 0, 0, 1}, {-1, 0, 1, 2}, {0, -1, 0, 2}, {0, -1, 1, 1}, {-1, -1, 1, 0}};
   double f[3] = {0, 0, 0};
   for (int q = 0; q < 6; ++q) {
@@ -2842,8 +2830,7 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
            : launch_tile<T, OpDiagG<T, false>, 0>(L, bc, OpDiagG<T, false>{div_term, hgk}, none, d, etav<T>(L), st);
   }
   if (e != cudaSuccess) return e;
-  const int64_t n = (int64_t)10 * 2 * (L.N + 1) * (L.N + 1);
-  k_diag_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
+  k_diag_A<T><<<dim3(nblk((int64_t)(L.N + 1) * (L.N + 1), 256), 2, 10), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
                                             bc.out, div_term, hgk, L.quad, d[0], d[1], d[2]);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -2853,8 +2840,7 @@ cudaError_t launch_diag_A(const Level& L, BC bc, int div_term, T* const* d, cuda
 template <typename T>
 cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b, cudaStream_t st) {
   Dims D = dims(L);
-  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
-  k_block_A<T><<<nblk(n, 256), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
+  k_block_A<T><<<dim3(nblk((int64_t)(L.N + 1) * (L.N + 1), 256), L.n_r, 10), 256, 0, st>>>(D, Tab<T>::geo(L), Tab<T>::lay(L), etav<T>(L), Tab<T>::s(L), bc.in,
                                              bc.out, div_term, (T)hg_coef(L, div_term), L.quad, b[0], b[1], b[2], b[3],
                                              b[4],
                                              b[5]);
@@ -2873,8 +2859,7 @@ cudaError_t launch_block_inv_A(const Level& L, BC bc, int div_term, T* const* b,
 
 template <typename T>
 cudaError_t launch_diag_pmass(const Level& F, const Level& C, T* m, cudaStream_t st) {
-  const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
-  k_diag_pmass<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), etav<T>(F), m);
+  k_diag_pmass<T><<<dim3(nblk((int64_t)(C.N + 1) * (C.N + 1), 256), C.n_r, 10), 256, 0, st>>>(dims(F), dims(C), Tab<T>::geo(F), Tab<T>::lay(F), etav<T>(F), m);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   T* out[1] = {m};
@@ -2900,13 +2885,12 @@ cudaError_t launch_interface(const Level& L, BC bc, int ncomp, int mode, T* cons
 template <typename T>
 cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* c,
                            T* const* f, cudaStream_t st) {
-  const int64_t n = (int64_t)10 * F.n_r * (F.N + 1) * (F.N + 1);
   const T* c1 = ncomp > 1 ? c[1] : c[0];
   const T* c2 = ncomp > 2 ? c[2] : c[0];
   T* f1 = ncomp > 1 ? f[1] : f[0];
   T* f2 = ncomp > 2 ? f[2] : f[0];
   const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
-  k_prolong<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, apply_bc, c[0], c1, c2, f[0], f1, f2,
+  k_prolong<T><<<dim3(nblk((int64_t)(F.N + 1) * (F.N + 1), 256), F.n_r, 10), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, apply_bc, c[0], c1, c2, f[0], f1, f2,
                                              Tab<T>::s(F), bc.in, bc.out);
   return cudaGetLastError();
 }
@@ -2914,31 +2898,29 @@ cudaError_t launch_prolong(const Level& F, const Level& C, BC bc, int ncomp, int
 template <typename T>
 cudaError_t launch_restrict(const Level& F, const Level& C, BC bc, int ncomp, int apply_bc, const T* const* f,
                             T* const* c, cudaStream_t st) {
-  const int64_t n = (int64_t)10 * C.n_r * (C.N + 1) * (C.N + 1);
   const T* f1 = ncomp > 1 ? f[1] : f[0];
   const T* f2 = ncomp > 2 ? f[2] : f[0];
   T* c1 = ncomp > 1 ? c[1] : c[0];
   T* c2 = ncomp > 2 ? c[2] : c[0];
   const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
-  k_restrict<T><<<nblk(n, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, F.owned, f[0], f1, f2, c[0], c1, c2);
+  k_restrict<T><<<dim3(nblk((int64_t)(C.N + 1) * (C.N + 1), 256), C.n_r, 10), 256, 0, st>>>(dims(F), dims(C), lf, rf, ncomp, F.owned, f[0], f1, f2, c[0], c1, c2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_interface<T>(C, bc, ncomp, 0, c, nullptr, st);
   if (e != cudaSuccess || !(apply_bc && ncomp == 3)) return e;
-  const int64_t nb = (int64_t)10 * 2 * (C.N + 1) * (C.N + 1);
-  k_project_bdry<T><<<nblk(nb, 256), 256, 0, st>>>(dims(C), c[0], c[1], c[2], Tab<T>::s(C), bc.in, bc.out);
+  k_project_bdry<T><<<dim3(nblk((int64_t)(C.N + 1) * (C.N + 1), 256), 2, 10), 256, 0, st>>>(dims(C), c[0], c[1], c[2], Tab<T>::s(C), bc.in, bc.out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eta_from_T(const Level& L, const double* T, double E, double jump_r, double jump_f, double* eta,
                               cudaStream_t st) {
-  k_eta_from_T<<<nblk(L.n_wedges, 256), 256, 0, st>>>(dims(L), T, E, jump_r, jump_f, L.lay64, eta);
+  k_eta_from_T<<<dim3(nblk((int64_t)2 * L.N * L.N, 256), L.n_r - 1, 10), 256, 0, st>>>(dims(L), T, E, jump_r, jump_f, L.lay64, eta);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eta_coarsen(const Level& F, const Level& C, const double* ef, double* ec, cudaStream_t st) {
   const int lf = F.N / C.N, rf = (F.n_r - 1) / (C.n_r - 1);
-  k_eta_coarsen<<<nblk(C.n_wedges, 256), 256, 0, st>>>(dims(F), dims(C), lf, rf, ef, ec);
+  k_eta_coarsen<<<dim3(nblk((int64_t)2 * C.N * C.N, 256), C.n_r - 1, 10), 256, 0, st>>>(dims(F), dims(C), lf, rf, ef, ec);
   return cudaGetLastError();
 }
 
@@ -2986,8 +2968,7 @@ cudaError_t launch_to_f32(const double* a, float* b, int64_t n, cudaStream_t st)
 }
 
 cudaError_t launch_buoyancy(const Level& L, BC bc, const double* T, double Ra, double* const* f, cudaStream_t st) {
-  const int64_t n = (int64_t)10 * L.n_r * (L.N + 1) * (L.N + 1);
-  k_buoyancy<<<nblk(n, 256), 256, 0, st>>>(dims(L), L.geo64, L.lay64, L.s64, T, Ra, bc.in, bc.out, L.bw64, f[0],
+  k_buoyancy<<<dim3(nblk((int64_t)(L.N + 1) * (L.N + 1), 256), L.n_r, 10), 256, 0, st>>>(dims(L), L.geo64, L.lay64, L.s64, T, Ra, bc.in, bc.out, L.bw64, f[0],
                                            f[1], f[2]);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
