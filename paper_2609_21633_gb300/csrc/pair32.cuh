@@ -9,14 +9,16 @@
 //   A = (i, j) and B = (i + 1, j), and every element operation works on both at once: lane x of a
 //   float2 is cell A, lane y cell B.  Both cells run the same instruction stream, so the packed
 //   arithmetic needs no lane exchange (the wedges are taken one after the other).
-// * Node values arrive in shared memory by cp.async, several node layers ahead of the radial
-//   sweep (kPStages buffers of the 17 x 36 node patch of a layer per component), so no thread
-//   computes global addresses or waits on a global load in the sweep.
+// * Node values (the 17 x 36 node patch of a layer per component), the tile's viscosity of a cell
+//   layer and the layer constants arrive in shared memory by cp.async, kPAhead layers ahead of the
+//   radial sweep in kPStages buffers, so no thread computes global addresses or waits on a global
+//   load in the sweep.
 // * Cell contributions are summed into node values in a fixed order: the two cells of a thread in
 //   registers, the left neighbour's by a warp shuffle, the upper warp's through shared memory.
-//   Nodes on the tile lines i = i0, i0 + 16 and j = j0, j0 + 32 leave one partial per tile in the
-//   level's ring buffer (the layout of the FP64 halo-free tiles), which k_ring_fix sums and
-//   finishes; no atomics, so results do not depend on scheduling.
+//   Nodes on the tile lines i = i0, i0 + 16 and j = j0, j0 + 32 leave one float4 partial per tile
+//   in the level's ring buffer (the tile-line index of the FP64 halo-free tiles).  k_ring4_fix
+//   sums and finishes those inside the diamond, k_ring4_edges those on the diamond edges with the
+//   sum over their copies; no atomics, so results do not depend on scheduling.
 
 constexpr int kPTI = 16, kPTJ = 32, kPThreads = 256;  // cells per tile, threads per CTA
 constexpr int kPRows = kPTI + 1;                      // node rows i0 .. i0 + 16 of a tile
